@@ -1,0 +1,218 @@
+/*
+ * chi0.h -- C-ABI of the GB300 (sm_103a) bare-susceptibility library.
+ *
+ * Computes the non-interacting susceptibility of Heil, Sormann, Boeri, Aichhorn and
+ * von der Linden, "Accurate bare susceptibilities from full-potential ab initio
+ * calculations" (Sec. II):
+ *
+ *   Re chi0(q,w) =  sum_{n,m} int_1BZ dk/(4 pi^3) Th(eF - e^m_k) Th(e^n_{k+q} - eF)
+ *                   |<m,k|e^{-iq.r}|n,k+q>|^2 [1/(e^m_k - e^n_{k+q} + w) + 1/(e^m_k - e^n_{k+q} - w)]
+ *                                                                                    (Eq. 1)
+ *   Im chi0(q,w) = -sum_{n,m} int_1BZ dk/(4 pi^2) Th Th |<..>|^2 delta(w + e^m_k - e^n_{k+q})
+ *                                                                         (Eq. 2, w >= 0)
+ *   Im chi0(q,-w) = -Im chi0(q,w)                                                  (Eq. 3)
+ *
+ * by the linear tetrahedron method with the two carvings of Sec. II (first by
+ * Th(eF - e^m_k), then by Th(e^n_{k+q} - eF), Eq. 4), energies and |M|^2 linearly
+ * interpolated on every tetrahedron, and closed-form integrals on the final
+ * tetrahedra (static w = 0, PV real part, delta-function imaginary part).
+ *
+ * Matrix elements use the tight-binding form M_mn(k,q) = sum_o conj(C_k[o][m]) C_{k+q}[o][n]
+ * (Sec. III footnote; orbitals at the cell origin, periodic gauge), or |M|^2 = 1 (the
+ * constant-matrix-element approximation, CMA, Sec. III).
+ *
+ * Units and normalisation: k is integrated in fractional coordinates (BZ volume 1);
+ * chi0 is returned per unit cell, both spins, in states/(energy unit) -- i.e. the
+ * dk/(4 pi^3) measure of Eq. 1 times the cell volume.  Energies in any unit (eV, Ha).
+ *
+ * Threading: a plan is used by one host thread at a time; all work of a plan runs on
+ * the CUDA stream given in its options.  Every call returns CHI0_OK (0) or a negative
+ * status; no C++ exception crosses this interface.  Validation happens before any
+ * launch.  After any error the plan can still be destroyed, and chi0_last_error()
+ * describes the failure.
+ */
+#ifndef CHI0_H
+#define CHI0_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define CHI0_OK 0
+#define CHI0_EINVAL -1    /* invalid argument (sizes, window, pointers, layout)      */
+#define CHI0_ENOMEM -2    /* device or host allocation failed                        */
+#define CHI0_ECUDA -3     /* CUDA runtime error (launch, copy, device fault)         */
+#define CHI0_ETIMEOUT -4  /* a bounded device-side wait ran out of its budget        */
+#define CHI0_ENOTSUP -5   /* option combination not supported                        */
+#define CHI0_EINTERNAL -6 /* internal consistency check failed                        */
+
+/* ---------------------------------------------------------------- enumerations */
+#define CHI0_C64 1  /* complex64: interleaved float (re, im)  */
+#define CHI0_C128 2 /* complex128: interleaved double (re, im) */
+
+#define CHI0_PREC_FP64 0  /* every step in FP64 (overlaps, weights, accumulation)          */
+#define CHI0_PREC_MIXED 1 /* FP32 overlaps/weights, FP64 in the near-degenerate branches,
+                             FP64 accumulation                                            */
+
+#define CHI0_OVL_FP32 0   /* mixed precision: overlaps with FP32 FMA on the CUDA cores     */
+#define CHI0_OVL_BF16X3 1 /* mixed precision: overlaps on the tensor cores, 3-piece BF16
+                             split of each operand, FP32 accumulate (nbands >= 16)        */
+
+#define CHI0_SIGN_POSITIVE 0 /* return -(Eq. 1) and -(Eq. 2): static chi0 > 0, Im >= 0 (w>0) */
+#define CHI0_SIGN_PAPER 1    /* return Eq. 1 and Eq. 2 exactly as printed                    */
+
+/* ---------------------------------------------------------------- input structs */
+/* k mesh and eigen-data at its corners.
+ *   n[3]       cubes per reciprocal axis.
+ *   periodic   1: Gamma-centred periodic grid, n0*n1*n2 corners at fractional k = i/n,
+ *                 corner indices wrap modulo n (tight-binding models);
+ *              0: open grid spanning one cube edge to edge, (n0+1)(n1+1)(n2+1) corners,
+ *                 no wrap (free-electron tests); q must then be given explicitly.
+ *   Corner index c = (i0*N1 + i1)*N2 + i2 with N the corner counts per axis.
+ *   energies   [Nc][nbands] float64, ascending per corner.
+ *   evecs      [Nc][norb][nbands] complex (evec_dtype): evecs[c][o][b] is the weight of
+ *              orbital o in band b at corner c.  May be NULL only with opts.cma = 1.
+ *   e_fermi    Fermi level (an input: the library never solves for it).
+ * Host or device pointers according to opts.inputs_on_device. */
+typedef struct {
+  int n[3];
+  int periodic;
+  int nbands;
+  int norb;
+  const double *energies;
+  const void *evecs;
+  int evec_dtype;
+  double e_fermi;
+} chi0_kgrid_t;
+
+/* Tetrahedral mesh (Sec. II: the integration domain split into tetrahedra).
+ *   corners == NULL: builtin mesh, 6 tetrahedra per cube sharing the cube's
+ *     (000)-(111) diagonal, tetrahedron 6*cube + p = {000, e_a, e_a + e_b, 111} for the
+ *     p-th axis order (a, b, c) in lexicographic order of the permutations of (0,1,2);
+ *     cube = (i0*n1 + i1)*n2 + i2; each of volume 1/(6 n0 n1 n2).
+ *   corners != NULL: ntet tetrahedra, corners[4*t + i] corner indices, volume[t] their
+ *     fractional volumes (BZ volume 1).  Always HOST pointers, copied by chi0_plan. */
+typedef struct {
+  int ntet;
+  const int32_t *corners;
+  const double *volume;
+} chi0_tetra_t;
+
+/* Band window [lo, hi): both the occupied band m and the empty band n run over it
+ * (Sec. III band truncation). */
+typedef struct {
+  int lo, hi;
+} chi0_band_window_t;
+
+/* One q point.
+ *   e_kq == NULL: on-grid q, k+q corner = corner shifted by shift[] (periodic grids).
+ *   e_kq != NULL: explicit energies [Nc][nbands] at k+q for every corner c, and (unless
+ *     CMA) c_kq [Nc][norb][nbands] eigenvectors at k+q (same layout/dtype as the plan).
+ *     Host or device according to opts.inputs_on_device; read during the call only.
+ *   win   per-q band window; {-1, -1} selects the plan's window.
+ *   gamma 1: q is Gamma (or a reciprocal lattice vector).  Eq. 1 then has an empty
+ *     intraband region; the library replaces the intraband terms by their q -> 0 limit,
+ *     the density of states N(eF) (Sec. III), added to the static value and to Re at
+ *     w = 0.  An all-zero shift with e_kq == NULL sets this automatically. */
+typedef struct {
+  int shift[3];
+  const double *e_kq;
+  const void *c_kq;
+  chi0_band_window_t win;
+  int gamma;
+} chi0_q_t;
+
+/* Options (initialise with chi0_opts_default).
+ *   precision     CHI0_PREC_FP64 | CHI0_PREC_MIXED.
+ *   overlap       CHI0_OVL_* (mixed precision only).
+ *   cma           1: |M|^2 = 1 (no eigenvectors needed).
+ *   sign          CHI0_SIGN_POSITIVE | CHI0_SIGN_PAPER.
+ *   tau           mixed precision: knot-gap threshold (relative to the largest knot)
+ *                 below which a final tetrahedron's weights are evaluated in FP64.
+ *   inputs_on_device   1: every energy/eigenvector pointer (plan and q) is a device
+ *                 pointer the caller keeps alive; 0: host pointers, copied.
+ *   outputs_on_device  1: chi/re/im are device pointers; 0: host pointers.
+ *   stream        cudaStream_t (NULL = legacy default stream) for every copy and launch.
+ *   profile       1: time each kernel with CUDA events on the stream (chi0_plan_stats).
+ *   wait_budget   reserved for bounded device waits (cycles; 0 = library default). */
+typedef struct {
+  int precision;
+  int overlap;
+  int cma;
+  int sign;
+  double tau;
+  int inputs_on_device;
+  int outputs_on_device;
+  void *stream;
+  int profile;
+  long long wait_budget;
+  int reserved[8];
+} chi0_opts_t;
+
+typedef struct chi0_plan chi0_plan_t;
+
+/* Per-kernel timing and work counters accumulated over a plan's calls (opts.profile):
+ * time_ms[k] / launches[k] for k = CHI0_K_* (CUDA events on the plan's stream around each
+ * launch), calls, and the final-tetrahedron and FP64-branch counts of the weight kernels. */
+#define CHI0_K_OVERLAP 0
+#define CHI0_K_STATIC 1
+#define CHI0_K_DYNAMIC 2
+#define CHI0_K_REDUCE 3
+#define CHI0_K_DOS 4
+#define CHI0_K_BANDS 5
+#define CHI0_K_COUNT 8
+typedef struct {
+  double time_ms[CHI0_K_COUNT];
+  long long launches[CHI0_K_COUNT];
+  long long calls;
+  long long pieces;     /* final tetrahedra evaluated (profile mode)                     */
+  long long fp64_evals; /* weight evaluations taken by the FP64 branch (mixed, profile)  */
+} chi0_stats_t;
+
+/* ---------------------------------------------------------------- entry points */
+
+/* Fills *opts with defaults: FP64, FP32 overlaps, exact |M|^2, positive sign,
+ * tau = 2^-10, host inputs and outputs, default stream, no profiling. */
+void chi0_opts_default(chi0_opts_t *opts);
+
+/* Builds a plan for one k mesh (Sec. II: the tetrahedron decomposition and the corner
+ * eigen-data).  Validates every size, copies host inputs (or adopts device pointers),
+ * and allocates the device scratch for the largest window.  *out receives the plan
+ * (NULL on error).  Errors: CHI0_EINVAL (bad sizes, window outside [0, nbands),
+ * evecs missing without CMA, non-periodic grid with builtin tetrahedra missing),
+ * CHI0_ENOMEM, CHI0_ECUDA. */
+int chi0_plan(const chi0_kgrid_t *kgrid, const chi0_tetra_t *tetra, chi0_band_window_t window,
+              const chi0_opts_t *opts, chi0_plan_t **out);
+
+/* Static chi0(q, w = 0) (Eq. 1 at w = 0, Sec. III) for nq q points: chi[iq].
+ * Errors: CHI0_EINVAL (nq <= 0, NULL pointers, shift on a non-periodic grid, window
+ * outside the plan's), CHI0_ECUDA, CHI0_ETIMEOUT. */
+int chi0_static(chi0_plan_t *plan, const chi0_q_t *q, int nq, double *chi);
+
+/* Dynamic chi0(q, w) (Eqs. 1-3) on nw frequencies: re[iq*nw + iw], im[iq*nw + iw].
+ * Re is the principal value of Eq. 1; Im is Eq. 2 for w > 0, 0 at w = 0, and odd
+ * (Eq. 3) for w < 0.  Errors as chi0_static, plus CHI0_EINVAL for nw <= 0. */
+int chi0_dynamic(chi0_plan_t *plan, const chi0_q_t *q, int nq, const double *omega, int nw,
+                 double *re, double *im);
+
+/* Copies the plan's accumulated counters into *stats.  CHI0_EINVAL on NULL. */
+int chi0_plan_stats(const chi0_plan_t *plan, chi0_stats_t *stats);
+
+/* Releases every device and host resource of the plan.  NULL-safe. */
+void chi0_destroy(chi0_plan_t *plan);
+
+/* Static-lifetime description of the last error of the plan (or of the last failed
+ * chi0_plan call when plan == NULL). */
+const char *chi0_last_error(const chi0_plan_t *plan);
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+int chi0_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHI0_H */

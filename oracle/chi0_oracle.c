@@ -185,28 +185,30 @@ double oracle_delta_weight(const double d[4], int j, double w) {
 /* ============================================================================
  * carving (Sec. II)
  * ========================================================================== */
+/* vertex of a (carved) tetrahedron: a = e^m_k - eF, D = e^n_{k+q} - e^m_k (so that
+ * b = e^n_{k+q} - eF = a + D), f = |M|^2, all linear; D is carried as its own attribute
+ * so that it vanishes exactly wherever it vanishes at the corners */
 typedef struct {
-  double a, b, f;
+  double a, D, f;
   double l[4]; /* barycentric coordinates in the parent tetrahedron */
 } vtx;
 
 static void vmix(const vtx *P, const vtx *Q, double t, vtx *R) {
   int i;
   R->a = (1.0 - t) * P->a + t * Q->a;
-  R->b = (1.0 - t) * P->b + t * Q->b;
+  R->D = (1.0 - t) * P->D + t * Q->D;
   R->f = (1.0 - t) * P->f + t * Q->f;
   for (i = 0; i < 4; ++i) R->l[i] = (1.0 - t) * P->l[i] + t * Q->l[i];
 }
 
-static double vkey(const vtx *v, int which) { return which == 0 ? v->a : -v->b; }
+static double vkey(const vtx *v, int which) { return which == 0 ? v->a : -(v->a + v->D); }
 
 /* Point on edge P-Q where the cut function vanishes; key(P) < 0 <= key(Q). */
 static void vcut(const vtx *P, const vtx *Q, int which, vtx *R) {
   double kp = vkey(P, which), kq = vkey(Q, which);
   double t = kp / (kp - kq);
   vmix(P, Q, t, R);
-  if (which == 0) R->a = 0.0;
-  else R->b = 0.0;
+  if (which == 0) R->a = 0.0; /* on the first cut plane; the second cut is the last one */
 }
 
 /* Keep the part of tetrahedron T where key < 0 (which = 0: a < 0, first carving;
@@ -281,7 +283,7 @@ int oracle_carve(const double a[4], const double b[4], const double f[4], double
   int i, n1, p, n2, q, nout = 0;
   for (i = 0; i < 4; ++i) {
     T[i].a = a[i];
-    T[i].b = b[i];
+    T[i].D = b[i] - a[i];
     T[i].f = f[i];
     memset(T[i].l, 0, sizeof(T[i].l));
     T[i].l[i] = 1.0;
@@ -292,7 +294,7 @@ int oracle_carve(const double a[4], const double b[4], const double f[4], double
     for (q = 0; q < n2; ++q) {
       vol[nout] = vfrac(P2[q]);
       for (i = 0; i < 4; ++i) {
-        double d = P2[q][i].b - P2[q][i].a;
+        double d = P2[q][i].D;
         dv[4 * nout + i] = d > 0.0 ? d : 0.0;
         fv[4 * nout + i] = P2[q][i].f;
       }

@@ -1,0 +1,454 @@
+// chi0_abi.cu -- the C-ABI of include/chi0.h: plan objects, validation, uploads and the
+// per-q launch sequence overlap -> weights -> (Gamma DOS) -> reduction on one stream.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/chi0.h"
+#include "chi0_internal.h"
+
+using namespace chi0int;
+
+struct chi0_plan {
+  Grid g;
+  Tet tet;
+  chi0_opts_t opts;
+  chi0_band_window_t win;
+  cudaStream_t stream;
+  int dtype;
+  double *E_d = nullptr;
+  void *C_d = nullptr;
+  bool own_E = false, own_C = false;
+  int4 *tet_d = nullptr;
+  double *vol_d = nullptr;
+  void *W2_d = nullptr;
+  double *partR = nullptr, *partI = nullptr, *dos_d = nullptr;
+  double *out_d = nullptr;
+  size_t out_cap = 0;
+  double *omega_d = nullptr;
+  size_t omega_cap = 0;
+  double *Eq_stage = nullptr;
+  void *Cq_stage = nullptr;
+  unsigned long long *counters_d = nullptr;
+  short *occ_d = nullptr, *emp_d = nullptr, *occq_d = nullptr, *empq_d = nullptr;
+  float *E32_d = nullptr, *Eq32_d = nullptr;  // energies - eF in FP32 (mixed precision)
+  int *next_d = nullptr;                      // batch counter of the persistent kernels
+  int static_grid = 0;
+  size_t part_cap = 0;
+  chi0_stats_t stats;
+  char err[512];
+};
+
+static char g_plan_err[512] = "";
+
+static int fail(chi0_plan_t *p, int code, const char *fmt, ...) {
+  char *dst = p ? p->err : g_plan_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(p, call)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail((p), e_ == cudaErrorMemoryAllocation ? CHI0_ENOMEM : CHI0_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+  } while (0)
+
+static size_t cplx_size(int dtype) { return dtype == CHI0_C64 ? 8 : 16; }
+
+extern "C" void chi0_opts_default(chi0_opts_t *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = CHI0_PREC_FP64;
+  o->overlap = CHI0_OVL_FP32;
+  o->cma = 0;
+  o->sign = CHI0_SIGN_POSITIVE;
+  o->tau = 9.765625e-4; /* 2^-10 */
+  o->inputs_on_device = 0;
+  o->outputs_on_device = 0;
+  o->stream = nullptr;
+  o->profile = 0;
+  o->wait_budget = 0;
+}
+
+extern "C" int chi0_version(void) { return 100; }
+
+extern "C" const char *chi0_last_error(const chi0_plan_t *p) { return p ? p->err : g_plan_err; }
+
+extern "C" int chi0_plan_stats(const chi0_plan_t *p, chi0_stats_t *s) {
+  if (!p || !s) return CHI0_EINVAL;
+  *s = p->stats;
+  return CHI0_OK;
+}
+
+static void release(chi0_plan_t *p) {
+  if (!p) return;
+  if (p->own_E) cudaFree(p->E_d);
+  if (p->own_C) cudaFree(p->C_d);
+  cudaFree(p->tet_d);
+  cudaFree(p->vol_d);
+  cudaFree(p->W2_d);
+  cudaFree(p->partR);
+  cudaFree(p->partI);
+  cudaFree(p->dos_d);
+  cudaFree(p->out_d);
+  cudaFree(p->omega_d);
+  cudaFree(p->Eq_stage);
+  cudaFree(p->Cq_stage);
+  cudaFree(p->counters_d);
+  cudaFree(p->occ_d);
+  cudaFree(p->emp_d);
+  cudaFree(p->empq_d);
+  cudaFree(p->occq_d);
+  cudaFree(p->E32_d);
+  cudaFree(p->Eq32_d);
+  cudaFree(p->next_d);
+}
+
+extern "C" void chi0_destroy(chi0_plan_t *p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  else cudaDeviceSynchronize();
+  release(p);
+  delete p;
+}
+
+static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t *tt, chi0_band_window_t win,
+                      const chi0_opts_t *o) {
+  if (!kg) return fail(p, CHI0_EINVAL, "kgrid is NULL");
+  if (o) p->opts = *o;
+  else chi0_opts_default(&p->opts);
+  const chi0_opts_t &op = p->opts;
+  if (op.precision != CHI0_PREC_FP64 && op.precision != CHI0_PREC_MIXED)
+    return fail(p, CHI0_EINVAL, "precision %d unknown", op.precision);
+  if (op.overlap != CHI0_OVL_FP32 && op.overlap != CHI0_OVL_BF16X3)
+    return fail(p, CHI0_EINVAL, "overlap mode %d unknown", op.overlap);
+  if (op.overlap == CHI0_OVL_BF16X3)
+    return fail(p, CHI0_ENOTSUP, "tensor-core overlap mode not available in this build");
+  if (!(op.tau >= 0.0 && op.tau < 1.0)) return fail(p, CHI0_EINVAL, "tau must lie in [0, 1)");
+  for (int d = 0; d < 3; ++d)
+    if (kg->n[d] < 1 || kg->n[d] > (1 << 12)) return fail(p, CHI0_EINVAL, "n[%d] = %d out of range", d, kg->n[d]);
+  if (kg->nbands < 1 || kg->nbands > 4096) return fail(p, CHI0_EINVAL, "nbands = %d out of range", kg->nbands);
+  if (!op.cma && (kg->norb < 1 || kg->norb > 65536)) return fail(p, CHI0_EINVAL, "norb = %d out of range", kg->norb);
+  if (!kg->energies) return fail(p, CHI0_EINVAL, "energies is NULL");
+  if (!op.cma && !kg->evecs) return fail(p, CHI0_EINVAL, "evecs is NULL without CMA");
+  if (!op.cma && kg->evec_dtype != CHI0_C64 && kg->evec_dtype != CHI0_C128)
+    return fail(p, CHI0_EINVAL, "evec_dtype %d unknown", kg->evec_dtype);
+  if (win.lo < 0 || win.hi > kg->nbands || win.lo >= win.hi)
+    return fail(p, CHI0_EINVAL, "band window [%d, %d) outside [0, %d)", win.lo, win.hi, kg->nbands);
+  if (!(kg->e_fermi == kg->e_fermi)) return fail(p, CHI0_EINVAL, "e_fermi is NaN");
+
+  Grid &g = p->g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = kg->n[d];
+    g.N[d] = kg->periodic ? kg->n[d] : kg->n[d] + 1;
+  }
+  g.periodic = kg->periodic ? 1 : 0;
+  g.nb = kg->nbands;
+  g.norb = op.cma ? 0 : kg->norb;
+  g.nc = (long long)g.N[0] * g.N[1] * g.N[2];
+  g.ef = kg->e_fermi;
+  p->win = win;
+  p->dtype = op.cma ? CHI0_C128 : kg->evec_dtype;
+  p->stream = (cudaStream_t)op.stream;
+
+  // tetrahedra
+  if (tt && tt->corners) {
+    if (tt->ntet < 1 || !tt->volume) return fail(p, CHI0_EINVAL, "custom tetrahedra need ntet >= 1 and volumes");
+    for (long long t = 0; t < tt->ntet; ++t)
+      for (int i = 0; i < 4; ++i) {
+        const long long c = tt->corners[4 * t + i];
+        if (c < 0 || c >= g.nc) return fail(p, CHI0_EINVAL, "tetrahedron %lld corner %lld outside [0, %lld)", t, c, g.nc);
+      }
+    g.ntet = tt->ntet;
+    CK(p, cudaMalloc(&p->tet_d, sizeof(int4) * g.ntet));
+    CK(p, cudaMalloc(&p->vol_d, sizeof(double) * g.ntet));
+    CK(p, cudaMemcpyAsync(p->tet_d, tt->corners, sizeof(int4) * g.ntet, cudaMemcpyHostToDevice, p->stream));
+    CK(p, cudaMemcpyAsync(p->vol_d, tt->volume, sizeof(double) * g.ntet, cudaMemcpyHostToDevice, p->stream));
+  } else {
+    g.ntet = 6LL * g.n[0] * g.n[1] * g.n[2];
+  }
+  p->tet.corners = p->tet_d;
+  p->tet.vol = p->vol_d;
+  p->tet.vol_builtin = 1.0 / (6.0 * g.n[0] * g.n[1] * g.n[2]);
+
+  // eigen-data
+  const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;
+  const size_t cb = op.cma ? 0 : cplx_size(p->dtype) * (size_t)g.nc * g.norb * g.nb;
+  if (op.inputs_on_device) {
+    p->E_d = (double *)kg->energies;
+    p->C_d = (void *)kg->evecs;
+  } else {
+    for (long long c = 0; c < g.nc; ++c)
+      for (int b = 1; b < g.nb; ++b)
+        if (kg->energies[c * g.nb + b] < kg->energies[c * g.nb + b - 1])
+          return fail(p, CHI0_EINVAL, "energies not ascending at corner %lld band %d", c, b);
+    CK(p, cudaMalloc(&p->E_d, eb));
+    p->own_E = true;
+    CK(p, cudaMemcpyAsync(p->E_d, kg->energies, eb, cudaMemcpyHostToDevice, p->stream));
+    if (!op.cma) {
+      CK(p, cudaMalloc(&p->C_d, cb));
+      p->own_C = true;
+      CK(p, cudaMemcpyAsync(p->C_d, kg->evecs, cb, cudaMemcpyHostToDevice, p->stream));
+    }
+  }
+  // scratch: |M|^2 at the plan's window, block partials, counters
+  const int w = win.hi - win.lo;
+  if (!op.cma) {
+    const size_t es = op.precision == CHI0_PREC_FP64 ? sizeof(double) : sizeof(float);
+    CK(p, cudaMalloc(&p->W2_d, es * (size_t)g.nc * w * w));
+  }
+  const size_t np = (size_t)dynamic_blocks(dynamic_max_nw()) * dynamic_max_nw();
+  size_t ns = (size_t)static_batches(g.ntet);
+  if (ns < (size_t)static_blocks()) ns = (size_t)static_blocks();
+  p->part_cap = np > ns ? np : ns;
+  CK(p, cudaMalloc(&p->partR, sizeof(double) * p->part_cap));
+  CK(p, cudaMalloc(&p->partI, sizeof(double) * np));
+  CK(p, cudaMalloc(&p->dos_d, sizeof(double) * static_blocks()));
+  CK(p, cudaMalloc(&p->counters_d, sizeof(unsigned long long) * 4));
+  if (g.nc >= (1LL << 31)) return fail(p, CHI0_EINVAL, "more than 2^31 corners");
+  CK(p, cudaMalloc(&p->occ_d, sizeof(short) * g.nc));
+  CK(p, cudaMalloc(&p->emp_d, sizeof(short) * g.nc));
+  CK(p, cudaMalloc(&p->empq_d, sizeof(short) * g.nc));
+  CK(p, cudaMalloc(&p->occq_d, sizeof(short) * g.nc));
+  CK(p, cudaMalloc(&p->next_d, sizeof(int)));
+  if (op.precision == CHI0_PREC_MIXED) {
+    CK(p, cudaMalloc(&p->E32_d, sizeof(float) * (size_t)g.nc * g.nb));
+    CK(p, cudaMalloc(&p->Eq32_d, sizeof(float) * (size_t)g.nc * g.nb));
+  }
+  CK(p, launch_bands(p->E_d, g.nc, g.nb, g.ef, p->occ_d, p->emp_d, p->E32_d, p->stream));
+  p->static_grid = static_persistent_blocks(op.precision == CHI0_PREC_FP64);
+  CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, p->stream));
+  CK(p, cudaStreamSynchronize(p->stream));
+  memset(&p->stats, 0, sizeof(p->stats));
+  return CHI0_OK;
+}
+
+extern "C" int chi0_plan(const chi0_kgrid_t *kg, const chi0_tetra_t *tt, chi0_band_window_t win,
+                         const chi0_opts_t *o, chi0_plan_t **out) {
+  if (!out) return fail(nullptr, CHI0_EINVAL, "out is NULL");
+  *out = nullptr;
+  chi0_plan_t *p = new (std::nothrow) chi0_plan_t();
+  if (!p) return fail(nullptr, CHI0_ENOMEM, "host allocation failed");
+  p->err[0] = 0;
+  int rc = build_plan(p, kg, tt, win, o);
+  if (rc != CHI0_OK) {
+    snprintf(g_plan_err, sizeof(g_plan_err), "%s", p->err);
+    release(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return CHI0_OK;
+}
+
+// ------------------------------------------------------------------ per-call helpers
+namespace {
+
+struct Timer {
+  chi0_plan_t *p;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  int start(int k) {
+    if (!p->opts.profile) return 0;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1;
+    ev.push_back(a);
+    ev.push_back(b);
+    kind.push_back(k);
+    return cudaEventRecord(a, p->stream) == cudaSuccess ? 0 : -1;
+  }
+  int stop() {
+    if (!p->opts.profile) return 0;
+    return cudaEventRecord(ev.back(), p->stream) == cudaSuccess ? 0 : -1;
+  }
+  void collect() {
+    for (size_t i = 0; i < kind.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+        p->stats.time_ms[kind[i]] += ms;
+        p->stats.launches[kind[i]] += 1;
+      }
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    kind.clear();
+  }
+};
+
+int ensure(chi0_plan_t *p, void **buf, size_t *cap, size_t bytes) {
+  if (*cap >= bytes) return CHI0_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  CK(p, cudaMalloc(buf, bytes));
+  *cap = bytes;
+  return CHI0_OK;
+}
+
+// Resolves one q descriptor into device pointers (staging host explicit data).
+int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q) {
+  const Grid &g = p->g;
+  q.lo = qd.win.lo < 0 ? p->win.lo : qd.win.lo;
+  q.hi = qd.win.lo < 0 ? p->win.hi : qd.win.hi;
+  if (q.lo < p->win.lo || q.hi > p->win.hi || q.lo >= q.hi)
+    return fail(p, CHI0_EINVAL, "q window [%d, %d) outside the plan window [%d, %d)", q.lo, q.hi, p->win.lo, p->win.hi);
+  q.gamma = qd.gamma ? 1 : 0;
+  q.Eq = nullptr;
+  q.Cq = nullptr;
+  if (qd.e_kq) {
+    if (!p->opts.cma && !qd.c_kq) return fail(p, CHI0_EINVAL, "explicit e_kq needs c_kq without CMA");
+    for (int d = 0; d < 3; ++d) q.shift[d] = 0;
+    if (p->opts.inputs_on_device) {
+      q.Eq = qd.e_kq;
+      q.Cq = qd.c_kq;
+    } else {
+      const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;
+      if (!p->Eq_stage) CK(p, cudaMalloc(&p->Eq_stage, eb));
+      CK(p, cudaMemcpyAsync(p->Eq_stage, qd.e_kq, eb, cudaMemcpyHostToDevice, p->stream));
+      q.Eq = p->Eq_stage;
+      if (!p->opts.cma) {
+        const size_t cb = cplx_size(p->dtype) * (size_t)g.nc * g.norb * g.nb;
+        if (!p->Cq_stage) CK(p, cudaMalloc(&p->Cq_stage, cb));
+        CK(p, cudaMemcpyAsync(p->Cq_stage, qd.c_kq, cb, cudaMemcpyHostToDevice, p->stream));
+        q.Cq = p->Cq_stage;
+      }
+    }
+  } else {
+    if (!g.periodic) return fail(p, CHI0_EINVAL, "on-grid q shift needs a periodic grid");
+    bool zero = true;
+    for (int d = 0; d < 3; ++d) {
+      int s = qd.shift[d] % g.N[d];
+      if (s < 0) s += g.N[d];
+      q.shift[d] = s;
+      zero = zero && s == 0;
+    }
+    if (zero) q.gamma = 1;
+  }
+  return CHI0_OK;
+}
+
+}  // namespace
+
+static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, int nw, double *re,
+               double *im) {
+  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
+  if (nq <= 0 || !qs) return fail(p, CHI0_EINVAL, "nq = %d or q NULL", nq);
+  const bool dyn = omega != nullptr;
+  if (dyn && (nw <= 0 || !re || !im)) return fail(p, CHI0_EINVAL, "dynamic call needs nw > 0, re and im");
+  if (!dyn && !re) return fail(p, CHI0_EINVAL, "chi is NULL");
+  const chi0_opts_t &op = p->opts;
+  const int fp64 = op.precision == CHI0_PREC_FP64;
+  const double scale = op.sign == CHI0_SIGN_PAPER ? -2.0 : 2.0;
+  cudaStream_t s = p->stream;
+  Timer tm{p, {}, {}};
+  const int nwo = dyn ? nw : 1;
+  const size_t outn = (size_t)nq * nwo * (dyn ? 2 : 1);
+  double *outR = nullptr, *outI = nullptr;
+  const double *om_d = nullptr;
+  if (op.outputs_on_device) {
+    outR = re;
+    outI = dyn ? im : nullptr;
+  } else {
+    int rc = ensure(p, (void **)&p->out_d, &p->out_cap, sizeof(double) * outn);
+    if (rc) return rc;
+    outR = p->out_d;
+    outI = dyn ? p->out_d + (size_t)nq * nw : nullptr;
+  }
+  if (dyn) {
+    if (op.inputs_on_device) {
+      om_d = omega;
+    } else {
+      int rc = ensure(p, (void **)&p->omega_d, &p->omega_cap, sizeof(double) * nw);
+      if (rc) return rc;
+      CK(p, cudaMemcpyAsync(p->omega_d, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
+      om_d = p->omega_d;
+    }
+  }
+  CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, s));
+  for (int iq = 0; iq < nq; ++iq) {
+    Q q;
+    int rc = prepare_q(p, qs[iq], q);
+    if (rc) return rc;
+    if (!op.cma) {
+      tm.start(CHI0_K_OVERLAP);
+      CK(p, launch_overlap(p->g, p->E_d, p->C_d, p->dtype, q, p->W2_d, fp64, s));
+      tm.stop();
+    }
+    const int ndos = static_blocks();
+    if (q.gamma) {
+      tm.start(CHI0_K_DOS);
+      CK(p, launch_dos(p->g, p->tet, p->E_d, q.lo, q.hi, p->dos_d, ndos, s));
+      tm.stop();
+    }
+    if (!dyn) {
+      const int nb = (int)static_batches(p->g.ntet);
+      const short *empq = p->emp_d;
+      const void *Ek = fp64 ? (const void *)p->E_d : (const void *)p->E32_d;
+      const void *Ekq = Ek;
+      if (q.Eq) {
+        tm.start(CHI0_K_BANDS);
+        CK(p, launch_bands(q.Eq, p->g.nc, p->g.nb, p->g.ef, p->occq_d, p->empq_d, fp64 ? nullptr : p->Eq32_d, s));
+        tm.stop();
+        empq = p->empq_d;
+        Ekq = fp64 ? (const void *)q.Eq : (const void *)p->Eq32_d;
+      }
+      tm.start(CHI0_K_STATIC);
+      CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
+                          p->partR, p->next_d, p->static_grid, p->counters_d, s));
+      tm.stop();
+      tm.start(CHI0_K_REDUCE);
+      CK(p, launch_reduce(p->partR, nb, 1, scale, q.gamma ? p->dos_d : nullptr, ndos, nullptr, outR + iq, s));
+      tm.stop();
+    } else {
+      const int maxw = dynamic_max_nw();
+      for (int w0 = 0; w0 < nw; w0 += maxw) {
+        const int nwc = nw - w0 < maxw ? nw - w0 : maxw;
+        const int nb = dynamic_blocks(nwc);
+        tm.start(CHI0_K_DYNAMIC);
+        CK(p, launch_dynamic(p->g, p->tet, p->E_d, q, p->W2_d, op.cma, fp64, (float)op.tau, om_d + w0, nwc,
+                             p->partR, p->partI, nb, p->counters_d, s));
+        tm.stop();
+        tm.start(CHI0_K_REDUCE);
+        CK(p, launch_reduce(p->partR, nb, nwc, scale, q.gamma ? p->dos_d : nullptr, ndos, om_d + w0,
+                            outR + (size_t)iq * nw + w0, s));
+        CK(p, launch_reduce(p->partI, nb, nwc, scale, nullptr, 0, nullptr, outI + (size_t)iq * nw + w0, s));
+        tm.stop();
+      }
+    }
+  }
+  if (!op.outputs_on_device) {
+    CK(p, cudaMemcpyAsync(re, outR, sizeof(double) * nq * nwo, cudaMemcpyDeviceToHost, s));
+    if (dyn) CK(p, cudaMemcpyAsync(im, outI, sizeof(double) * nq * nw, cudaMemcpyDeviceToHost, s));
+  }
+  if (op.profile || !op.outputs_on_device) CK(p, cudaStreamSynchronize(s));
+  CK(p, cudaGetLastError());
+  if (op.profile) {
+    unsigned long long cnt[2] = {0, 0};
+    CK(p, cudaMemcpy(cnt, p->counters_d, sizeof(cnt), cudaMemcpyDeviceToHost));
+    p->stats.pieces += (long long)cnt[0];
+    p->stats.fp64_evals += (long long)cnt[1];
+  }
+  tm.collect();
+  p->stats.calls += 1;
+  return CHI0_OK;
+}
+
+extern "C" int chi0_static(chi0_plan_t *p, const chi0_q_t *q, int nq, double *chi) {
+  return run(p, q, nq, nullptr, 0, chi, nullptr);
+}
+
+extern "C" int chi0_dynamic(chi0_plan_t *p, const chi0_q_t *q, int nq, const double *omega, int nw, double *re,
+                            double *im) {
+  if (!omega) return fail(p, CHI0_EINVAL, "omega is NULL");
+  return run(p, q, nq, omega, nw, re, im);
+}

@@ -1,0 +1,625 @@
+// chi0_kernels.cu -- sm_103a kernels of the doubly carved tetrahedron method.
+//
+//  k_overlap  (Eq. 1 matrix elements, tight-binding form of the Sec. III footnote):
+//             W2[c][m][n] = |sum_o conj(C_k[o][m]) C_{k+q}[o][n]|^2 at every k corner.
+//  k_static   one warp per tetrahedron: lanes find the occupied bands m (some corner with
+//             e^m_k < eF) and the empty bands n (some corner with e^n_{k+q} > eF), then
+//             walk the (m, n) rectangle; per pair the two carvings of Sec. II and the
+//             closed-form 2/D integral (Eq. 1 at w = 0).  Per-block FP64 partial sums.
+//  k_dynamic  one warp per tetrahedron, pairs walked by the whole warp, the lanes own the
+//             frequencies: PV 1/(D-w) + 1/(D+w) (Eq. 1) and pi delta(w - D) (Eq. 2).
+//  k_dos      Gamma: the intraband q -> 0 limit, tetrahedron DOS at eF (Sec. III).
+//  k_reduce   deterministic fixed-order sum of the block partials.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "chi0_internal.h"
+#include "chi0_math.cuh"
+
+using namespace chi0dev;
+
+namespace chi0int {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kSMs = 152;
+constexpr int kStaticBlocks = kSMs * 8;
+constexpr int kDynBlocks = kSMs * 4;
+constexpr int kNWPass = 256;  // frequencies per dynamic pass (shared-memory accumulators)
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ long long wrap(int i, int N) { return i >= N ? i - N : i; }
+
+__device__ __forceinline__ long long cid(const Grid &g, int i0, int i1, int i2) {
+  if (g.periodic) {
+    i0 = (int)wrap(i0, g.N[0]);
+    i1 = (int)wrap(i1, g.N[1]);
+    i2 = (int)wrap(i2, g.N[2]);
+  }
+  return ((long long)i0 * g.N[1] + i1) * g.N[2] + i2;
+}
+
+__device__ __forceinline__ long long shift_corner(const Grid &g, long long c, const int s[3]) {
+  const int i2 = (int)(c % g.N[2]);
+  const int i1 = (int)((c / g.N[2]) % g.N[1]);
+  const int i0 = (int)(c / ((long long)g.N[2] * g.N[1]));
+  return cid(g, i0 + s[0], i1 + s[1], i2 + s[2]);
+}
+
+// Corners of tetrahedron t at k and at k+q, and its fractional volume.  Builtin mesh:
+// tetrahedron 6*cube + p = {000, e_a, e_a + e_b, 111} for the p-th axis order (a, b, .)
+// of the lexicographically ordered permutations of (0, 1, 2).
+__device__ __forceinline__ void tet_corners(const Grid &g, const Tet &tet, const Q &q, long long t,
+                                            long long c[4], long long cq[4], double &vol) {
+  if (tet.corners) {
+    const int4 v = tet.corners[t];
+    c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+    vol = tet.vol[t];
+    for (int i = 0; i < 4; ++i) cq[i] = q.Eq ? c[i] : shift_corner(g, c[i], q.shift);
+    return;
+  }
+  const long long cube = t / 6;
+  const int p = (int)(t - cube * 6);
+  const int i2 = (int)(cube % g.n[2]);
+  const int i1 = (int)((cube / g.n[2]) % g.n[1]);
+  const int i0 = (int)(cube / ((long long)g.n[2] * g.n[1]));
+  const int ax = p >> 1;                                // first axis: 0,0,1,1,2,2
+  const int bx = (p == 0) ? 1 : (p == 1) ? 2 : (p == 2) ? 0 : (p == 3) ? 2 : (p == 4) ? 0 : 1;
+  int o1[3] = {0, 0, 0}, o2[3] = {0, 0, 0};
+  o1[ax] = 1;
+  o2[ax] = 1;
+  o2[bx] = 1;
+  const int *s = q.shift;
+  const bool ex = q.Eq != nullptr;
+  c[0] = cid(g, i0, i1, i2);
+  c[1] = cid(g, i0 + o1[0], i1 + o1[1], i2 + o1[2]);
+  c[2] = cid(g, i0 + o2[0], i1 + o2[1], i2 + o2[2]);
+  c[3] = cid(g, i0 + 1, i1 + 1, i2 + 1);
+  if (ex) {
+    for (int i = 0; i < 4; ++i) cq[i] = c[i];
+  } else {
+    cq[0] = cid(g, i0 + s[0], i1 + s[1], i2 + s[2]);
+    cq[1] = cid(g, i0 + o1[0] + s[0], i1 + o1[1] + s[1], i2 + o1[2] + s[2]);
+    cq[2] = cid(g, i0 + o2[0] + s[0], i1 + o2[1] + s[1], i2 + o2[2] + s[2]);
+    cq[3] = cid(g, i0 + 1 + s[0], i1 + 1 + s[1], i2 + 1 + s[2]);
+  }
+  vol = tet.vol_builtin;
+}
+
+// Lanes over bands: the rectangle [lo, mhi) x [nlo, hi) holds every pair with an
+// occupied corner at k and an empty corner at k+q.
+__device__ __forceinline__ void band_extent(const Grid &g, const double *__restrict__ E,
+                                            const double *__restrict__ Eq, const long long c[4],
+                                            const long long cq[4], int lo, int hi, int lane, int &mhi,
+                                            int &nlo) {
+  mhi = lo;
+  nlo = hi;
+  for (int b0 = lo; b0 < hi; b0 += 32) {
+    const int band = b0 + lane;
+    bool occ = false, emp = false;
+    if (band < hi) {
+      double amin = E[c[0] * g.nb + band], bmax = Eq[cq[0] * g.nb + band];
+#pragma unroll
+      for (int i = 1; i < 4; ++i) {
+        amin = fmin(amin, E[c[i] * g.nb + band]);
+        bmax = fmax(bmax, Eq[cq[i] * g.nb + band]);
+      }
+      occ = amin - g.ef < 0.0;
+      emp = bmax - g.ef > 0.0;
+    }
+    const unsigned mo = __ballot_sync(kFull, occ), me = __ballot_sync(kFull, emp);
+    if (mo) mhi = b0 + 32 - __clz(mo);
+    if (me && nlo == hi) nlo = b0 + __ffs(me) - 1;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool load_pair(const Grid &g, const double *__restrict__ E,
+                                          const double *__restrict__ Eq, const void *__restrict__ W2v,
+                                          int cma, const long long c[4], const long long cq[4], int m,
+                                          int n, int lo, int w, T a[4], T b[4], T f[4]) {
+  T amin, bmax;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = (T)(E[c[i] * g.nb + m] - g.ef);
+    b[i] = (T)(Eq[cq[i] * g.nb + n] - g.ef);
+  }
+  amin = fmin(fmin(a[0], a[1]), fmin(a[2], a[3]));
+  bmax = fmax(fmax(b[0], b[1]), fmax(b[2], b[3]));
+  if (!(amin < T(0)) || !(bmax > T(0))) return false;
+  const T *W2 = (const T *)W2v;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) f[i] = cma ? T(1) : W2[(c[i] * w + (m - lo)) * w + (n - lo)];
+  return true;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void block_sum_store(double v, double *out) {
+  __shared__ double red[kWarps];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (lane == 0) red[wib] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kWarps; ++i) s += red[i];
+    *out = s;
+  }
+}
+
+// ---------------------------------------------------------------- overlap
+template <typename CT, typename T>
+__global__ void __launch_bounds__(kThreads) k_overlap(Grid g, const CT *__restrict__ C,
+                                                       const CT *__restrict__ Cqx, Q q, T *__restrict__ W2) {
+  const int w = q.hi - q.lo;
+  const long long total = g.nc * (long long)w * w;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long c = idx / ((long long)w * w);
+    const int r = (int)(idx - c * w * w);
+    const int mm = r / w, nn = r - (r / w) * w;
+    const long long ck = Cqx ? c : shift_corner(g, c, q.shift);
+    const CT *Cb = Cqx ? Cqx : C;
+    T re = T(0), im = T(0);
+    for (int o = 0; o < g.norb; ++o) {
+      const CT x = C[(c * g.norb + o) * g.nb + q.lo + mm];
+      const CT y = Cb[(ck * g.norb + o) * g.nb + q.lo + nn];
+      const T xr = (T)x.x, xi = (T)x.y, yr = (T)y.x, yi = (T)y.y;
+      re += xr * yr + xi * yi;  // conj(x) * y
+      im += xr * yi - xi * yr;
+    }
+    W2[idx] = re * re + im * im;
+  }
+}
+
+// ---------------------------------------------------------------- band bounds per corner
+// occ[c] = 1 + highest band with e < eF at corner c (0 if none): bands m >= occ[c] are empty
+// there.  emp[c] = lowest band with e > eF (nb if none): bands n < emp[c] are not empty.
+// E32 (optional) receives the energies relative to eF in FP32 for the mixed-precision path.
+__global__ void __launch_bounds__(kThreads) k_bands(const double *__restrict__ E, long long nc, int nb,
+                                                    double ef, short *__restrict__ occ,
+                                                    short *__restrict__ emp, float *__restrict__ E32) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += (long long)gridDim.x * blockDim.x) {
+    int o = 0, e = nb;
+    for (int b = 0; b < nb; ++b) {
+      const double x = E[c * nb + b] - ef;
+      if (x < 0.0) o = b + 1;
+      if (x > 0.0 && e == nb) e = b;
+      if (E32) E32[c * nb + b] = (float)x;
+    }
+    occ[c] = (short)o;
+    emp[c] = (short)e;
+  }
+}
+
+// ---------------------------------------------------------------- static weights
+// Persistent warps take batches of 32 tetrahedra from an atomic counter.  A batch's
+// (m, n) rectangles are flattened into one item list shared by the lanes.  Final
+// tetrahedra whose knots fit the series branch are evaluated where they are produced;
+// the others (knots spanning a wide range, e.g. D = 0 vertices) are queued in shared
+// memory and evaluated 32 at a time by the whole warp.  Every batch writes its own
+// partial sum, so the result does not depend on which warp took which batch.
+template <typename T> struct QCap {
+  static constexpr int value = sizeof(T) == 8 ? 32 : 64;  // queue entries per warp
+};
+
+template <typename T> struct Piece {
+  T d[4], f[4], w;
+};
+
+// compensated (Neumaier) accumulator in the kernel's precision
+template <typename T> struct Acc {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    const T t = s + x;
+    if (tabs(s) >= tabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <bool FP64>
+__device__ __forceinline__ typename std::conditional<FP64, double, float>::type table_eval(
+    const Piece<typename std::conditional<FP64, double, float>::type> &pc, float tau, int &nfp64) {
+  if constexpr (FP64) {
+    return pc.w * inv_sum_table(pc.d, pc.f);
+  } else {
+    const float s = fmaxf(fabsf(pc.d[0]), fabsf(pc.d[3]));
+    float g = s;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float gi = pc.d[i + 1] - pc.d[i];
+      if (gi > 0.0f) g = fminf(g, gi);  // exact ties (two D = 0 vertices) are exact in FP32
+    }
+    if (g >= tau * s) return pc.w * inv_sum_table(pc.d, pc.f);
+    ++nfp64;  // near-degenerate knots: the table in FP64
+    double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
+    return pc.w * (float)inv_sum_table(xd, fd);
+  }
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_static(Grid g, Tet tet, const void *__restrict__ Ek,
+                                                      const void *__restrict__ Ekq, Q q,
+                                                      const void *__restrict__ W2, int cma, float tau,
+                                                      const short *__restrict__ occ,
+                                                      const short *__restrict__ empq,
+                                                      double *__restrict__ partial, int *__restrict__ next,
+                                                      unsigned long long *__restrict__ counters) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  constexpr int kQCap = QCap<T>::value;
+  __shared__ int s_c[kWarps][32][4], s_cq[kWarps][32][4];
+  __shared__ T s_vol[kWarps][32];
+  __shared__ int s_nlo[kWarps][32], s_nn[kWarps][32], s_pre[kWarps][33];
+  __shared__ Piece<T> s_q[kWarps][kQCap];
+  __shared__ int s_qn[kWarps];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = q.hi - q.lo;
+  const long long nbatch = (g.ntet + 31) / 32;
+  int nfp64 = 0, npieces = 0;
+  if (lane == 0) s_qn[wib] = 0;
+  __syncwarp();
+  for (;;) {
+    int batch = 0;
+    if (lane == 0) batch = atomicAdd(next, 1);
+    batch = __shfl_sync(kFull, batch, 0);
+    if (batch >= nbatch) break;
+    Acc<T> acc;
+    auto drain = [&](bool all) {
+      for (;;) {
+        const int qn = s_qn[wib];
+        if (qn == 0 || (!all && qn < 32)) break;
+        const int take = qn < 32 ? qn : 32;
+        if (lane < take) acc.add(table_eval<FP64>(s_q[wib][qn - take + lane], tau, nfp64));
+        __syncwarp();
+        if (lane == 0) s_qn[wib] = qn - take;
+        __syncwarp();
+      }
+    };
+    // one tetrahedron per lane: corners, volume, band rectangle
+    const long long t = (long long)batch * 32 + lane;
+    int cnt = 0;
+    if (t < g.ntet) {
+      long long c[4], cq[4];
+      double vol;
+      tet_corners(g, tet, q, t, c, cq, vol);
+      int mhi = 0, nlo = g.nb;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        s_c[wib][lane][i] = (int)c[i];
+        s_cq[wib][lane][i] = (int)cq[i];
+        mhi = max(mhi, (int)occ[c[i]]);
+        nlo = min(nlo, (int)empq[cq[i]]);
+      }
+      mhi = min(mhi, q.hi);
+      nlo = max(nlo, q.lo);
+      const int nm = mhi - q.lo, nn = q.hi - nlo;
+      cnt = (nm > 0 && nn > 0) ? nm * nn : 0;
+      s_vol[wib][lane] = (T)(2.0 * vol);
+      s_nlo[wib][lane] = nlo;
+      s_nn[wib][lane] = nn;
+    }
+    int pre = cnt;  // inclusive prefix sum over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, pre, o);
+      if (lane >= o) pre += v;
+    }
+    s_pre[wib][lane + 1] = pre;
+    if (lane == 0) s_pre[wib][0] = 0;
+    const int total = __shfl_sync(kFull, pre, 31);
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+      const int it = base + lane;
+      if (it < total) {
+        int lo_ = 0, hi_ = 32;  // owner: largest l with s_pre[l] <= it
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+          const int mid = (lo_ + hi_) >> 1;
+          if (s_pre[wib][mid] <= it) lo_ = mid;
+          else hi_ = mid;
+        }
+        const int l = lo_;
+        const int loc = it - s_pre[wib][l];
+        const int nn = s_nn[wib][l];
+        const int m = q.lo + loc / nn, n = s_nlo[wib][l] + loc % nn;
+        if (!(q.gamma && m == n)) {  // intraband at Gamma: replaced by the DOS limit
+          T a[4], b[4], f[4];
+          T amin = T(1e30), bmax = T(-1e30);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
+            if constexpr (FP64) {
+              a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
+              b[i] = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
+            } else {
+              a[i] = ((const float *)Ek)[(long long)ck * g.nb + m];
+              b[i] = ((const float *)Ekq)[(long long)cq * g.nb + n];
+            }
+            amin = a[i] < amin ? a[i] : amin;
+            bmax = b[i] > bmax ? b[i] : bmax;
+          }
+          if (amin < T(0) && bmax > T(0)) {
+            const T *W2t = (const T *)W2;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
+            const T vol2 = s_vol[wib][l];
+            carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) {
+              sort4(d, ff);
+              ++npieces;
+              if (series_ok(d, T(Num<T>::kappa))) {
+                acc.add(vol2 * r * series_sum(d, ff));
+              } else {
+                const int slot = atomicAdd(&s_qn[wib], 1);
+                Piece<T> pc;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  pc.d[i] = d[i];
+                  pc.f[i] = ff[i];
+                }
+                pc.w = vol2 * r;
+                if (slot < kQCap) s_q[wib][slot] = pc;
+                else acc.add(table_eval<FP64>(pc, tau, nfp64));  // queue full: evaluate in place
+              }
+            });
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0 && s_qn[wib] > kQCap) s_qn[wib] = kQCap;
+      __syncwarp();
+      drain(false);
+    }
+    drain(true);  // this batch's pieces stay in this batch's sum
+    const double v = warp_sum(acc.value());
+    if (lane == 0) partial[batch] = v;
+  }
+  if (counters) {
+    unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&counters[0], a);
+      atomicAdd(&counters[1], b);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- dynamic weights
+// Frequencies live in shared memory; lane l of a warp owns w_l, w_{l+32}, ... and adds
+// into its warp's own accumulator row (no atomics, fixed order).
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_dynamic(Grid g, Tet tet, const double *__restrict__ E, Q q,
+                                                       const void *__restrict__ W2, int cma, float tau,
+                                                       const double *__restrict__ omega, int nw,
+                                                       double *__restrict__ partialR,
+                                                       double *__restrict__ partialI,
+                                                       unsigned long long *__restrict__ counters) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  __shared__ double sR[kWarps][kNWPass], sI[kWarps][kNWPass];
+  __shared__ double sW[kNWPass];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long warp = (long long)blockIdx.x * kWarps + wib;
+  const long long nwarps = (long long)gridDim.x * kWarps;
+  const double *Eq = q.Eq ? q.Eq : E;
+  const int w = q.hi - q.lo;
+  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) sW[iw] = omega[iw];
+  for (int iw = lane; iw < kNWPass; iw += 32) {
+    sR[wib][iw] = 0.0;
+    sI[wib][iw] = 0.0;
+  }
+  __syncthreads();
+  int nfp64 = 0, npieces = 0;
+  for (long long t = warp; t < g.ntet; t += nwarps) {
+    long long c[4], cq[4];
+    double vol;
+    tet_corners(g, tet, q, t, c, cq, vol);
+    int mhi, nlo;
+    band_extent(g, E, Eq, c, cq, q.lo, q.hi, lane, mhi, nlo);
+    const int nm = mhi - q.lo, nn = q.hi - nlo;
+    const int npair = nm > 0 && nn > 0 ? nm * nn : 0;
+    for (int p = 0; p < npair; ++p) {  // warp-uniform
+      const int m = q.lo + p / nn, n = nlo + p % nn;
+      if (q.gamma && m == n) continue;
+      T a[4], b[4], f[4];
+      if (!load_pair<T>(g, E, Eq, W2, cma, c, cq, m, n, q.lo, w, a, b, f)) continue;
+      carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) {
+        sort4(d, ff);
+        ++npieces;
+        const double vr = vol * (double)r;
+#pragma unroll 1
+        for (int iw = lane; iw < nw; iw += 32) {
+          const double omd = sW[iw];
+          const T om = (T)fabs(omd);
+          T xm[4], xp[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            xm[i] = d[i] - om;
+            xp[i] = d[i] + om;
+          }
+          T re;
+          if constexpr (FP64) {
+            re = inv_sum(xm, ff) + inv_sum(xp, ff);
+          } else {
+            re = inv_sum_mixed(xm, ff, tau, &nfp64) + inv_sum_mixed(xp, ff, tau, &nfp64);
+          }
+          sR[wib][iw] += vr * (double)re;
+          if (om > T(0)) {
+            const T im = delta_sum(d, ff, om);
+            sI[wib][iw] += (omd < 0.0 ? -vr : vr) * 3.141592653589793 * (double)im;
+          }
+        }
+      });
+    }
+  }
+  if (counters) {
+    unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&counters[0], a / 32);  // every lane counted each piece
+      atomicAdd(&counters[1], b);
+    }
+  }
+  __syncthreads();
+  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
+    double r = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) {
+      r += sR[k][iw];
+      im += sI[k][iw];
+    }
+    partialR[(long long)blockIdx.x * nw + iw] = r;
+    partialI[(long long)blockIdx.x * nw + iw] = im;
+  }
+}
+
+// ---------------------------------------------------------------- Gamma DOS term
+__global__ void __launch_bounds__(kThreads) k_dos(Grid g, Tet tet, const double *__restrict__ E, int lo,
+                                                   int hi, double *__restrict__ partial) {
+  const int w = hi - lo;
+  const long long total = g.ntet * (long long)w;
+  Q q0{};
+  q0.Eq = E;  // corners at k only
+  double acc = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long t = idx / w;
+    const int band = lo + (int)(idx - t * w);
+    long long c[4], cq[4];
+    double vol;
+    tet_corners(g, tet, q0, t, c, cq, vol);
+    acc += vol * dos4(E[c[0] * g.nb + band] - g.ef, E[c[1] * g.nb + band] - g.ef,
+                      E[c[2] * g.nb + band] - g.ef, E[c[3] * g.nb + band] - g.ef);
+  }
+  block_sum_store(acc, &partial[blockIdx.x]);
+}
+
+// ---------------------------------------------------------------- reduction
+__global__ void __launch_bounds__(kThreads) k_reduce(const double *__restrict__ partial, int nblocks, int nw,
+                                                      double scale, const double *__restrict__ dos, int ndos,
+                                                      const double *__restrict__ omega,
+                                                      double *__restrict__ out) {
+  const int k = blockIdx.x;
+  double s = 0.0, sd = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(long long)b * nw + k];
+  const bool add_dos = dos && (omega == nullptr || omega[k] == 0.0);
+  if (add_dos)
+    for (int b = threadIdx.x; b < ndos; b += blockDim.x) sd += dos[b];
+  __shared__ double r1[kThreads], r2[kThreads];
+  r1[threadIdx.x] = s;
+  r2[threadIdx.x] = sd;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+      r2[threadIdx.x] += r2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] = scale * (r1[0] + r2[0]);
+}
+
+}  // namespace
+
+// ======================================================================= launchers
+int static_blocks() { return kStaticBlocks; }
+int dynamic_blocks(int) { return kDynBlocks; }
+int dynamic_max_nw() { return kNWPass; }
+
+cudaError_t launch_overlap(const Grid &g, const double *, const void *C, int dtype, const Q &q, void *W2,
+                           int fp64, cudaStream_t s) {
+  const int w = q.hi - q.lo;
+  const long long total = g.nc * (long long)w * w;
+  long long nb = (total + kThreads - 1) / kThreads;
+  const int blocks = (int)(nb < kSMs * 16 ? nb : kSMs * 16);
+  if (blocks <= 0) return cudaSuccess;
+  if (dtype == DT_C128) {
+    const double2 *Cx = (const double2 *)C, *Cq = (const double2 *)q.Cq;
+    if (fp64) k_overlap<double2, double><<<blocks, kThreads, 0, s>>>(g, Cx, Cq, q, (double *)W2);
+    else k_overlap<double2, float><<<blocks, kThreads, 0, s>>>(g, Cx, Cq, q, (float *)W2);
+  } else {
+    const float2 *Cx = (const float2 *)C, *Cq = (const float2 *)q.Cq;
+    if (fp64) k_overlap<float2, double><<<blocks, kThreads, 0, s>>>(g, Cx, Cq, q, (double *)W2);
+    else k_overlap<float2, float><<<blocks, kThreads, 0, s>>>(g, Cx, Cq, q, (float *)W2);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bands(const double *E, long long nc, int nb, double ef, short *occ, short *emp, float *E32,
+                         cudaStream_t s) {
+  long long nb_ = (nc + kThreads - 1) / kThreads;
+  const int blocks = (int)(nb_ < kSMs * 8 ? nb_ : kSMs * 8);
+  k_bands<<<blocks, kThreads, 0, s>>>(E, nc, nb, ef, occ, emp, E32);
+  return cudaGetLastError();
+}
+
+int static_persistent_blocks(int fp64) {
+  int nb = 0;
+  cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<true>, kThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<false>, kThreads, 0);
+  if (e != cudaSuccess || nb < 1) nb = 1;
+  int dev = 0, sms = kSMs;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return nb * sms;
+}
+
+long long static_batches(long long ntet) { return (ntet + 31) / 32; }
+
+cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
+                          const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
+                          double *partial, int *next, int nblocks, unsigned long long *counters,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (fp64)
+    k_static<true><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, partial, next,
+                                                 counters);
+  else
+    k_static<false><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, partial, next,
+                                                  counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const double *E, const Q &q, const void *W2,
+                           int cma, int fp64, float tau, const double *omega, int nw, double *partialR,
+                           double *partialI, int nblocks, unsigned long long *counters, cudaStream_t s) {
+  if (nw > kNWPass || nw <= 0) return cudaErrorInvalidValue;
+  if (fp64)
+    k_dynamic<true><<<nblocks, kThreads, 0, s>>>(g, tet, E, q, W2, cma, tau, omega, nw, partialR, partialI, counters);
+  else
+    k_dynamic<false><<<nblocks, kThreads, 0, s>>>(g, tet, E, q, W2, cma, tau, omega, nw, partialR, partialI, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,
+                       int nblocks, cudaStream_t s) {
+  k_dos<<<nblocks, kThreads, 0, s>>>(g, tet, E, lo, hi, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double *partial, int nblocks, int nw, double scale, const double *dos,
+                          int ndos, const double *omega, double *out, cudaStream_t s) {
+  k_reduce<<<nw, kThreads, 0, s>>>(partial, nblocks, nw, scale, dos, ndos, omega, out);
+  return cudaGetLastError();
+}
+
+}  // namespace chi0int

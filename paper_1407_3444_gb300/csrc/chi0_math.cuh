@@ -1,0 +1,446 @@
+// chi0_math.cuh -- device arithmetic of the doubly carved linear tetrahedron method.
+//
+// Sec. II of Heil et al. (arXiv:1407.3444): the integrand of Eqs. 1-2 is restricted to
+// the region where Th(eF - e^m_k) Th(e^n_{k+q} - eF) = 1 (Eq. 4) by cutting every
+// tetrahedron twice, first by a = e^m_k - eF < 0, then by b = e^n_{k+q} - eF > 0.  On
+// each final tetrahedron S (volume V, vertex values d_j = b_j - a_j >= 0 of
+// D = e^n_{k+q} - e^m_k and f_j of |M|^2) the integrals are exact for the linear
+// interpolants (Hermite-Genocchi):
+//   (1/V) int_S lambda_j / (D - x)   = g[d_1-x, .., d_4-x, d_j-x],  g(t) = t^3 ln|t|
+//   (1/V) int_S lambda_j delta(w - D) = M(w; d_1..d_4, d_j) / 4     (cubic B-spline density)
+// with g[...] the fourth divided difference (knot d_j repeated).  The paper does not print
+// its formulas; these are the closed forms for linear integrands on a simplex.
+//
+// Evaluation strategy (GPU-first; all branches exact up to rounding):
+//  * knots clustered away from 0 (spread <= RHO * |nearest|): one Taylor series about
+//    the mean for all four j at once (h_k complete homogeneous polynomials);
+//  * otherwise the divided-difference table of the sorted knots, each entry by the
+//    difference recursion or, where its own knots cluster, by its Taylor series;
+//  * mixed precision: the table in FP32 only when every gap between sorted knots is at
+//    least tau * max|knot|; below that (the near-degenerate, cancellation-prone case)
+//    the table is evaluated in FP64.
+#pragma once
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#endif
+#include <math.h>
+#include <stdint.h>
+
+namespace chi0dev {
+
+constexpr double kRho = 0.25;                     // Taylor branch threshold
+constexpr double kFloor = 9.313225746154785e-10;  // 2^-30: >= 3 exactly-zero knots
+
+template <typename T> struct Num;
+template <> struct Num<double> {
+  static __device__ __forceinline__ double lg(double x) { return log(x); }
+  static constexpr double tol = 1e-17;
+  static constexpr double kappa = 0.25;  // series branch: (x3 - x0) <= kappa (x3 + x0)
+  static constexpr int kmax = 80;
+};
+template <> struct Num<float> {
+  static __device__ __forceinline__ float lg(float x) { return logf(x); }
+  static constexpr float tol = 2e-8f;
+  static constexpr float kappa = 0.5f;
+  static constexpr int kmax = 40;
+};
+
+template <typename T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+template <typename T> __device__ __forceinline__ void cswap(T &x, T &y, T &fx, T &fy) {
+  if (y < x) {
+    T t = x; x = y; y = t;
+    t = fx; fx = fy; fy = t;
+  }
+}
+
+// ascending sort of 4 knots carrying their weights (5-comparator network)
+template <typename T> __device__ __forceinline__ void sort4(T d[4], T f[4]) {
+  cswap(d[0], d[1], f[0], f[1]);
+  cswap(d[2], d[3], f[2], f[3]);
+  cswap(d[0], d[2], f[0], f[2]);
+  cswap(d[1], d[3], f[1], f[3]);
+  cswap(d[1], d[2], f[1], f[2]);
+}
+
+// g(t) = t^3 ln|t|, g(0) = 0
+template <typename T> __device__ __forceinline__ T g0(T t) {
+  return t == T(0) ? T(0) : t * t * t * Num<T>::lg(tabs(t));
+}
+
+// g^(k)(c)/k! for k = 1..3 (c != 0)
+template <typename T> __device__ __forceinline__ T glow(int k, T c, T L) {
+  if (k == 1) return T(3) * c * c * L + c * c;
+  if (k == 2) return (T(6) * c * L + T(5) * c) * T(0.5);
+  return (T(6) * L + T(11)) * T(1.0 / 6.0);
+}
+
+// knot t[idx] for a compile-time sized register array without dynamic indexing
+template <typename T> __device__ __forceinline__ T pick5(const T t[5], int idx) {
+  T r = t[0];
+  r = idx == 1 ? t[1] : r;
+  r = idx == 2 ? t[2] : r;
+  r = idx == 3 ? t[3] : r;
+  r = idx == 4 ? t[4] : r;
+  return r;
+}
+
+// Taylor series of the divided difference g[t_i..t_j] (n = j - i) of knots clustered about
+// their mean c != 0, in the scaled offsets e = (t - c)/c (no powers of 1/c that could
+// overflow):  g[t_i..t_j] = sum_{k=n}^{3} g^(k)(c)/k! c^(k-n) h_{k-n}(e)
+//                        + c^(3-n) sum_{k>=4} 6 (-1)^(k-4) / (k(k-1)(k-2)(k-3)) h_{k-n}(e)
+// with h_m the complete homogeneous symmetric polynomials.
+template <typename T> __device__ __noinline__ T dd_taylor(const T t[5], int i, int j) {
+  const int n = j - i;
+  T c = T(0);
+#pragma unroll
+  for (int l = 0; l < 5; ++l) c += (l >= i && l <= j) ? t[l] : T(0);
+  c = c / T(n + 1);
+  const T ci = T(1) / c;
+  T e[5], h[5];
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    e[l] = (l >= i && l <= j) ? (t[l] - c) * ci : T(0);  // padding variables are 0: no effect on h
+    h[l] = T(1);
+  }
+  const T L = Num<T>::lg(tabs(c));
+  T low = T(0), cp = T(1);  // cp = c^(k-n)
+  for (int k = n; k < 4; ++k) {
+    if (k > n) {
+      h[0] = e[0] * h[0];
+#pragma unroll
+      for (int l = 1; l < 5; ++l) h[l] = h[l - 1] + e[l] * h[l];
+      cp *= c;
+    }
+    low += (k == 0 ? g0(c) : glow(k, c, L)) * cp * h[4];
+  }
+  T high = T(0), prev = T(0), big = T(0);
+  for (int k = 4; k < n + Num<T>::kmax; ++k) {
+    if (k > n) {
+      h[0] = e[0] * h[0];
+#pragma unroll
+      for (int l = 1; l < 5; ++l) h[l] = h[l - 1] + e[l] * h[l];
+    }
+    const T kk = T(k);
+    T coef = T(6) / (kk * (kk - T(1)) * (kk - T(2)) * (kk - T(3)));
+    if ((k - 4) & 1) coef = -coef;
+    const T term = coef * h[4];
+    high += term;
+    big = tabs(term) > big ? tabs(term) : big;
+    if (k >= 5 && k - n >= 2 &&
+        tabs(term) + tabs(prev) <= Num<T>::tol * (tabs(high) > big ? tabs(high) : big))
+      break;
+    prev = term;
+  }
+  T scale = T(1);  // c^(3-n)
+  if (n == 4) scale = ci;
+  else if (n == 2) scale = c;
+  else if (n == 1) scale = c * c;
+  return low + scale * high;
+}
+
+// Fourth divided difference g[t0..t4] of sorted knots (no 4 equal zeros).
+template <typename T> __device__ T dd5(const T t[5]) {
+  const T rho = T(kRho);
+  T v[5];
+#pragma unroll
+  for (int l = 0; l < 5; ++l) v[l] = g0(t[l]);
+#pragma unroll
+  for (int n = 1; n <= 4; ++n) {
+#pragma unroll
+    for (int i = 0; i + n <= 4; ++i) {
+      const int j = i + n;
+      const T ti = t[i], tj = t[j];
+      T r;
+      if (ti == tj) {
+        // all knots equal: g^(n)(t)/n!; at t = 0: 0 for n <= 2
+        r = (ti == T(0)) ? T(0) : glow(n < 4 ? n : 3, ti, Num<T>::lg(tabs(ti)));
+        if (n == 4) r = (ti == T(0)) ? T(0) : T(0.25) / ti;
+      } else if ((ti > T(0) && tj - ti <= rho * ti) || (tj < T(0) && tj - ti <= rho * (-tj))) {
+        r = dd_taylor(t, i, j);
+      } else {
+        r = (v[i + 1] - v[i]) / (tj - ti);
+      }
+      v[i] = r;
+    }
+  }
+  return v[0];
+}
+
+// sum_j f_j (1/V) int_S lambda_j / X for sorted knots x of one sign with
+// |x_i - c| <= kappa |c| about the midpoint c = (x_0 + x_3)/2:
+// 1/(c (1 + lambda.e)), e = (x - c)/c, expanded in lambda.e:
+//   (1/V) int lambda_j / X = (1/c) sum_k (-1)^k 6 k!/(k+4)! h_k(e_1..e_4, e_j)
+template <typename T> __device__ T series_sum(const T x[4], const T f[4]) {
+  const T c = (x[0] + x[3]) * T(0.5);
+  const T ci = T(1) / c;
+  T e[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) e[l] = (x[l] - c) * ci;
+  T H[4] = {T(1), T(1), T(1), T(1)};  // H_k over the first l+1 variables
+  T P[4] = {T(1), T(1), T(1), T(1)};  // h_k(e, e_j)
+  T sum = T(0.25) * (f[0] + f[1] + f[2] + f[3]);  // k = 0: 6/24 sum_j f_j
+  T prev = T(0), big = tabs(sum);
+  for (int k = 1; k < Num<T>::kmax; ++k) {
+    H[0] = e[0] * H[0];
+#pragma unroll
+    for (int l = 1; l < 4; ++l) H[l] = H[l - 1] + e[l] * H[l];
+    T s = T(0);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      P[jj] = H[3] + e[jj] * P[jj];
+      s += f[jj] * P[jj];
+    }
+    const T kk = T(k);
+    T coef = T(6) / ((kk + T(1)) * (kk + T(2)) * (kk + T(3)) * (kk + T(4)));
+    if (k & 1) coef = -coef;
+    const T term = coef * s;
+    sum += term;
+    big = tabs(term) > big ? tabs(term) : big;
+    if (k >= 2 && tabs(term) + tabs(prev) <= Num<T>::tol * (tabs(sum) > big ? tabs(sum) : big)) break;
+    prev = term;
+  }
+  return sum * ci;
+}
+
+// sum_j f_j (1/V) int lambda_j / X for sorted knots x (any signs; PV across X = 0)
+template <typename T> __device__ T inv_sum_table(const T xin[4], const T f[4]) {
+  T x[4] = {xin[0], xin[1], xin[2], xin[3]};
+  T s = tabs(x[0]) > tabs(x[3]) ? tabs(x[0]) : tabs(x[3]);
+  if (s == T(0)) return T(0);
+  const int nz = (x[0] == T(0)) + (x[1] == T(0)) + (x[2] == T(0)) + (x[3] == T(0));
+  if (nz >= 3) {
+    // a face with X = 0 (log-divergent): exact zeros floored, measure-zero input
+#pragma unroll
+    for (int l = 0; l < 4; ++l) x[l] = x[l] == T(0) ? T(kFloor) * s : x[l];
+    // re-sort (floored zeros stay below the positive knots; negative knots stay first)
+    T dummy[4] = {T(0), T(0), T(0), T(0)};
+    sort4(x, dummy);
+  }
+  const T si = T(1) / s;
+  T u[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) u[l] = x[l] * si;
+  T acc = T(0);
+#pragma unroll 1
+  for (int jj = 0; jj < 4; ++jj) {
+    T t5[5];
+    t5[0] = u[0];
+#pragma unroll
+    for (int l = 1; l < 5; ++l) t5[l] = l <= jj ? u[l] : u[l - 1];
+    const T fj = jj == 0 ? f[0] : jj == 1 ? f[1] : jj == 2 ? f[2] : f[3];
+    acc += fj * dd5(t5);
+  }
+  return acc * si;
+}
+
+// series branch: sorted knots of one sign with (x3 - x0) <= kappa |x0 + x3|
+template <typename T> __device__ __forceinline__ bool series_ok(const T x[4], T kappa) {
+  return (x[0] > T(0) || x[3] < T(0)) && (x[3] - x[0]) <= kappa * tabs(x[0] + x[3]);
+}
+
+// sum_j f_j (1/V) int_S lambda_j / X, sorted knots x (FP64 or FP32 throughout)
+template <typename T> __device__ __forceinline__ T inv_sum(const T x[4], const T f[4]) {
+  if (series_ok(x, T(Num<T>::kappa))) return series_sum(x, f);
+  return inv_sum_table(x, f);
+}
+
+// mixed precision: FP32 series / table; the table in FP64 when the sorted knots have an
+// inner gap below tau times their scale (sub-clusters, where FP32 differences cancel).
+__device__ __forceinline__ float inv_sum_mixed(const float x[4], const float f[4], float tau,
+                                               int *fp64) {
+  if (series_ok(x, Num<float>::kappa)) return series_sum(x, f);
+  const float s = fmaxf(fabsf(x[0]), fabsf(x[3]));
+  float g = s;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float gi = x[i + 1] - x[i];
+    if (gi > 0.0f) g = fminf(g, gi);  // exact ties (e.g. two zero knots) are exact in the table
+  }
+  if (g >= tau * s) return inv_sum_table(x, f);
+  ++*fp64;
+  double xd[4] = {x[0], x[1], x[2], x[3]}, fd[4] = {f[0], f[1], f[2], f[3]};
+  return (float)inv_sum_table(xd, fd);
+}
+
+// Normalised cubic B-spline density M(w; t0..t4) (integral 1) by the de Boor-Cox
+// recursion for M-splines; sorted knots, half-open support.
+template <typename T> __device__ __forceinline__ T mspline5(const T t[5], T w) {
+  T M[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    M[i] = (t[i] <= w && w < t[i + 1]) ? T(1) / (t[i + 1] - t[i]) : T(0);
+#pragma unroll
+  for (int k = 2; k <= 4; ++k) {
+#pragma unroll
+    for (int i = 0; i + k <= 4; ++i) {
+      const T den = t[i + k] - t[i];
+      M[i] = den > T(0) ? T(k) * ((w - t[i]) * M[i] + (t[i + k] - w) * M[i + 1]) / (T(k - 1) * den)
+                        : T(0);
+    }
+  }
+  return M[0];
+}
+
+// sum_j f_j (1/V) int_S lambda_j delta(w - D) = (1/4) sum_j f_j M(w; d, d_j), sorted d
+template <typename T> __device__ __forceinline__ T delta_sum(const T d[4], const T f[4], T w) {
+  if (!(w > d[0] && w < d[3])) return T(0);
+  T acc = T(0);
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    T t5[5];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) t5[l] = l <= jj ? d[l] : d[l - 1];
+    acc += f[jj] * mspline5(t5, w);
+  }
+  return T(0.25) * acc;
+}
+
+// Tetrahedron density of states at eF for one band: M(0; a_0..a_3), quadratic B-spline
+template <typename T> __device__ __forceinline__ T dos4(T a0, T a1, T a2, T a3) {
+  T t[4] = {a0, a1, a2, a3};
+  T dm[4] = {T(0), T(0), T(0), T(0)};
+  sort4(t, dm);
+  if (!(T(0) >= t[0] && T(0) < t[3])) return T(0);
+  T M[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) M[i] = (t[i] <= T(0) && T(0) < t[i + 1]) ? T(1) / (t[i + 1] - t[i]) : T(0);
+#pragma unroll
+  for (int k = 2; k <= 3; ++k) {
+#pragma unroll
+    for (int i = 0; i + k <= 3; ++i) {
+      const T den = t[i + k] - t[i];
+      M[i] = den > T(0) ? T(k) * ((T(0) - t[i]) * M[i] + (t[i + k] - T(0)) * M[i + 1]) /
+                              (T(k - 1) * den)
+                        : T(0);
+    }
+  }
+  return M[0];
+}
+
+// ------------------------------------------------------------------------------------
+// carving (Sec. II, Fig. 1): keep the part of a tetrahedron where the key is negative.
+// WHICH = 0: key = a (first carving, occupied states); WHICH = 1: key = -b (second
+// carving, empty states at k+q).  Each piece is emitted with its volume relative to the
+// cut tetrahedron, from the cut fractions along the edges.
+// ------------------------------------------------------------------------------------
+// vertex: a = e^m_k - eF, D = e^n_{k+q} - e^m_k (b = a + D), f = |M|^2; D is its own
+// linear attribute so it is exactly 0 wherever the corner data make it 0
+template <typename T> struct Vt {
+  T a, D, f;
+};
+
+template <typename T> __device__ __forceinline__ Vt<T> vmix(const Vt<T> &P, const Vt<T> &Q, T t) {
+  const T s = T(1) - t;
+  return Vt<T>{s * P.a + t * Q.a, s * P.D + t * Q.D, s * P.f + t * Q.f};
+}
+
+template <int WHICH, typename T> __device__ __forceinline__ T vkey(const Vt<T> &v) {
+  return WHICH == 0 ? v.a : -(v.a + v.D);
+}
+
+// point where the key vanishes on edge P (key < 0) - Q (key >= 0); returns the fraction
+template <int WHICH, typename T>
+__device__ __forceinline__ Vt<T> vcut(const Vt<T> &P, const Vt<T> &Q, T &frac) {
+  const T kp = vkey<WHICH>(P), kq = vkey<WHICH>(Q);
+  frac = kp / (kp - kq);
+  Vt<T> R = vmix(P, Q, frac);
+  if (WHICH == 0) R.a = T(0);  // on the first cut plane; the second cut is the last one
+  return R;
+}
+
+template <int WHICH, typename T> __device__ __forceinline__ void vswap(Vt<T> &x, Vt<T> &y) {
+  if (vkey<WHICH>(y) < vkey<WHICH>(x)) {
+    Vt<T> t = x; x = y; y = t;
+  }
+}
+
+// Pieces of one cut: out[0..count) with volumes r[] relative to the input tetrahedron.
+template <int WHICH, typename T>
+__device__ __forceinline__ int carve_pieces(const Vt<T> in[4], Vt<T> out[3][4], T r[3]) {
+  Vt<T> S[4] = {in[0], in[1], in[2], in[3]};
+  vswap<WHICH>(S[0], S[1]);
+  vswap<WHICH>(S[2], S[3]);
+  vswap<WHICH>(S[0], S[2]);
+  vswap<WHICH>(S[1], S[3]);
+  vswap<WHICH>(S[1], S[2]);
+  const int nneg = (vkey<WHICH>(S[0]) < T(0)) + (vkey<WHICH>(S[1]) < T(0)) +
+                   (vkey<WHICH>(S[2]) < T(0)) + (vkey<WHICH>(S[3]) < T(0));
+  if (nneg == 0) return 0;
+  if (nneg == 4) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[0][i] = S[i];
+    r[0] = T(1);
+    return 1;
+  }
+  if (nneg == 1) {  // corner tetrahedron at S0: volume t1 t2 t3
+    T t1, t2, t3;
+    out[0][0] = S[0];
+    out[0][1] = vcut<WHICH>(S[0], S[1], t1);
+    out[0][2] = vcut<WHICH>(S[0], S[2], t2);
+    out[0][3] = vcut<WHICH>(S[0], S[3], t3);
+    r[0] = t1 * t2 * t3;
+    return 1;
+  }
+  if (nneg == 2) {  // prism (S0, P02, P03) - (S1, P12, P13)
+    T u0, v0, u1, v1;
+    const Vt<T> P02 = vcut<WHICH>(S[0], S[2], u0), P03 = vcut<WHICH>(S[0], S[3], v0);
+    const Vt<T> P12 = vcut<WHICH>(S[1], S[2], u1), P13 = vcut<WHICH>(S[1], S[3], v1);
+    out[0][0] = S[0]; out[0][1] = P02; out[0][2] = P03; out[0][3] = S[1];
+    out[1][0] = P02;  out[1][1] = P03; out[1][2] = S[1]; out[1][3] = P12;
+    out[2][0] = P03;  out[2][1] = S[1]; out[2][2] = P12; out[2][3] = P13;
+    r[0] = u0 * v0;
+    r[1] = v0 * (T(1) - u0) * u1;
+    r[2] = (T(1) - v0) * u1 * v1;
+    return 3;
+  }
+  // nneg == 3: tetrahedron minus the corner at S3: prism (S0,S1,S2) - (P03,P13,P23)
+  T s0, s1, s2;
+  const Vt<T> P03 = vcut<WHICH>(S[0], S[3], s0), P13 = vcut<WHICH>(S[1], S[3], s1),
+              P23 = vcut<WHICH>(S[2], S[3], s2);
+  out[0][0] = S[0]; out[0][1] = S[1]; out[0][2] = S[2]; out[0][3] = P03;
+  out[1][0] = S[1]; out[1][1] = S[2]; out[1][2] = P03;  out[1][3] = P13;
+  out[2][0] = S[2]; out[2][1] = P03;  out[2][2] = P13;  out[2][3] = P23;
+  r[0] = s0;
+  r[1] = (T(1) - s0) * s1;
+  r[2] = (T(1) - s0) * (T(1) - s1) * s2;
+  return 3;
+}
+
+// Both carvings of one (tetrahedron, band pair): emit(vol_ratio, d[4], f[4]) for every
+// final tetrahedron (d = b - a >= 0, unsorted).  Loops stay rolled so the emitted body
+// is instantiated once.
+template <typename T, typename Emit>
+__device__ __forceinline__ void carve2(const T a[4], const T b[4], const T f[4], Emit &&emit) {
+  Vt<T> V[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) V[i] = Vt<T>{a[i], b[i] - a[i], f[i]};
+  Vt<T> P1[3][4];
+  T r1[3];
+  const int n1 = carve_pieces<0>(V, P1, r1);
+  // unrolled with static indices so the pieces stay in registers
+#pragma unroll
+  for (int i1 = 0; i1 < 3; ++i1) {
+    if (i1 >= n1 || r1[i1] <= T(0)) continue;
+    Vt<T> P2[3][4];
+    T r2[3];
+    const int n2 = carve_pieces<1>(P1[i1], P2, r2);
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2) {
+      if (i2 >= n2) continue;
+      const T r = r1[i1] * r2[i2];
+      if (r <= T(0)) continue;
+      T d[4], ff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const T dd = P2[i2][i].D;
+        d[i] = dd > T(0) ? dd : T(0);
+        ff[i] = P2[i2][i].f;
+      }
+      emit(r, d, ff);
+    }
+  }
+}
+
+}  // namespace chi0dev

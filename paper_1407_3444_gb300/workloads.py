@@ -42,6 +42,13 @@ def corner_dims(n: Sequence[int], periodic: bool) -> Tuple[int, int, int]:
     return tuple(int(x) if periodic else int(x) + 1 for x in n)
 
 
+def corner_index(n: Sequence[int], periodic: bool) -> np.ndarray:
+    """Integer grid indices [Nc, 3] of the corners, slowest axis first."""
+    N = corner_dims(n, periodic)
+    g = np.stack(np.meshgrid(*[np.arange(N[d]) for d in range(3)], indexing="ij"), axis=-1)
+    return g.reshape(-1, 3)
+
+
 def corner_frac(n: Sequence[int], periodic: bool) -> np.ndarray:
     """Fractional coordinates [Nc, 3] of the grid corners, slowest axis first."""
     N = corner_dims(n, periodic)
@@ -166,23 +173,38 @@ class TBModel:
     t0: np.ndarray                                    # [norb, norb] Hermitian
     bonds: List[Tuple[Tuple[int, int, int], np.ndarray]]  # half the bonds; partner -R implied
 
-    def hamiltonian(self, kfrac: np.ndarray) -> np.ndarray:
-        kfrac = np.asarray(kfrac, dtype=np.float64)
-        H = np.broadcast_to(self.t0, (kfrac.shape[0], self.norb, self.norb)).astype(np.complex128)
+    def hamiltonian(self, kfrac: np.ndarray, grid=None) -> np.ndarray:
+        """H(k) at fractional k.  ``grid = (idx [B,3] ints, n)``: k = idx/n exactly, with
+        the phase k.R reduced in integers so that k and -k (mod G) get bitwise-identical
+        Hamiltonians (exact symmetric degeneracies stay exact)."""
+        B = kfrac.shape[0] if grid is None else grid[0].shape[0]
+        H = np.broadcast_to(self.t0, (B, self.norb, self.norb)).astype(np.complex128)
         for R, t in self.bonds:
-            ph = 2.0 * np.cos(2.0 * np.pi * (kfrac @ np.asarray(R, dtype=np.float64)))
+            if grid is None:
+                ph = 2.0 * np.cos(2.0 * np.pi * (np.asarray(kfrac, dtype=np.float64) @ np.asarray(R, dtype=np.float64)))
+            else:
+                idx, n = grid
+                L = int(np.lcm.reduce(np.asarray(n, dtype=np.int64)))
+                p = (idx.astype(np.int64) * (np.asarray(R, dtype=np.int64) * (L // np.asarray(n, dtype=np.int64)))).sum(axis=1) % L
+                p = np.minimum(p, L - p)
+                ph = 2.0 * np.cos(2.0 * np.pi * p / L)
             H = H + ph[:, None, None] * t[None, :, :]
         return H
 
-    def eig(self, kfrac: np.ndarray, nproc: int = 1, cdtype=np.complex128, chunk: int = 1 << 16):
-        B = kfrac.shape[0]
+    def eig(self, kfrac: np.ndarray, nproc: int = 1, cdtype=np.complex128, chunk: int = 1 << 16, grid=None):
+        B = kfrac.shape[0] if grid is None else grid[0].shape[0]
         w = np.empty((B, self.norb), dtype=np.float64)
         v = np.empty((B, self.norb, self.norb), dtype=cdtype)
         for s in range(0, B, chunk * max(1, nproc)):
             e = min(B, s + chunk * max(1, nproc))
-            H = self.hamiltonian(kfrac[s:e])
+            H = self.hamiltonian(None if grid is not None else kfrac[s:e],
+                                 grid=None if grid is None else (grid[0][s:e], grid[1]))
             w[s:e], v[s:e] = eigh_batched(H, nproc=nproc, cdtype=cdtype)
         return w, v
+
+    def eig_grid(self, n, nproc: int = 1, cdtype=np.complex128):
+        """Eigen-data at the corners of the periodic grid n (exact symmetric phases)."""
+        return self.eig(None, nproc=nproc, cdtype=cdtype, grid=(corner_index(n, True), tuple(n)))
 
 
 def _herm(rng, n, sigma):
@@ -226,7 +248,7 @@ def random_model(norb: int, seed: int, spread: float = 8.0) -> TBModel:
     t0 = _herm(rng, norb, 1.0)
     bonds = [(R, _herm(rng, norb, 1.0)) for R in _SC1]
     m = TBModel(norb, t0, bonds)
-    w, _ = m.eig(corner_frac((6, 6, 6), True))
+    w, _ = m.eig_grid((6, 6, 6))
     s = spread / float(w.max() - w.min())
     return TBModel(norb, t0 * s, [(R, t * s) for R, t in bonds])
 
@@ -294,8 +316,7 @@ def cr_like(n: int = 48, nq: int = 256, nproc: int = 1, cdtype=np.complex128,
     """Cr-like 9-orbital static workload: 256 q on Gamma-X-M-Gamma (equal arc length,
     off-grid, explicit k+q eigen-data), E_F at 6/9 filling."""
     m = cr_like_model()
-    kf = corner_frac((n, n, n), True)
-    E, C = m.eig(kf, nproc=nproc, cdtype=cdtype)
+    E, C = m.eig_grid((n, n, n), nproc=nproc, cdtype=cdtype)
     ef = fermi_level(E, 6.0)
     if qfracs is None:
         qfracs = path_points([(0, 0, 0), (0.5, 0, 0), (0.5, 0.5, 0), (0, 0, 0)], nq)
@@ -309,8 +330,7 @@ def fese_like(n=(64, 64, 16), nq: int = 64, nw: int = 512, wmax: float = 2.0, np
     """FeSe-like dynamic workload: 10 bands, E_F at 6/10 filling, 64 q on Gamma-M
     (q_j = (j+1)/64 M, explicit k+q eigen-data), 512 omega in [0, 2] eV."""
     m = fese_like_model()
-    kf = corner_frac(n, True)
-    E, C = m.eig(kf, nproc=nproc, cdtype=cdtype)
+    E, C = m.eig_grid(n, nproc=nproc, cdtype=cdtype)
     ef = fermi_level(E, 6.0)
     if qfracs is None:
         qfracs = [np.array([0.5, 0.5, 0.0]) * (j + 1) / nq for j in range(nq)]
@@ -338,8 +358,7 @@ def band_sweep(n: int = 32, nb: int = 40, nq: int = 128, nw: int = 128, wmax: fl
     w ~ U{4..40} centred on E_F: lo = clamp(n_occ - w//2, 0, nb - w)."""
     seed = SEED_BASE + 4
     m = random_model(nb, seed)
-    kf = corner_frac((n, n, n), True)
-    E, C = m.eig(kf, nproc=nproc, cdtype=cdtype)
+    E, C = m.eig_grid((n, n, n), nproc=nproc, cdtype=cdtype)
     nocc = nb // 2
     ef = fermi_level(E, nocc)
     rng = np.random.default_rng(seed + 1000)
@@ -360,8 +379,7 @@ def large_mixed(n: int = 72, nb: int = 80, nq: int = 128, nw: int = 256, wmax: f
     256 omega in [0, 2] eV, full band window."""
     seed = SEED_BASE + 5
     m = random_model(nb, seed)
-    kf = corner_frac((n, n, n), True)
-    E, C = m.eig(kf, nproc=nproc, cdtype=cdtype)
+    E, C = m.eig_grid((n, n, n), nproc=nproc, cdtype=cdtype)
     ef = fermi_level(E, nb // 2)
     rng = np.random.default_rng(seed + 1000)
     qs = [QPoint(shift=s, frac=tuple(si / n for si in s)) for s in _random_shifts(rng, (n, n, n), nq)]
@@ -374,8 +392,7 @@ def tiny_tb(n: int = 4, norb: int = 3, seed: int = SEED_BASE + 7, nq: int = 3, f
             explicit: bool = True, cdtype=np.complex128) -> Workload:
     """Small random model for brute-force and parity checks."""
     m = random_model(norb, seed, spread=4.0)
-    kf = corner_frac((n, n, n), True)
-    E, C = m.eig(kf, cdtype=cdtype)
+    E, C = m.eig_grid((n, n, n), cdtype=cdtype)
     nocc = norb / 2 if filling is None else filling
     ef = fermi_level(E, nocc)
     rng = np.random.default_rng(seed + 1)

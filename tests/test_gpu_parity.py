@@ -1,0 +1,171 @@
+"""CUDA path (through the C-ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances (normwise per q, separately for Re and Im: max_w |gpu - ref| / max_w |ref|):
+  * all-FP64 GPU form: 1e-12;
+  * mixed precision (FP32 overlaps and weights, FP64 near-degenerate branches, FP64
+    accumulation): 1e-6.
+"""
+import numpy as np
+import pytest
+
+from paper_1407_3444_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def C():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1407_3444_gb300 import build, chi0
+    build.build()
+    chi0.lib()
+    return chi0
+
+
+@pytest.fixture(scope="module")
+def O(oracle_mod):
+    return oracle_mod
+
+
+def nerr(got, ref):
+    got = np.atleast_2d(np.asarray(got, dtype=np.float64))
+    ref = np.atleast_2d(np.asarray(ref, dtype=np.float64))
+    scale = np.max(np.abs(ref), axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return float(np.max(np.max(np.abs(got - ref), axis=1) / scale))
+
+
+def run_static(C, W, prec, device=True, **kw):
+    P = C.Plan(W, precision=prec, device=device, **kw)
+    out = P.static()
+    P.close()
+    return out.cpu().numpy() if hasattr(out, "cpu") else out
+
+
+def run_dynamic(C, W, prec, omega, device=True, **kw):
+    P = C.Plan(W, precision=prec, device=device, **kw)
+    re, im = P.dynamic(omega)
+    P.close()
+    if hasattr(re, "cpu"):
+        re, im = re.cpu().numpy(), im.cpu().numpy()
+    return re, im
+
+
+# ------------------------------------------------------------------------ static
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_static_free_electron(C, O, prec):
+    W = wl.free_electron(12, 7)
+    ref = O.chi0(W)
+    got = run_static(C, W, prec)
+    assert nerr(got[:, None], ref[:, None]) < TOL[prec], (got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_static_tb_explicit_ragged(C, O, prec):
+    # 12^3 grid: 10368 tetrahedra > one grid-stride round of warps; 5 bands
+    W = wl.tiny_tb(n=12, norb=5, nq=3, seed=wl.SEED_BASE + 40)
+    ref = O.chi0(W)
+    got = run_static(C, W, prec)
+    assert nerr(got[:, None], ref[:, None]) < TOL[prec], (got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_static_tb_shift_and_gamma(C, O, prec):
+    W = wl.tiny_tb(n=8, norb=4, nq=0, seed=wl.SEED_BASE + 41)
+    W.qs = [wl.QPoint(shift=(0, 0, 0), gamma=True), wl.QPoint(shift=(1, 0, 0)), wl.QPoint(shift=(3, 5, 7)),
+            wl.QPoint(shift=(-1, 2, -3))]
+    Wo = wl.Workload(W.name, W.n, W.periodic, W.nb, W.norb, W.E, W.C, W.ef, W.window, W.cma,
+                     [wl.QPoint(shift=tuple(s % 8 for s in q.shift), gamma=q.gamma) for q in W.qs])
+    ref = O.chi0(Wo)
+    got = run_static(C, W, prec)
+    assert nerr(got[:, None], ref[:, None]) < TOL[prec], (got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_static_per_q_windows(C, O, prec):
+    W = wl.tiny_tb(n=6, norb=8, nq=0, seed=wl.SEED_BASE + 42)
+    rng = np.random.default_rng(5)
+    qs = []
+    for j in range(6):
+        w = int(rng.integers(2, 9))
+        lo = min(max(4 - w // 2, 0), 8 - w)
+        qs.append(wl.QPoint(shift=tuple(int(x) for x in rng.integers(0, 6, 3)), window=(lo, lo + w)))
+    W.qs = qs
+    ref = O.chi0(W)
+    got = run_static(C, W, prec)
+    assert nerr(got[:, None], ref[:, None]) < TOL[prec]
+
+
+def test_static_host_inputs_and_c64(C, O):
+    W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 43, cdtype=np.complex64)
+    ref = O.chi0(W)  # the oracle promotes the same complex64 values
+    got_h = run_static(C, W, "fp64", device=False)
+    got_d = run_static(C, W, "fp64", device=True)
+    assert nerr(got_h[:, None], ref[:, None]) < 1e-12
+    assert np.array_equal(got_h, got_d)
+
+
+def test_static_custom_tetra_list(C, O):
+    W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 44)
+    rng = np.random.default_rng(3)
+    tet = rng.integers(0, W.ncorner, size=(500, 4)).astype(np.int32)
+    vol = rng.uniform(1e-4, 1e-3, 500)
+    ref = np.array([O.chi0_q(W, q, tet=tet, tvol=vol) for q in W.qs])
+    got = run_static(C, W, "fp64", tetra=(tet, vol))
+    assert nerr(got[:, None], ref[:, None]) < 1e-12
+
+
+def test_static_sign_and_cma(C, O):
+    W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 45)
+    pos = run_static(C, W, "fp64")
+    neg = run_static(C, W, "fp64", sign=C.CHI0_SIGN_PAPER)
+    assert np.array_equal(pos, -neg)
+    W.cma = True
+    ref = O.chi0(W)
+    got = run_static(C, W, "fp64")
+    assert nerr(got[:, None], ref[:, None]) < 1e-12
+
+
+def test_static_deterministic(C):
+    W = wl.tiny_tb(n=10, norb=5, nq=2, seed=wl.SEED_BASE + 46)
+    a = run_static(C, W, "mixed")
+    b = run_static(C, W, "mixed")
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------------ dynamic
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dynamic_tb(C, O, prec):
+    W = wl.tiny_tb(n=8, norb=4, nq=2, seed=wl.SEED_BASE + 47)
+    omega = np.concatenate([np.linspace(0.0, 3.0, 61), [-0.7, -1.9]])
+    ref_r, ref_i = zip(*[O.chi0_q(W, q, omega=omega) for q in W.qs])
+    gr, gi = run_dynamic(C, W, prec, omega)
+    assert nerr(gr, np.array(ref_r)) < TOL[prec]
+    assert nerr(gi, np.array(ref_i)) < TOL[prec]
+
+
+def test_dynamic_many_frequencies_and_gamma(C, O):
+    # 300 frequencies: two passes of the frequency loop; Gamma adds N(eF) at w = 0
+    W = wl.tiny_tb(n=6, norb=3, nq=0, seed=wl.SEED_BASE + 48)
+    W.qs = [wl.QPoint(shift=(0, 0, 0), gamma=True), wl.QPoint(shift=(2, 1, 0))]
+    omega = np.linspace(0.0, 4.0, 300)
+    ref_r, ref_i = zip(*[O.chi0_q(W, q, omega=omega) for q in W.qs])
+    gr, gi = run_dynamic(C, W, "fp64", omega)
+    assert nerr(gr, np.array(ref_r)) < 1e-12
+    # at Gamma the interband |M|^2 vanish (orthogonal eigenvectors): Im is rounding noise
+    # there, so Im is compared on the scale of the whole (q, w) table
+    ref_i = np.array(ref_i)
+    assert np.max(np.abs(gi - ref_i)) < 1e-12 * np.max(np.abs(ref_i))
+
+
+def test_dynamic_free_electron_open_grid(C, O):
+    W = wl.free_electron(10, 3, qmax_over_2kf=0.5)
+    omega = np.linspace(0.0, 6.0, 40)
+    ref_r, ref_i = zip(*[O.chi0_q(W, q, omega=omega) for q in W.qs])
+    gr, gi = run_dynamic(C, W, "fp64", omega)
+    assert nerr(gr, np.array(ref_r)) < 1e-12
+    assert nerr(gi[1:], np.array(ref_i)[1:]) < 1e-12
