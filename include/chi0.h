@@ -175,7 +175,7 @@ typedef struct {
 /* ---------------------------------------------------------------- entry points */
 
 /* Fills *opts with defaults: FP64, FP32 overlaps, exact |M|^2, positive sign,
- * tau = 2^-10, host inputs and outputs, default stream, no profiling. */
+ * tau = 2^-20, host inputs and outputs, default stream, no profiling. */
 void chi0_opts_default(chi0_opts_t *opts);
 
 /* Builds a plan for one k mesh (Sec. II: the tetrahedron decomposition and the corner

@@ -29,28 +29,30 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, defines=(), lib: str = LIB, out: str = OUT) -> str:
+    """Compile the sources (in parallel) and link ``lib``.  ``defines``: extra -D flags for
+    tuning builds, which then go to their own object folder ``out``."""
+    os.makedirs(out, exist_ok=True)
     hdrs = [os.path.join(SRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "chi0.h")]
     objs, procs = [], []
     for s in SOURCES:
         src = os.path.join(SRC, s)
-        obj = os.path.join(OUT, s.replace(".cu", ".o"))
+        obj = os.path.join(out, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
-            cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+            cmd = [nvcc()] + ARCH + FLAGS + ["-D" + d for d in defines] + ["-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((cmd, subprocess.Popen(cmd)))
     for cmd, p in procs:
         if p.wait() != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

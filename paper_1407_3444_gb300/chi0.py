@@ -238,7 +238,7 @@ class Plan:
     optionally pinned); the library copies them and returns host results."""
 
     def __init__(self, W, precision: str = "fp64", device: bool = True, stream=None, profile: bool = False,
-                 tau: float = 9.765625e-4, sign: int = CHI0_SIGN_POSITIVE, tetra=None, window=None, cma=None,
+                 tau: float = 9.5367431640625e-07, sign: int = CHI0_SIGN_POSITIVE, tetra=None, window=None, cma=None,
                  qs: Optional[Sequence] = None, staged: Optional[Staged] = None):
         self.W = W
         self.device = device

@@ -72,7 +72,7 @@ extern "C" void chi0_opts_default(chi0_opts_t *o) {
   o->overlap = CHI0_OVL_FP32;
   o->cma = 0;
   o->sign = CHI0_SIGN_POSITIVE;
-  o->tau = 9.765625e-4; /* 2^-10 */
+  o->tau = 9.5367431640625e-7; /* 2^-20 */
   o->inputs_on_device = 0;
   o->outputs_on_device = 0;
   o->stream = nullptr;

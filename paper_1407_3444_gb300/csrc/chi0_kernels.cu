@@ -157,6 +157,7 @@ __device__ __forceinline__ void block_sum_store(double v, double *out) {
 }
 
 // ---------------------------------------------------------------- overlap
+// Thread per output (m, n) at a corner: general sizes.
 template <typename CT, typename T>
 __global__ void __launch_bounds__(kThreads) k_overlap(Grid g, const CT *__restrict__ C,
                                                        const CT *__restrict__ Cqx, Q q, T *__restrict__ W2) {
@@ -178,6 +179,45 @@ __global__ void __launch_bounds__(kThreads) k_overlap(Grid g, const CT *__restri
       im += xr * yi - xi * yr;
     }
     W2[idx] = re * re + im * im;
+  }
+}
+
+// Warp per corner for small blocks (norb * w <= kOvlSmall): both eigenvector blocks
+// C_k[:, lo:hi] and C_{k+q}[:, lo:hi] are read once, coalesced, into shared memory in
+// the arithmetic precision, then the lanes form the w x w |overlap|^2 block.
+constexpr int kOvlSmall = 256;
+template <typename CT, typename T>
+__global__ void __launch_bounds__(kThreads) k_overlap_small(Grid g, const CT *__restrict__ C,
+                                                             const CT *__restrict__ Cqx, Q q,
+                                                             T *__restrict__ W2) {
+  __shared__ T sA[kWarps][2][kOvlSmall], sB[kWarps][2][kOvlSmall];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = q.hi - q.lo, no = g.norb, nel = no * w;
+  const CT *Cb = Cqx ? Cqx : C;
+  for (long long c = (long long)blockIdx.x * kWarps + wib; c < g.nc; c += (long long)gridDim.x * kWarps) {
+    const long long ck = Cqx ? c : shift_corner(g, c, q.shift);
+    for (int i = lane; i < nel; i += 32) {
+      const int o = i / w, mm = i - o * w;
+      const CT x = C[(c * no + o) * g.nb + q.lo + mm];
+      const CT y = Cb[(ck * no + o) * g.nb + q.lo + mm];
+      sA[wib][0][i] = (T)x.x;
+      sA[wib][1][i] = (T)x.y;
+      sB[wib][0][i] = (T)y.x;
+      sB[wib][1][i] = (T)y.y;
+    }
+    __syncwarp();
+    for (int out = lane; out < w * w; out += 32) {
+      const int mm = out / w, nn = out - mm * w;
+      T re = T(0), im = T(0);
+      for (int o = 0; o < no; ++o) {
+        const T xr = sA[wib][0][o * w + mm], xi = sA[wib][1][o * w + mm];
+        const T yr = sB[wib][0][o * w + nn], yi = sB[wib][1][o * w + nn];
+        re += xr * yr + xi * yi;  // conj(x) * y
+        im += xr * yi - xi * yr;
+      }
+      W2[c * w * w + out] = re * re + im * im;
+    }
+    __syncwarp();
   }
 }
 
@@ -230,7 +270,7 @@ template <typename T> struct Acc {
 };
 
 template <bool FP64>
-__device__ __forceinline__ typename std::conditional<FP64, double, float>::type table_eval(
+__device__ __noinline__ typename std::conditional<FP64, double, float>::type table_eval(
     const Piece<typename std::conditional<FP64, double, float>::type> &pc, float tau, int &nfp64) {
   if constexpr (FP64) {
     return pc.w * inv_sum_table(pc.d, pc.f);
@@ -249,8 +289,16 @@ __device__ __forceinline__ typename std::conditional<FP64, double, float>::type 
   }
 }
 
+// resident blocks per SM the register allocation of the static kernel must allow
+#ifndef CHI0_STATIC_MINB_F32
+#define CHI0_STATIC_MINB_F32 2
+#endif
+#ifndef CHI0_STATIC_MINB_F64
+#define CHI0_STATIC_MINB_F64 1
+#endif
+
 template <bool FP64>
-__global__ void __launch_bounds__(kThreads) k_static(Grid g, Tet tet, const void *__restrict__ Ek,
+__global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_STATIC_MINB_F32) k_static(Grid g, Tet tet, const void *__restrict__ Ek,
                                                       const void *__restrict__ Ekq, Q q,
                                                       const void *__restrict__ W2, int cma, float tau,
                                                       const short *__restrict__ occ,
@@ -552,6 +600,18 @@ cudaError_t launch_overlap(const Grid &g, const double *, const void *C, int dty
   long long nb = (total + kThreads - 1) / kThreads;
   const int blocks = (int)(nb < kSMs * 16 ? nb : kSMs * 16);
   if (blocks <= 0) return cudaSuccess;
+  const bool small = (long long)g.norb * w <= kOvlSmall && !fp64;
+  if (small) {
+    long long nbw = (g.nc + kWarps - 1) / kWarps;
+    const int bw = (int)(nbw < kSMs * 8 ? nbw : kSMs * 8);
+    if (dtype == DT_C128)
+      k_overlap_small<double2, float><<<bw, kThreads, 0, s>>>(g, (const double2 *)C, (const double2 *)q.Cq, q,
+                                                              (float *)W2);
+    else
+      k_overlap_small<float2, float><<<bw, kThreads, 0, s>>>(g, (const float2 *)C, (const float2 *)q.Cq, q,
+                                                             (float *)W2);
+    return cudaGetLastError();
+  }
   if (dtype == DT_C128) {
     const double2 *Cx = (const double2 *)C, *Cq = (const double2 *)q.Cq;
     if (fp64) k_overlap<double2, double><<<blocks, kThreads, 0, s>>>(g, Cx, Cq, q, (double *)W2);

@@ -168,6 +168,22 @@ template <typename T> __device__ T dd5(const T t[5]) {
   return v[0];
 }
 
+// (-1)^k 6 k!/(k+4)! = (-1)^k 6/((k+1)(k+2)(k+3)(k+4)), the series coefficients below
+template <typename T, int N> struct SeriesCoef {
+  T v[N];
+  constexpr SeriesCoef() : v() {
+    for (int k = 0; k < N; ++k) {
+      const T c = T(6) / (T(k + 1) * T(k + 2) * T(k + 3) * T(k + 4));
+      v[k] = (k & 1) ? -c : c;
+    }
+  }
+};
+__constant__ constexpr SeriesCoef<float, Num<float>::kmax> kCoefF{};
+__constant__ constexpr SeriesCoef<double, Num<double>::kmax> kCoefD{};
+template <typename T> __device__ __forceinline__ T series_coef(int k);
+template <> __device__ __forceinline__ float series_coef<float>(int k) { return kCoefF.v[k]; }
+template <> __device__ __forceinline__ double series_coef<double>(int k) { return kCoefD.v[k]; }
+
 // sum_j f_j (1/V) int_S lambda_j / X for sorted knots x of one sign with
 // |x_i - c| <= kappa |c| about the midpoint c = (x_0 + x_3)/2:
 // 1/(c (1 + lambda.e)), e = (x - c)/c, expanded in lambda.e:
@@ -192,10 +208,7 @@ template <typename T> __device__ T series_sum(const T x[4], const T f[4]) {
       P[jj] = H[3] + e[jj] * P[jj];
       s += f[jj] * P[jj];
     }
-    const T kk = T(k);
-    T coef = T(6) / ((kk + T(1)) * (kk + T(2)) * (kk + T(3)) * (kk + T(4)));
-    if (k & 1) coef = -coef;
-    const T term = coef * s;
+    const T term = series_coef<T>(k) * s;
     sum += term;
     big = tabs(term) > big ? tabs(term) : big;
     if (k >= 2 && tabs(term) + tabs(prev) <= Num<T>::tol * (tabs(sum) > big ? tabs(sum) : big)) break;
@@ -356,9 +369,11 @@ template <int WHICH, typename T> __device__ __forceinline__ void vswap(Vt<T> &x,
   }
 }
 
-// Pieces of one cut: out[0..count) with volumes r[] relative to the input tetrahedron.
+// Piece idx of one cut (keep key < 0) and the number of pieces (0, 1 or 3); r = volume of
+// the piece relative to the input tetrahedron, from the cut fractions along the edges.
+// Pieces are built on demand so that only one of them is live at a time.
 template <int WHICH, typename T>
-__device__ __forceinline__ int carve_pieces(const Vt<T> in[4], Vt<T> out[3][4], T r[3]) {
+__device__ __forceinline__ int cut_piece(const Vt<T> in[4], int idx, Vt<T> P[4], T &r) {
   Vt<T> S[4] = {in[0], in[1], in[2], in[3]};
   vswap<WHICH>(S[0], S[1]);
   vswap<WHICH>(S[2], S[3]);
@@ -370,73 +385,89 @@ __device__ __forceinline__ int carve_pieces(const Vt<T> in[4], Vt<T> out[3][4], 
   if (nneg == 0) return 0;
   if (nneg == 4) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out[0][i] = S[i];
-    r[0] = T(1);
+    for (int i = 0; i < 4; ++i) P[i] = S[i];
+    r = T(1);
     return 1;
   }
   if (nneg == 1) {  // corner tetrahedron at S0: volume t1 t2 t3
     T t1, t2, t3;
-    out[0][0] = S[0];
-    out[0][1] = vcut<WHICH>(S[0], S[1], t1);
-    out[0][2] = vcut<WHICH>(S[0], S[2], t2);
-    out[0][3] = vcut<WHICH>(S[0], S[3], t3);
-    r[0] = t1 * t2 * t3;
+    P[0] = S[0];
+    P[1] = vcut<WHICH>(S[0], S[1], t1);
+    P[2] = vcut<WHICH>(S[0], S[2], t2);
+    P[3] = vcut<WHICH>(S[0], S[3], t3);
+    r = t1 * t2 * t3;
     return 1;
   }
   if (nneg == 2) {  // prism (S0, P02, P03) - (S1, P12, P13)
     T u0, v0, u1, v1;
     const Vt<T> P02 = vcut<WHICH>(S[0], S[2], u0), P03 = vcut<WHICH>(S[0], S[3], v0);
     const Vt<T> P12 = vcut<WHICH>(S[1], S[2], u1), P13 = vcut<WHICH>(S[1], S[3], v1);
-    out[0][0] = S[0]; out[0][1] = P02; out[0][2] = P03; out[0][3] = S[1];
-    out[1][0] = P02;  out[1][1] = P03; out[1][2] = S[1]; out[1][3] = P12;
-    out[2][0] = P03;  out[2][1] = S[1]; out[2][2] = P12; out[2][3] = P13;
-    r[0] = u0 * v0;
-    r[1] = v0 * (T(1) - u0) * u1;
-    r[2] = (T(1) - v0) * u1 * v1;
+    if (idx == 0) {
+      P[0] = S[0]; P[1] = P02; P[2] = P03; P[3] = S[1];
+      r = u0 * v0;
+    } else if (idx == 1) {
+      P[0] = P02; P[1] = P03; P[2] = S[1]; P[3] = P12;
+      r = v0 * (T(1) - u0) * u1;
+    } else {
+      P[0] = P03; P[1] = S[1]; P[2] = P12; P[3] = P13;
+      r = (T(1) - v0) * u1 * v1;
+    }
     return 3;
   }
   // nneg == 3: tetrahedron minus the corner at S3: prism (S0,S1,S2) - (P03,P13,P23)
   T s0, s1, s2;
   const Vt<T> P03 = vcut<WHICH>(S[0], S[3], s0), P13 = vcut<WHICH>(S[1], S[3], s1),
               P23 = vcut<WHICH>(S[2], S[3], s2);
-  out[0][0] = S[0]; out[0][1] = S[1]; out[0][2] = S[2]; out[0][3] = P03;
-  out[1][0] = S[1]; out[1][1] = S[2]; out[1][2] = P03;  out[1][3] = P13;
-  out[2][0] = S[2]; out[2][1] = P03;  out[2][2] = P13;  out[2][3] = P23;
-  r[0] = s0;
-  r[1] = (T(1) - s0) * s1;
-  r[2] = (T(1) - s0) * (T(1) - s1) * s2;
+  if (idx == 0) {
+    P[0] = S[0]; P[1] = S[1]; P[2] = S[2]; P[3] = P03;
+    r = s0;
+  } else if (idx == 1) {
+    P[0] = S[1]; P[1] = S[2]; P[2] = P03; P[3] = P13;
+    r = (T(1) - s0) * s1;
+  } else {
+    P[0] = S[2]; P[1] = P03; P[2] = P13; P[3] = P23;
+    r = (T(1) - s0) * (T(1) - s1) * s2;
+  }
   return 3;
 }
 
 // Both carvings of one (tetrahedron, band pair): emit(vol_ratio, d[4], f[4]) for every
-// final tetrahedron (d = b - a >= 0, unsorted).  Loops stay rolled so the emitted body
-// is instantiated once.
+// final tetrahedron (d = b - a >= 0, unsorted).  Rolled loops: one copy of the emitted
+// body, one live piece per level.
 template <typename T, typename Emit>
 __device__ __forceinline__ void carve2(const T a[4], const T b[4], const T f[4], Emit &&emit) {
+  const T amax = fmax(fmax(a[0], a[1]), fmax(a[2], a[3]));
+  const T bmin = fmin(fmin(b[0], b[1]), fmin(b[2], b[3]));
+  if (amax < T(0) && bmin > T(0)) {  // occupied at k and empty at k+q everywhere: no cut
+    T d[4] = {b[0] - a[0], b[1] - a[1], b[2] - a[2], b[3] - a[3]};
+    T ff[4] = {f[0], f[1], f[2], f[3]};
+    emit(T(1), d, ff);
+    return;
+  }
   Vt<T> V[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) V[i] = Vt<T>{a[i], b[i] - a[i], f[i]};
-  Vt<T> P1[3][4];
-  T r1[3];
-  const int n1 = carve_pieces<0>(V, P1, r1);
-  // unrolled with static indices so the pieces stay in registers
-#pragma unroll
+#pragma unroll 1
   for (int i1 = 0; i1 < 3; ++i1) {
-    if (i1 >= n1 || r1[i1] <= T(0)) continue;
-    Vt<T> P2[3][4];
-    T r2[3];
-    const int n2 = carve_pieces<1>(P1[i1], P2, r2);
-#pragma unroll
+    Vt<T> P[4];
+    T r1 = T(0);
+    const int n1 = cut_piece<0>(V, i1, P, r1);
+    if (i1 >= n1) break;
+    if (r1 <= T(0)) continue;
+#pragma unroll 1
     for (int i2 = 0; i2 < 3; ++i2) {
-      if (i2 >= n2) continue;
-      const T r = r1[i1] * r2[i2];
+      Vt<T> Qv[4];
+      T r2 = T(0);
+      const int n2 = cut_piece<1>(P, i2, Qv, r2);
+      if (i2 >= n2) break;
+      const T r = r1 * r2;
       if (r <= T(0)) continue;
       T d[4], ff[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const T dd = P2[i2][i].D;
+        const T dd = Qv[i].D;
         d[i] = dd > T(0) ? dd : T(0);
-        ff[i] = P2[i2][i].f;
+        ff[i] = Qv[i].f;
       }
       emit(r, d, ff);
     }

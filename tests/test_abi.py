@@ -47,7 +47,7 @@ def test_struct_layouts_match_header(lib):
 def test_opts_default(lib):
     o = lib.chi0_opts_default()
     assert o.precision == lib.CHI0_PREC_FP64 and o.sign == lib.CHI0_SIGN_POSITIVE
-    assert o.cma == 0 and abs(o.tau - 2.0 ** -10) < 1e-15 and o.inputs_on_device == 0
+    assert o.cma == 0 and abs(o.tau - 2.0 ** -20) < 1e-18 and o.inputs_on_device == 0
     assert lib.chi0_version() >= 100
 
 
