@@ -37,7 +37,12 @@ struct chi0_plan {
   unsigned long long *counters_d = nullptr;
   short *occ_d = nullptr, *emp_d = nullptr, *occq_d = nullptr, *empq_d = nullptr;
   float *E32_d = nullptr, *Eq32_d = nullptr;  // energies - eF in FP32 (mixed precision)
-  int *next_d = nullptr;                      // batch counter of the persistent kernels
+  void *C32_d = nullptr;                      // complex64 copy of complex128 eigenvectors (mixed)
+  int *next_d = nullptr;                      // [2] batch counter, FP64 list size
+  void *tq_d = nullptr;                       // queued final tetrahedra per batch
+  int *tq_n_d = nullptr, *list64_d = nullptr;
+  double *res64_d = nullptr;
+  int cap64 = 0;
   int static_grid = 0;
   size_t part_cap = 0;
   chi0_stats_t stats;
@@ -110,8 +115,13 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->empq_d);
   cudaFree(p->occq_d);
   cudaFree(p->E32_d);
+  cudaFree(p->C32_d);
   cudaFree(p->Eq32_d);
   cudaFree(p->next_d);
+  cudaFree(p->tq_d);
+  cudaFree(p->tq_n_d);
+  cudaFree(p->list64_d);
+  cudaFree(p->res64_d);
 }
 
 extern "C" void chi0_destroy(chi0_plan_t *p) {
@@ -208,7 +218,7 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     CK(p, cudaMalloc(&p->W2_d, es * (size_t)g.nc * w * w));
   }
   const size_t np = (size_t)dynamic_blocks(dynamic_max_nw()) * dynamic_max_nw();
-  size_t ns = (size_t)static_batches(g.ntet);
+  size_t ns = 2 * (size_t)static_batches(g.ntet);
   if (ns < (size_t)static_blocks()) ns = (size_t)static_blocks();
   p->part_cap = np > ns ? np : ns;
   CK(p, cudaMalloc(&p->partR, sizeof(double) * p->part_cap));
@@ -220,12 +230,31 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
   CK(p, cudaMalloc(&p->emp_d, sizeof(short) * g.nc));
   CK(p, cudaMalloc(&p->empq_d, sizeof(short) * g.nc));
   CK(p, cudaMalloc(&p->occq_d, sizeof(short) * g.nc));
-  CK(p, cudaMalloc(&p->next_d, sizeof(int)));
+  CK(p, cudaMalloc(&p->next_d, 2 * sizeof(int)));
+  {
+    const long long nbatch = static_batches(g.ntet);
+    const int fp64 = op.precision == CHI0_PREC_FP64;
+    CK(p, cudaMalloc(&p->tq_d, static_piece_bytes(fp64) * (size_t)nbatch * static_tab_cap()));
+    CK(p, cudaMalloc(&p->tq_n_d, sizeof(int) * (size_t)nbatch));
+    p->cap64 = (int)(nbatch * 8 < (1 << 22) ? (nbatch * 8 > 4096 ? nbatch * 8 : 4096) : (1 << 22));
+    CK(p, cudaMalloc(&p->list64_d, sizeof(int) * (size_t)p->cap64));
+    CK(p, cudaMalloc(&p->res64_d, sizeof(double) * (size_t)p->cap64));
+  }
   if (op.precision == CHI0_PREC_MIXED) {
     CK(p, cudaMalloc(&p->E32_d, sizeof(float) * (size_t)g.nc * g.nb));
     CK(p, cudaMalloc(&p->Eq32_d, sizeof(float) * (size_t)g.nc * g.nb));
   }
   CK(p, launch_bands(p->E_d, g.nc, g.nb, g.ef, p->occ_d, p->emp_d, p->E32_d, p->stream));
+  if (op.precision == CHI0_PREC_MIXED && !op.cma && p->dtype == CHI0_C128) {
+    const long long ne = g.nc * (long long)g.norb * g.nb;
+    CK(p, cudaMalloc(&p->C32_d, 8 * (size_t)ne));
+    CK(p, launch_c128_to_c64(p->C_d, p->C32_d, ne, p->stream));
+  }
+  g.fn1 = make_fastdiv((unsigned)g.n[1]);
+  g.fn2 = make_fastdiv((unsigned)g.n[2]);
+  g.fN1 = make_fastdiv((unsigned)g.N[1]);
+  g.fN2 = make_fastdiv((unsigned)g.N[2]);
+  if (g.ntet >= (1LL << 31)) return fail(p, CHI0_EINVAL, "more than 2^31 tetrahedra");
   p->static_grid = static_persistent_blocks(op.precision == CHI0_PREC_FP64);
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, p->stream));
   CK(p, cudaStreamSynchronize(p->stream));
@@ -381,7 +410,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     if (rc) return rc;
     if (!op.cma) {
       tm.start(CHI0_K_OVERLAP);
-      CK(p, launch_overlap(p->g, p->E_d, p->C_d, p->dtype, q, p->W2_d, fp64, s));
+      CK(p, launch_overlap(p->g, p->E_d, p->C_d, p->dtype, q, p->W2_d, fp64, s, p->C32_d));
       tm.stop();
     }
     const int ndos = static_blocks();
@@ -402,12 +431,13 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
         empq = p->empq_d;
         Ekq = fp64 ? (const void *)q.Eq : (const void *)p->Eq32_d;
       }
+      StaticBufs sb{p->tq_d, p->tq_n_d, p->list64_d, p->res64_d, p->cap64, p->partR, p->next_d};
       tm.start(CHI0_K_STATIC);
-      CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
-                          p->partR, p->next_d, p->static_grid, p->counters_d, s));
+      CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq, sb,
+                          p->static_grid, p->counters_d, s));
       tm.stop();
       tm.start(CHI0_K_REDUCE);
-      CK(p, launch_reduce(p->partR, nb, 1, scale, q.gamma ? p->dos_d : nullptr, ndos, nullptr, outR + iq, s));
+      CK(p, launch_reduce(p->partR, 2 * nb, 1, scale, q.gamma ? p->dos_d : nullptr, ndos, nullptr, outR + iq, s));
       tm.stop();
     } else {
       const int maxw = dynamic_max_nw();

@@ -6,14 +6,38 @@
 
 namespace chi0int {
 
+// n / d for 32-bit unsigned n by a multiply-high and shifts (Granlund-Montgomery): no
+// integer-division sequence and no int<->float conversions in the index arithmetic.
+struct FastDiv {
+  unsigned d, m, s;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f{d, 0u, 0u};
+  if (d <= 1) return f;
+  unsigned l = 0;
+  while ((1ull << l) < d) ++l;                                   // l = ceil(log2 d)
+  f.m = (unsigned)((((1ull << l) - d) << 32) / d + 1);           // floor(2^32 (2^l - d)/d) + 1
+  f.s = l - 1;
+  return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f) {
+  if (f.d <= 1) return n;
+  const unsigned t = __umulhi(n, f.m);
+  return (t + ((n - t) >> 1)) >> f.s;
+}
+#endif
+
 struct Grid {
   int n[3];   // cubes per axis
   int N[3];   // corners per axis
   int periodic;
   int nb, norb;
-  long long nc;    // corners
-  long long ntet;  // tetrahedra
+  long long nc;    // corners (< 2^31, checked when the plan is built)
+  long long ntet;  // tetrahedra (< 2^31)
   double ef;
+  FastDiv fn1, fn2;  // cube index decode: n1, n2
+  FastDiv fN1, fN2;  // corner index decode: N1, N2
 };
 
 struct Tet {
@@ -35,22 +59,36 @@ enum { DT_C64 = 1, DT_C128 = 2 };
 
 // |M_mn|^2 at every k corner for one q: W2[c][m-lo][n-lo] (fp64: double, else float)
 cudaError_t launch_overlap(const Grid &g, const double *E, const void *C, int dtype, const Q &q,
-                           void *W2, int fp64, cudaStream_t s);
+                           void *W2, int fp64, cudaStream_t s, const void *C32);
+// complex128 -> complex64 copy (the k-side eigenvectors of a mixed-precision plan)
+cudaError_t launch_c128_to_c64(const void *in, void *out, long long n, cudaStream_t s);
 
 // band bounds per corner: occ[c] (1 + highest occupied band), emp[c] (lowest empty band);
 // E32 (optional) receives (float)(E - ef)
 cudaError_t launch_bands(const double *E, long long nc, int nb, double ef, short *occ, short *emp, float *E32,
                          cudaStream_t s);
 
-// static weights: one FP64 partial per batch of 32 tetrahedra into partial[static_batches];
-// Ek/Ekq are the absolute FP64 energies (fp64) or the FP32 energies relative to eF (mixed);
-// occ from the k energies, empq from the k+q energies; next: a device int (batch counter)
+// Work buffers of the static kernels (device memory owned by the plan).
+struct StaticBufs {
+  void *tq;        // queued final tetrahedra: [nbatch][static_tab_cap()] pieces
+  int *tq_n;       // [nbatch] queued per batch
+  int *list64;     // FP64-branch list: queue positions
+  double *res64;   // FP64-branch results
+  int cap64;       // list capacity
+  double *partial; // [2 * nbatch]: series part, queued part
+  int *next;       // [2]: batch counter, FP64 list size
+};
+
+// static weights for one q: partial[2 * nbatch] (sum them for chi0); Ek/Ekq are the absolute
+// FP64 energies (fp64) or the FP32 energies relative to eF (mixed); occ from the k
+// energies, empq from the k+q energies
 cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
-                          double *partial, int *next, int nblocks, unsigned long long *counters,
-                          cudaStream_t s);
+                          const StaticBufs &sb, int nblocks, unsigned long long *counters, cudaStream_t s);
 int static_persistent_blocks(int fp64);
 long long static_batches(long long ntet);
+int static_tab_cap();
+size_t static_piece_bytes(int fp64);
 
 // dynamic weights: partialR/partialI [nblocks][nw]
 cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const double *E, const Q &q, const void *W2,

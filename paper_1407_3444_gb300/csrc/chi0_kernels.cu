@@ -32,23 +32,58 @@ constexpr int kDynBlocks = kSMs * 4;
 constexpr int kNWPass = 256;  // frequencies per dynamic pass (shared-memory accumulators)
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ long long wrap(int i, int N) { return i >= N ? i - N : i; }
+__device__ __forceinline__ int wrap(int i, int N) { return i >= N ? i - N : i; }
 
+// corner index (32-bit: the plan checks that the mesh has fewer than 2^31 corners)
 __device__ __forceinline__ long long cid(const Grid &g, int i0, int i1, int i2) {
   if (g.periodic) {
-    i0 = (int)wrap(i0, g.N[0]);
-    i1 = (int)wrap(i1, g.N[1]);
-    i2 = (int)wrap(i2, g.N[2]);
+    i0 = wrap(i0, g.N[0]);
+    i1 = wrap(i1, g.N[1]);
+    i2 = wrap(i2, g.N[2]);
   }
-  return ((long long)i0 * g.N[1] + i1) * g.N[2] + i2;
+  return (long long)(unsigned)((i0 * g.N[1] + i1) * g.N[2] + i2);
 }
 
 __device__ __forceinline__ long long shift_corner(const Grid &g, long long c, const int s[3]) {
-  const int i2 = (int)(c % g.N[2]);
-  const int i1 = (int)((c / g.N[2]) % g.N[1]);
-  const int i0 = (int)(c / ((long long)g.N[2] * g.N[1]));
-  return cid(g, i0 + s[0], i1 + s[1], i2 + s[2]);
+  const unsigned cu = (unsigned)c;
+  const unsigned r = fdiv(cu, g.fN2);
+  const int i2 = (int)(cu - r * (unsigned)g.N[2]);
+  const unsigned i0 = fdiv(r, g.fN1);
+  const int i1 = (int)(r - i0 * (unsigned)g.N[1]);
+  return cid(g, (int)i0 + s[0], i1 + s[1], i2 + s[2]);
 }
+
+// x / d for 0 <= x < qmax * d (small quotients): binary search, no division sequence
+__device__ __forceinline__ int div_small(int x, int d, int qmax) {
+  int lo = 0, hi = qmax;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (mid * d <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// double -> float rounded to nearest even by integer operations (keeps the conversion of
+// complex128 inputs off the FP64 pipe); magnitudes below 2^-126 flush to zero
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u | (((u << 12) != 0ull && e > 1000) ? 0x400000u : 0u));
+  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  unsigned m = (unsigned)(mant >> 29);
+  const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
+  m += (rem > 0x10000000u) | ((rem == 0x10000000u) & (m & 1u));
+  return __uint_as_float(sign | (((unsigned)e << 23) + m));  // a mantissa carry rounds into the exponent
+}
+
+template <typename T> __device__ __forceinline__ T cvt(double x);
+template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt<float>(double x) { return d2f_int(x); }
+template <typename T> __device__ __forceinline__ T cvt(float x) { return (T)x; }
 
 // Corners of tetrahedron t at k and at k+q, and its fractional volume.  Builtin mesh:
 // tetrahedron 6*cube + p = {000, e_a, e_a + e_b, 111} for the p-th axis order (a, b, .)
@@ -62,11 +97,14 @@ __device__ __forceinline__ void tet_corners(const Grid &g, const Tet &tet, const
     for (int i = 0; i < 4; ++i) cq[i] = q.Eq ? c[i] : shift_corner(g, c[i], q.shift);
     return;
   }
-  const long long cube = t / 6;
-  const int p = (int)(t - cube * 6);
-  const int i2 = (int)(cube % g.n[2]);
-  const int i1 = (int)((cube / g.n[2]) % g.n[1]);
-  const int i0 = (int)(cube / ((long long)g.n[2] * g.n[1]));
+  const unsigned tu = (unsigned)t;
+  const unsigned cube = tu / 6u;
+  const int p = (int)(tu - cube * 6u);
+  const unsigned r = fdiv(cube, g.fn2);
+  const int i2 = (int)(cube - r * (unsigned)g.n[2]);
+  const unsigned i0u = fdiv(r, g.fn1);
+  const int i1 = (int)(r - i0u * (unsigned)g.n[1]);
+  const int i0 = (int)i0u;
   const int ax = p >> 1;                                // first axis: 0,0,1,1,2,2
   const int bx = (p == 0) ? 1 : (p == 1) ? 2 : (p == 2) ? 0 : (p == 3) ? 2 : (p == 4) ? 0 : 1;
   int o1[3] = {0, 0, 0}, o2[3] = {0, 0, 0};
@@ -186,24 +224,23 @@ __global__ void __launch_bounds__(kThreads) k_overlap(Grid g, const CT *__restri
 // C_k[:, lo:hi] and C_{k+q}[:, lo:hi] are read once, coalesced, into shared memory in
 // the arithmetic precision, then the lanes form the w x w |overlap|^2 block.
 constexpr int kOvlSmall = 256;
-template <typename CT, typename T>
+template <typename CT, typename CTq, typename T>
 __global__ void __launch_bounds__(kThreads) k_overlap_small(Grid g, const CT *__restrict__ C,
-                                                             const CT *__restrict__ Cqx, Q q,
+                                                             const CTq *__restrict__ Cb, int explicit_q, Q q,
                                                              T *__restrict__ W2) {
   __shared__ T sA[kWarps][2][kOvlSmall], sB[kWarps][2][kOvlSmall];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = q.hi - q.lo, no = g.norb, nel = no * w;
-  const CT *Cb = Cqx ? Cqx : C;
   for (long long c = (long long)blockIdx.x * kWarps + wib; c < g.nc; c += (long long)gridDim.x * kWarps) {
-    const long long ck = Cqx ? c : shift_corner(g, c, q.shift);
+    const long long ck = explicit_q ? c : shift_corner(g, c, q.shift);
     for (int i = lane; i < nel; i += 32) {
       const int o = i / w, mm = i - o * w;
       const CT x = C[(c * no + o) * g.nb + q.lo + mm];
-      const CT y = Cb[(ck * no + o) * g.nb + q.lo + mm];
-      sA[wib][0][i] = (T)x.x;
-      sA[wib][1][i] = (T)x.y;
-      sB[wib][0][i] = (T)y.x;
-      sB[wib][1][i] = (T)y.y;
+      const CTq y = Cb[(ck * no + o) * g.nb + q.lo + mm];
+      sA[wib][0][i] = cvt<T>(x.x);
+      sA[wib][1][i] = cvt<T>(x.y);
+      sB[wib][0][i] = cvt<T>(y.x);
+      sB[wib][1][i] = cvt<T>(y.y);
     }
     __syncwarp();
     for (int out = lane; out < w * w; out += 32) {
@@ -243,18 +280,21 @@ __global__ void __launch_bounds__(kThreads) k_bands(const double *__restrict__ E
 }
 
 // ---------------------------------------------------------------- static weights
-// Persistent warps take batches of 32 tetrahedra from an atomic counter.  A batch's
-// (m, n) rectangles are flattened into one item list shared by the lanes.  Final
-// tetrahedra whose knots fit the series branch are evaluated where they are produced;
-// the others (knots spanning a wide range, e.g. D = 0 vertices) are queued in shared
-// memory and evaluated 32 at a time by the whole warp.  Every batch writes its own
-// partial sum, so the result does not depend on which warp took which batch.
-template <typename T> struct QCap {
-  static constexpr int value = sizeof(T) == 8 ? 32 : 64;  // queue entries per warp
-};
+// Three kernels per q:
+//  k_static      persistent warps take batches of 32 tetrahedra from an atomic counter; a
+//                batch's (m, n) rectangles are flattened into one item list shared by the
+//                lanes; carving; final tetrahedra whose knots fit the short series are
+//                evaluated on the spot (compact hot loop), the others are queued in the
+//                batch's region of a global queue (FP64-branch ones also in a compact list)
+//  k_static_f64  (mixed precision) the FP64-branch list, full warps of FP64
+//  k_static_tab  one warp per batch region: long series or divided-difference table
+// Every batch has its own partial sums (series part, queued part), added in a fixed
+// order, so the result does not depend on which warp took which batch.
+constexpr int kTabCap = 64;  // queued final tetrahedra per batch
 
 template <typename T> struct Piece {
   T d[4], f[4], w;
+  int i64;  // index in the FP64 list, -1 if none
 };
 
 // compensated (Neumaier) accumulator in the kernel's precision
@@ -269,23 +309,18 @@ template <typename T> struct Acc {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// a queued piece evaluated where it is (only when its batch region is full)
 template <bool FP64>
-__device__ __noinline__ typename std::conditional<FP64, double, float>::type table_eval(
-    const Piece<typename std::conditional<FP64, double, float>::type> &pc, float tau, int &nfp64) {
+__device__ __noinline__ double piece_eval(const Piece<typename std::conditional<FP64, double, float>::type> &pc,
+                                          float tau, int &nfp64) {
   if constexpr (FP64) {
     return pc.w * inv_sum_table(pc.d, pc.f);
   } else {
-    const float s = fmaxf(fabsf(pc.d[0]), fabsf(pc.d[3]));
-    float g = s;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float gi = pc.d[i + 1] - pc.d[i];
-      if (gi > 0.0f) g = fminf(g, gi);  // exact ties (two D = 0 vertices) are exact in FP32
-    }
-    if (g >= tau * s) return pc.w * inv_sum_table(pc.d, pc.f);
-    ++nfp64;  // near-degenerate knots: the table in FP64
-    double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
-    return pc.w * (float)inv_sum_table(xd, fd);
+    float x[4];
+    if (!mixed_knots(x, pc.d, tau)) return (double)(pc.w * inv_sum_long(x, pc.f));
+    ++nfp64;
+    double xd[4] = {x[0], x[1], x[2], x[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
+    return (double)pc.w * inv_sum_table(xd, fd);
   }
 }
 
@@ -298,43 +333,28 @@ __device__ __noinline__ typename std::conditional<FP64, double, float>::type tab
 #endif
 
 template <bool FP64>
-__global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_STATIC_MINB_F32) k_static(Grid g, Tet tet, const void *__restrict__ Ek,
-                                                      const void *__restrict__ Ekq, Q q,
-                                                      const void *__restrict__ W2, int cma, float tau,
-                                                      const short *__restrict__ occ,
-                                                      const short *__restrict__ empq,
-                                                      double *__restrict__ partial, int *__restrict__ next,
-                                                      unsigned long long *__restrict__ counters) {
+__global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_STATIC_MINB_F32)
+    k_static(Grid g, Tet tet, const void *__restrict__ Ek, const void *__restrict__ Ekq, Q q,
+             const void *__restrict__ W2, int cma, float tau, const short *__restrict__ occ,
+             const short *__restrict__ empq, StaticBufs sb, unsigned long long *__restrict__ counters) {
   using T = typename std::conditional<FP64, double, float>::type;
-  constexpr int kQCap = QCap<T>::value;
   __shared__ int s_c[kWarps][32][4], s_cq[kWarps][32][4];
   __shared__ T s_vol[kWarps][32];
   __shared__ int s_nlo[kWarps][32], s_nn[kWarps][32], s_pre[kWarps][33];
-  __shared__ Piece<T> s_q[kWarps][kQCap];
   __shared__ int s_qn[kWarps];
+  Piece<T> *tq = (Piece<T> *)sb.tq;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = q.hi - q.lo;
   const long long nbatch = (g.ntet + 31) / 32;
   int nfp64 = 0, npieces = 0;
-  if (lane == 0) s_qn[wib] = 0;
-  __syncwarp();
   for (;;) {
     int batch = 0;
-    if (lane == 0) batch = atomicAdd(next, 1);
+    if (lane == 0) batch = atomicAdd(sb.next, 1);
     batch = __shfl_sync(kFull, batch, 0);
     if (batch >= nbatch) break;
+    if (lane == 0) s_qn[wib] = 0;
     Acc<T> acc;
-    auto drain = [&](bool all) {
-      for (;;) {
-        const int qn = s_qn[wib];
-        if (qn == 0 || (!all && qn < 32)) break;
-        const int take = qn < 32 ? qn : 32;
-        if (lane < take) acc.add(table_eval<FP64>(s_q[wib][qn - take + lane], tau, nfp64));
-        __syncwarp();
-        if (lane == 0) s_qn[wib] = qn - take;
-        __syncwarp();
-      }
-    };
+    double acc_q = 0.0;  // pieces evaluated in place when the batch region is full
     // one tetrahedron per lane: corners, volume, band rectangle
     const long long t = (long long)batch * 32 + lane;
     int cnt = 0;
@@ -368,71 +388,83 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
     if (lane == 0) s_pre[wib][0] = 0;
     const int total = __shfl_sync(kFull, pre, 31);
     __syncwarp();
-    for (int base = 0; base < total; base += 32) {
-      const int it = base + lane;
-      if (it < total) {
-        int lo_ = 0, hi_ = 32;  // owner: largest l with s_pre[l] <= it
+    for (int it = lane; it < total; it += 32) {
+      int lo_ = 0, hi_ = 32;  // owner: largest l with s_pre[l] <= it
 #pragma unroll
-        for (int step = 0; step < 5; ++step) {
-          const int mid = (lo_ + hi_) >> 1;
-          if (s_pre[wib][mid] <= it) lo_ = mid;
-          else hi_ = mid;
-        }
-        const int l = lo_;
-        const int loc = it - s_pre[wib][l];
-        const int nn = s_nn[wib][l];
-        const int m = q.lo + loc / nn, n = s_nlo[wib][l] + loc % nn;
-        if (!(q.gamma && m == n)) {  // intraband at Gamma: replaced by the DOS limit
-          T a[4], b[4], f[4];
-          T amin = T(1e30), bmax = T(-1e30);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
-            if constexpr (FP64) {
-              a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
-              b[i] = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
-            } else {
-              a[i] = ((const float *)Ek)[(long long)ck * g.nb + m];
-              b[i] = ((const float *)Ekq)[(long long)cq * g.nb + n];
-            }
-            amin = a[i] < amin ? a[i] : amin;
-            bmax = b[i] > bmax ? b[i] : bmax;
-          }
-          if (amin < T(0) && bmax > T(0)) {
-            const T *W2t = (const T *)W2;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
-            const T vol2 = s_vol[wib][l];
-            carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) {
-              sort4(d, ff);
-              ++npieces;
-              if (series_ok(d, T(Num<T>::kappa))) {
-                acc.add(vol2 * r * series_sum(d, ff));
-              } else {
-                const int slot = atomicAdd(&s_qn[wib], 1);
-                Piece<T> pc;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                  pc.d[i] = d[i];
-                  pc.f[i] = ff[i];
-                }
-                pc.w = vol2 * r;
-                if (slot < kQCap) s_q[wib][slot] = pc;
-                else acc.add(table_eval<FP64>(pc, tau, nfp64));  // queue full: evaluate in place
-              }
-            });
-          }
-        }
+      for (int step = 0; step < 5; ++step) {
+        const int mid = (lo_ + hi_) >> 1;
+        if (s_pre[wib][mid] <= it) lo_ = mid;
+        else hi_ = mid;
       }
-      __syncwarp();
-      if (lane == 0 && s_qn[wib] > kQCap) s_qn[wib] = kQCap;
-      __syncwarp();
-      drain(false);
+      const int l = lo_;
+      const int loc = it - s_pre[wib][l];
+      const int nn = s_nn[wib][l];
+      const int mo = div_small(loc, nn, q.hi - q.lo);
+      const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
+      if (q.gamma && m == n) continue;  // intraband at Gamma: replaced by the DOS limit
+      T a[4], b[4], f[4];
+      T amin = T(1e30), bmax = T(-1e30);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
+        if constexpr (FP64) {
+          a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
+          b[i] = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
+        } else {
+          a[i] = ((const float *)Ek)[(long long)ck * g.nb + m];
+          b[i] = ((const float *)Ekq)[(long long)cq * g.nb + n];
+        }
+        amin = a[i] < amin ? a[i] : amin;
+        bmax = b[i] > bmax ? b[i] : bmax;
+      }
+      if (!(amin < T(0) && bmax > T(0))) continue;
+      const T *W2t = (const T *)W2;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
+      const T vol2 = s_vol[wib][l];
+      carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) {
+        sort4(d, ff);
+        ++npieces;
+        if (series_ok(d, T(Num<T>::kappa))) {
+          acc.add(vol2 * r * series_sum(d, ff));
+          return;
+        }
+        Piece<T> pc;
+        int fp = 0;
+        if constexpr (FP64) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) pc.d[i] = d[i];
+        } else {
+          fp = mixed_knots(pc.d, d, tau) ? 1 : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pc.f[i] = ff[i];
+        pc.w = vol2 * r;
+        pc.i64 = -1;
+        const int slot = atomicAdd(&s_qn[wib], 1);
+        if (slot < kTabCap) {
+          if (fp) {
+            const int idx = atomicAdd(sb.next + 1, 1);
+            if (idx < sb.cap64) {
+              pc.i64 = idx;
+              sb.list64[idx] = batch * kTabCap + slot;
+              ++nfp64;
+            }
+          }
+          tq[(long long)batch * kTabCap + slot] = pc;
+        } else {
+          acc_q += piece_eval<FP64>(pc, tau, nfp64);
+        }
+      });
     }
-    drain(true);  // this batch's pieces stay in this batch's sum
-    const double v = warp_sum(acc.value());
-    if (lane == 0) partial[batch] = v;
+    __syncwarp();
+    const double v = warp_sum(acc.value() + acc_q);
+    if (lane == 0) {
+      sb.partial[batch] = v;
+      sb.tq_n[batch] = min(s_qn[wib], kTabCap);
+    }
+    __syncwarp();
   }
   if (counters) {
     unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64;
@@ -445,6 +477,40 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
       atomicAdd(&counters[0], a);
       atomicAdd(&counters[1], b);
     }
+  }
+}
+
+// FP64 branch of the mixed path: every listed piece's table in FP64, full warps
+__global__ void __launch_bounds__(kThreads) k_static_f64(StaticBufs sb) {
+  const Piece<float> *tq = (const Piece<float> *)sb.tq;
+  const int n = min(sb.next[1], sb.cap64);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const Piece<float> pc = tq[sb.list64[i]];
+    double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
+    sb.res64[i] = (double)pc.w * inv_sum_table(xd, fd);
+  }
+}
+
+// one warp per batch region: queued pieces in slot order
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, StaticBufs sb) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  const Piece<T> *tq = (const Piece<T> *)sb.tq;
+  const int lane = threadIdx.x & 31;
+  for (long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbatch;
+       b += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int n = sb.tq_n[b];
+    double acc = 0.0;
+    for (int slot = lane; slot < n; slot += 32) {
+      const Piece<T> pc = tq[b * kTabCap + slot];
+      if constexpr (FP64) {
+        acc += pc.w * inv_sum_table(pc.d, pc.f);
+      } else {
+        acc += pc.i64 >= 0 ? sb.res64[pc.i64] : (double)(pc.w * inv_sum_long(pc.d, pc.f));
+      }
+    }
+    const double v = warp_sum(acc);
+    if (lane == 0) sb.partial[nbatch + b] = v;
   }
 }
 
@@ -593,8 +659,21 @@ int static_blocks() { return kStaticBlocks; }
 int dynamic_blocks(int) { return kDynBlocks; }
 int dynamic_max_nw() { return kNWPass; }
 
+__global__ void __launch_bounds__(kThreads) k_c128_to_c64(const double2 *__restrict__ in, float2 *__restrict__ out,
+                                                         long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+cudaError_t launch_c128_to_c64(const void *in, void *out, long long n, cudaStream_t s) {
+  k_c128_to_c64<<<kSMs * 8, kThreads, 0, s>>>((const double2 *)in, (float2 *)out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_overlap(const Grid &g, const double *, const void *C, int dtype, const Q &q, void *W2,
-                           int fp64, cudaStream_t s) {
+                           int fp64, cudaStream_t s, const void *C32) {
   const int w = q.hi - q.lo;
   const long long total = g.nc * (long long)w * w;
   long long nb = (total + kThreads - 1) / kThreads;
@@ -602,14 +681,18 @@ cudaError_t launch_overlap(const Grid &g, const double *, const void *C, int dty
   if (blocks <= 0) return cudaSuccess;
   const bool small = (long long)g.norb * w <= kOvlSmall && !fp64;
   if (small) {
+    // k side in complex64 (the plan's copy when the inputs are complex128)
+    const float2 *Ck = (const float2 *)(C32 ? C32 : C);
     long long nbw = (g.nc + kWarps - 1) / kWarps;
     const int bw = (int)(nbw < kSMs * 8 ? nbw : kSMs * 8);
-    if (dtype == DT_C128)
-      k_overlap_small<double2, float><<<bw, kThreads, 0, s>>>(g, (const double2 *)C, (const double2 *)q.Cq, q,
-                                                              (float *)W2);
+    if (q.Cq && dtype == DT_C128)
+      k_overlap_small<float2, double2, float><<<bw, kThreads, 0, s>>>(g, Ck, (const double2 *)q.Cq, 1, q,
+                                                                      (float *)W2);
+    else if (q.Cq)
+      k_overlap_small<float2, float2, float><<<bw, kThreads, 0, s>>>(g, Ck, (const float2 *)q.Cq, 1, q,
+                                                                     (float *)W2);
     else
-      k_overlap_small<float2, float><<<bw, kThreads, 0, s>>>(g, (const float2 *)C, (const float2 *)q.Cq, q,
-                                                             (float *)W2);
+      k_overlap_small<float2, float2, float><<<bw, kThreads, 0, s>>>(g, Ck, Ck, 0, q, (float *)W2);
     return cudaGetLastError();
   }
   if (dtype == DT_C128) {
@@ -643,19 +726,28 @@ int static_persistent_blocks(int fp64) {
 }
 
 long long static_batches(long long ntet) { return (ntet + 31) / 32; }
+int static_tab_cap() { return kTabCap; }
+size_t static_piece_bytes(int fp64) { return fp64 ? sizeof(Piece<double>) : sizeof(Piece<float>); }
 
 cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
-                          double *partial, int *next, int nblocks, unsigned long long *counters,
-                          cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), s);
+                          const StaticBufs &sb, int nblocks, unsigned long long *counters, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sb.next, 0, 2 * sizeof(int), s);  // batch counter, FP64 list size
   if (e != cudaSuccess) return e;
+  const long long nbatch = static_batches(g.ntet);
   if (fp64)
-    k_static<true><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, partial, next,
-                                                 counters);
+    k_static<true><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
   else
-    k_static<false><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, partial, next,
-                                                  counters);
+    k_static<false><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!fp64) {
+    k_static_f64<<<kSMs * 4, kThreads, 0, s>>>(sb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  long long tb = (nbatch * 32 + kThreads - 1) / kThreads;
+  const int tblocks = (int)(tb < kSMs * 16 ? tb : kSMs * 16);
+  if (fp64) k_static_tab<true><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
+  else k_static_tab<false><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
   return cudaGetLastError();
 }
 

@@ -37,13 +37,15 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double lg(double x) { return log(x); }
   static constexpr double tol = 1e-17;
   static constexpr double kappa = 0.25;  // series branch: (x3 - x0) <= kappa (x3 + x0)
+  static constexpr double kappa_long = 0.25;
   static constexpr int kmax = 80;
 };
 template <> struct Num<float> {
   static __device__ __forceinline__ float lg(float x) { return logf(x); }
   static constexpr float tol = 2e-8f;
-  static constexpr float kappa = 0.5f;
-  static constexpr int kmax = 40;
+  static constexpr float kappa = 0.5f;       // series branch inside the carving loop
+  static constexpr float kappa_long = 0.7f;  // series branch of queued pieces (evaluated together)
+  static constexpr int kmax = 64;
 };
 
 template <typename T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
@@ -259,19 +261,37 @@ template <typename T> __device__ __forceinline__ T inv_sum(const T x[4], const T
   return inv_sum_table(x, f);
 }
 
-// mixed precision: FP32 series / table; the table in FP64 when the sorted knots have an
-// inner gap below tau times their scale (sub-clusters, where FP32 differences cancel).
-__device__ __forceinline__ float inv_sum_mixed(const float x[4], const float f[4], float tau,
-                                               int *fp64) {
-  if (series_ok(x, Num<float>::kappa)) return series_sum(x, f);
-  const float s = fmaxf(fabsf(x[0]), fabsf(x[3]));
+// Mixed precision, knots of a final tetrahedron that missed the short series: the D = 0
+// value of a vertex on both cut planes, interpolated in FP32 along different edges, comes
+// out at the FP32 noise level of the corner energies instead of 0, so knots below 2^-20 of
+// the largest are set to exactly 0 (the piece's integral moves by ~1e-5 relative; such
+// pieces are a few in 10^4).  Returns true when the sorted knots keep an inner gap below
+// tau times their scale (the near-degenerate case evaluated in FP64).
+constexpr float kZeroSnap = 9.5367431640625e-07f;  // 2^-20
+__device__ __forceinline__ bool mixed_knots(float x[4], const float d[4], float tau) {
+  const float s = fmaxf(fabsf(d[0]), fabsf(d[3]));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = fabsf(d[i]) < kZeroSnap * s ? 0.0f : d[i];
   float g = s;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float gi = x[i + 1] - x[i];
-    if (gi > 0.0f) g = fminf(g, gi);  // exact ties (e.g. two zero knots) are exact in the table
+    if (gi > 0.0f) g = fminf(g, gi);  // exact ties (e.g. two D = 0 vertices) are exact in FP32
   }
-  if (g >= tau * s) return inv_sum_table(x, f);
+  return g < tau * s;
+}
+
+// FP32 evaluation of queued knots: the long series where it converges, else the table
+__device__ __forceinline__ float inv_sum_long(const float x[4], const float f[4]) {
+  if (series_ok(x, Num<float>::kappa_long)) return series_sum(x, f);
+  return inv_sum_table(x, f);
+}
+
+// mixed precision, all branches in one place (dynamic kernel)
+__device__ __forceinline__ float inv_sum_mixed(const float d[4], const float f[4], float tau, int *fp64) {
+  if (series_ok(d, Num<float>::kappa)) return series_sum(d, f);
+  float x[4];
+  if (!mixed_knots(x, d, tau)) return inv_sum_long(x, f);
   ++*fp64;
   double xd[4] = {x[0], x[1], x[2], x[3]}, fd[4] = {f[0], f[1], f[2], f[3]};
   return (float)inv_sum_table(xd, fd);
