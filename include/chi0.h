@@ -198,6 +198,33 @@ int chi0_static(chi0_plan_t *plan, const chi0_q_t *q, int nq, double *chi);
 int chi0_dynamic(chi0_plan_t *plan, const chi0_q_t *q, int nq, const double *omega, int nw,
                  double *re, double *im);
 
+/* Static chi0 without any device allocation (the paper has no counterpart: this is a
+ * deployment variant of chi0_static).
+ *
+ * For callers that cannot call cudaMalloc where they need chi0: cudaMalloc/cudaFree can
+ * synchronize the device and take unbounded time, which a real-time loop or a step with a
+ * latency budget cannot afford, and some applications give all device memory to their own
+ * pool allocator, which must account for every byte.  Such callers keep inputs and outputs
+ * in memory they already own; this call uses a fixed work array inside the library instead.
+ *
+ *   kgrid  as for chi0_plan, but energies/evecs are DEVICE pointers; builtin tetrahedra.
+ *   window band window [lo, hi) for m and n.
+ *   opts   precision, cma, sign, tau, stream are used (inputs/outputs are always device).
+ *   q[nq]  as for chi0_static; e_kq/c_kq, when given, are DEVICE pointers.
+ *   chi    DEVICE pointer, [nq] results (same values as chi0_static on the same inputs).
+ * Work memory: one array of CHI0_NOALLOC_SCRATCH_BYTES compiled into the library; every
+ * GPU that loads the library holds it until the process exits.  A mesh whose work buffers
+ * do not fit returns CHI0_EINVAL (chi0_last_error(NULL) states the bytes needed).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All calls share the
+ * array and see the previous call's contents (what must start at zero is cleared on the
+ * stream), so calls that overlap on the GPU race: serialize them on one stream.  The call
+ * only enqueues work on opts->stream; it does not synchronize.  Errors: CHI0_EINVAL,
+ * CHI0_ENOTSUP, CHI0_ECUDA; messages through chi0_last_error(NULL). */
+#define CHI0_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int chi0_static_noalloc(const chi0_kgrid_t *kgrid, chi0_band_window_t window, const chi0_opts_t *opts,
+                        const chi0_q_t *q, int nq, double *chi);
+
 /* Copies the plan's accumulated counters into *stats.  CHI0_EINVAL on NULL. */
 int chi0_plan_stats(const chi0_plan_t *plan, chi0_stats_t *stats);
 

@@ -78,7 +78,8 @@ _lib = None
 
 # every entry point declared in include/chi0.h (checked by the ABI test)
 EXPORTS = ["chi0_opts_default", "chi0_plan", "chi0_static", "chi0_dynamic", "chi0_plan_stats",
-           "chi0_destroy", "chi0_last_error", "chi0_version"]
+           "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc"]
+CHI0_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def lib():
@@ -106,6 +107,9 @@ def lib():
         L.chi0_last_error.restype = ct.c_char_p
         L.chi0_version.argtypes = []
         L.chi0_version.restype = ct.c_int
+        L.chi0_static_noalloc.argtypes = [ct.POINTER(chi0_kgrid_t), chi0_band_window_t, ct.POINTER(chi0_opts_t),
+                                          ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p]
+        L.chi0_static_noalloc.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -157,6 +161,13 @@ def chi0_last_error(plan=None) -> str:
 
 def chi0_version() -> int:
     return lib().chi0_version()
+
+
+def chi0_static_noalloc(kgrid: chi0_kgrid_t, window: chi0_band_window_t, opts: chi0_opts_t, q, nq: int,
+                        chi_ptr: int) -> None:
+    """Static chi0 with device-resident inputs/outputs and no device allocation (the
+    library's fixed work array); see include/chi0.h."""
+    _check(lib().chi0_static_noalloc(ct.byref(kgrid), window, ct.byref(opts), q, nq, chi_ptr), None)
 
 
 # --------------------------------------------------------------- convenience wrapper

@@ -51,6 +51,10 @@ struct chi0_plan {
 
 static char g_plan_err[512] = "";
 
+namespace chi0int {
+void set_global_error(const char *msg) { snprintf(g_plan_err, sizeof(g_plan_err), "%s", msg); }
+}  // namespace chi0int
+
 static int fail(chi0_plan_t *p, int code, const char *fmt, ...) {
   char *dst = p ? p->err : g_plan_err;
   va_list ap;
@@ -431,7 +435,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
         empq = p->empq_d;
         Ekq = fp64 ? (const void *)q.Eq : (const void *)p->Eq32_d;
       }
-      StaticBufs sb{p->tq_d, p->tq_n_d, p->list64_d, p->res64_d, p->cap64, p->partR, p->next_d};
+      StaticBufs sb{p->tq_d, p->tq_n_d, p->list64_d, p->res64_d, p->cap64, p->partR, p->next_d, static_tab_cap()};
       tm.start(CHI0_K_STATIC);
       CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq, sb,
                           p->static_grid, p->counters_d, s));

@@ -77,6 +77,7 @@ struct StaticBufs {
   int cap64;       // list capacity
   double *partial; // [2 * nbatch]: series part, queued part
   int *next;       // [2]: batch counter, FP64 list size
+  int tcap;        // queue entries per batch (at most static_tab_cap())
 };
 
 // static weights for one q: partial[2 * nbatch] (sum them for chi0); Ek/Ekq are the absolute
@@ -88,6 +89,9 @@ cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const v
 int static_persistent_blocks(int fp64);
 long long static_batches(long long ntet);
 int static_tab_cap();
+
+// message of the last failed call made without a plan (chi0_last_error(NULL))
+void set_global_error(const char *msg);
 size_t static_piece_bytes(int fp64);
 
 // dynamic weights: partialR/partialI [nblocks][nw]

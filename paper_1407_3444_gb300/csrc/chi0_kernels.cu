@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_bands(const double *__restrict__ E
 //  k_static_tab  one warp per batch region: long series or divided-difference table
 // Every batch has its own partial sums (series part, queued part), added in a fixed
 // order, so the result does not depend on which warp took which batch.
-constexpr int kTabCap = 64;  // queued final tetrahedra per batch
+constexpr int kTabCap = 64;  // queued final tetrahedra per batch (plans; StaticBufs::tcap at run time)
 
 template <typename T> struct Piece {
   T d[4], f[4], w;
@@ -443,16 +443,16 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
         pc.w = vol2 * r;
         pc.i64 = -1;
         const int slot = atomicAdd(&s_qn[wib], 1);
-        if (slot < kTabCap) {
+        if (slot < sb.tcap) {
           if (fp) {
             const int idx = atomicAdd(sb.next + 1, 1);
             if (idx < sb.cap64) {
               pc.i64 = idx;
-              sb.list64[idx] = batch * kTabCap + slot;
+              sb.list64[idx] = batch * sb.tcap + slot;
               ++nfp64;
             }
           }
-          tq[(long long)batch * kTabCap + slot] = pc;
+          tq[(long long)batch * sb.tcap + slot] = pc;
         } else {
           acc_q += piece_eval<FP64>(pc, tau, nfp64);
         }
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
     const double v = warp_sum(acc.value() + acc_q);
     if (lane == 0) {
       sb.partial[batch] = v;
-      sb.tq_n[batch] = min(s_qn[wib], kTabCap);
+      sb.tq_n[batch] = min(s_qn[wib], sb.tcap);
     }
     __syncwarp();
   }
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
     const int n = sb.tq_n[b];
     double acc = 0.0;
     for (int slot = lane; slot < n; slot += 32) {
-      const Piece<T> pc = tq[b * kTabCap + slot];
+      const Piece<T> pc = tq[b * sb.tcap + slot];
       if constexpr (FP64) {
         acc += pc.w * inv_sum_table(pc.d, pc.f);
       } else {
