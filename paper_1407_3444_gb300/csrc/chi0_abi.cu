@@ -43,7 +43,7 @@ struct chi0_plan {
   int *tq_n_d = nullptr, *list64_d = nullptr;
   double *res64_d = nullptr;
   int cap64 = 0;
-  int static_grid = 0;
+  int static_grid = 0, dynamic_grid = 0;
   size_t part_cap = 0;
   chi0_stats_t stats;
   char err[512];
@@ -221,12 +221,12 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     const size_t es = op.precision == CHI0_PREC_FP64 ? sizeof(double) : sizeof(float);
     CK(p, cudaMalloc(&p->W2_d, es * (size_t)g.nc * w * w));
   }
-  const size_t np = (size_t)dynamic_blocks(dynamic_max_nw()) * dynamic_max_nw();
+  const size_t np = (size_t)static_batches(g.ntet) * dynamic_max_nw();
   size_t ns = 2 * (size_t)static_batches(g.ntet);
   if (ns < (size_t)static_blocks()) ns = (size_t)static_blocks();
   p->part_cap = np > ns ? np : ns;
   CK(p, cudaMalloc(&p->partR, sizeof(double) * p->part_cap));
-  CK(p, cudaMalloc(&p->partI, sizeof(double) * np));
+  CK(p, cudaMalloc(&p->partI, sizeof(double) * p->part_cap));
   CK(p, cudaMalloc(&p->dos_d, sizeof(double) * static_blocks()));
   CK(p, cudaMalloc(&p->counters_d, sizeof(unsigned long long) * 4));
   if (g.nc >= (1LL << 31)) return fail(p, CHI0_EINVAL, "more than 2^31 corners");
@@ -260,6 +260,7 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
   g.fN2 = make_fastdiv((unsigned)g.N[2]);
   if (g.ntet >= (1LL << 31)) return fail(p, CHI0_EINVAL, "more than 2^31 tetrahedra");
   p->static_grid = static_persistent_blocks(op.precision == CHI0_PREC_FP64);
+  p->dynamic_grid = dynamic_persistent_blocks(op.precision == CHI0_PREC_FP64);
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, p->stream));
   CK(p, cudaStreamSynchronize(p->stream));
   memset(&p->stats, 0, sizeof(p->stats));
@@ -423,18 +424,18 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
       CK(p, launch_dos(p->g, p->tet, p->E_d, q.lo, q.hi, p->dos_d, ndos, s));
       tm.stop();
     }
+    const int nb = (int)static_batches(p->g.ntet);
+    const short *empq = p->emp_d;
+    const void *Ek = fp64 ? (const void *)p->E_d : (const void *)p->E32_d;
+    const void *Ekq = Ek;
+    if (q.Eq) {
+      tm.start(CHI0_K_BANDS);
+      CK(p, launch_bands(q.Eq, p->g.nc, p->g.nb, p->g.ef, p->occq_d, p->empq_d, fp64 ? nullptr : p->Eq32_d, s));
+      tm.stop();
+      empq = p->empq_d;
+      Ekq = fp64 ? (const void *)q.Eq : (const void *)p->Eq32_d;
+    }
     if (!dyn) {
-      const int nb = (int)static_batches(p->g.ntet);
-      const short *empq = p->emp_d;
-      const void *Ek = fp64 ? (const void *)p->E_d : (const void *)p->E32_d;
-      const void *Ekq = Ek;
-      if (q.Eq) {
-        tm.start(CHI0_K_BANDS);
-        CK(p, launch_bands(q.Eq, p->g.nc, p->g.nb, p->g.ef, p->occq_d, p->empq_d, fp64 ? nullptr : p->Eq32_d, s));
-        tm.stop();
-        empq = p->empq_d;
-        Ekq = fp64 ? (const void *)q.Eq : (const void *)p->Eq32_d;
-      }
       StaticBufs sb{p->tq_d, p->tq_n_d, p->list64_d, p->res64_d, p->cap64, p->partR, p->next_d, static_tab_cap()};
       tm.start(CHI0_K_STATIC);
       CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq, sb,
@@ -447,10 +448,10 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
       const int maxw = dynamic_max_nw();
       for (int w0 = 0; w0 < nw; w0 += maxw) {
         const int nwc = nw - w0 < maxw ? nw - w0 : maxw;
-        const int nb = dynamic_blocks(nwc);
+        DynBufs db{p->partR, p->partI, p->next_d};
         tm.start(CHI0_K_DYNAMIC);
-        CK(p, launch_dynamic(p->g, p->tet, p->E_d, q, p->W2_d, op.cma, fp64, (float)op.tau, om_d + w0, nwc,
-                             p->partR, p->partI, nb, p->counters_d, s));
+        CK(p, launch_dynamic(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
+                             om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s));
         tm.stop();
         tm.start(CHI0_K_REDUCE);
         CK(p, launch_reduce(p->partR, nb, nwc, scale, q.gamma ? p->dos_d : nullptr, ndos, om_d + w0,

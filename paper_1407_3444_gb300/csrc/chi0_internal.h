@@ -94,10 +94,18 @@ int static_tab_cap();
 void set_global_error(const char *msg);
 size_t static_piece_bytes(int fp64);
 
-// dynamic weights: partialR/partialI [nblocks][nw]
-cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const double *E, const Q &q, const void *W2,
-                           int cma, int fp64, float tau, const double *omega, int nw, double *partialR,
-                           double *partialI, int nblocks, unsigned long long *counters, cudaStream_t s);
+// Work buffers of the dynamic kernel: one partial per (batch of 32 tetrahedra, frequency)
+struct DynBufs {
+  double *partR, *partI;  // [nbatch][nw]
+  int *next;              // batch counter
+};
+
+// dynamic weights for one q and nw <= dynamic_max_nw() frequencies
+cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
+                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
+                           const double *omega, int nw, const DynBufs &db, int nblocks,
+                           unsigned long long *counters, cudaStream_t s);
+int dynamic_persistent_blocks(int fp64);
 
 // Gamma: intraband q -> 0 limit, tetrahedron DOS at eF: partial[nblocks]
 cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,
@@ -108,7 +116,6 @@ cudaError_t launch_reduce(const double *partial, int nblocks, int nw, double sca
                           int ndos, const double *omega, double *out, cudaStream_t s);
 
 int static_blocks();
-int dynamic_blocks(int nw);
 int dynamic_max_nw();
 
 }  // namespace chi0int

@@ -28,8 +28,6 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kSMs = 152;
 constexpr int kStaticBlocks = kSMs * 8;
-constexpr int kDynBlocks = kSMs * 4;
-constexpr int kNWPass = 256;  // frequencies per dynamic pass (shared-memory accumulators)
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ int wrap(int i, int N) { return i >= N ? i - N : i; }
@@ -126,53 +124,6 @@ __device__ __forceinline__ void tet_corners(const Grid &g, const Tet &tet, const
     cq[3] = cid(g, i0 + 1 + s[0], i1 + 1 + s[1], i2 + 1 + s[2]);
   }
   vol = tet.vol_builtin;
-}
-
-// Lanes over bands: the rectangle [lo, mhi) x [nlo, hi) holds every pair with an
-// occupied corner at k and an empty corner at k+q.
-__device__ __forceinline__ void band_extent(const Grid &g, const double *__restrict__ E,
-                                            const double *__restrict__ Eq, const long long c[4],
-                                            const long long cq[4], int lo, int hi, int lane, int &mhi,
-                                            int &nlo) {
-  mhi = lo;
-  nlo = hi;
-  for (int b0 = lo; b0 < hi; b0 += 32) {
-    const int band = b0 + lane;
-    bool occ = false, emp = false;
-    if (band < hi) {
-      double amin = E[c[0] * g.nb + band], bmax = Eq[cq[0] * g.nb + band];
-#pragma unroll
-      for (int i = 1; i < 4; ++i) {
-        amin = fmin(amin, E[c[i] * g.nb + band]);
-        bmax = fmax(bmax, Eq[cq[i] * g.nb + band]);
-      }
-      occ = amin - g.ef < 0.0;
-      emp = bmax - g.ef > 0.0;
-    }
-    const unsigned mo = __ballot_sync(kFull, occ), me = __ballot_sync(kFull, emp);
-    if (mo) mhi = b0 + 32 - __clz(mo);
-    if (me && nlo == hi) nlo = b0 + __ffs(me) - 1;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ bool load_pair(const Grid &g, const double *__restrict__ E,
-                                          const double *__restrict__ Eq, const void *__restrict__ W2v,
-                                          int cma, const long long c[4], const long long cq[4], int m,
-                                          int n, int lo, int w, T a[4], T b[4], T f[4]) {
-  T amin, bmax;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    a[i] = (T)(E[c[i] * g.nb + m] - g.ef);
-    b[i] = (T)(Eq[cq[i] * g.nb + n] - g.ef);
-  }
-  amin = fmin(fmin(a[0], a[1]), fmin(a[2], a[3]));
-  bmax = fmax(fmax(b[0], b[1]), fmax(b[2], b[3]));
-  if (!(amin < T(0)) || !(bmax > T(0))) return false;
-  const T *W2 = (const T *)W2v;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) f[i] = cma ? T(1) : W2[(c[i] * w + (m - lo)) * w + (n - lo)];
-  return true;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -515,71 +466,241 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
 }
 
 // ---------------------------------------------------------------- dynamic weights
-// Frequencies live in shared memory; lane l of a warp owns w_l, w_{l+32}, ... and adds
-// into its warp's own accumulator row (no atomics, fixed order).
+// Persistent warps take batches of 32 tetrahedra (as k_static); the warp walks the batch's
+// (m, n) items together and the lanes own the frequencies.  Per final tetrahedron the warp
+// forms the far-field moments once; each lane then evaluates 1/(D - w) + 1/(D + w) for its
+// frequencies from them (Horner in z = c/(c -+ w)) wherever rho = max|D - c|/|c -+ w| is at
+// most kappa_far, and from the divided-difference table (principal value) nearer; Im uses
+// the B-spline density inside the knot range.  Per (warp, w) compensated accumulators in
+// shared memory; one partial per (batch, w), summed in a fixed order.
+constexpr int kDynThreads = 128;
+constexpr int kDynWarps = kDynThreads / 32;
+constexpr int kNWPass = 256;  // frequencies per dynamic pass
+
+template <typename T> struct FarK {
+  static constexpr int value = sizeof(T) == 8 ? 64 : 32;  // moments kept per final tetrahedron
+};
+constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed per warp
+
+template <typename T> __device__ __forceinline__ void kadd_t(T &sum, T &comp, T x) {
+  const T t = sum + x;
+  if (tabs(sum) >= tabs(x)) comp += (sum - t) + x;
+  else comp += (x - t) + sum;
+  sum = t;
+}
+
+// 1/(D - w) (sgn 0) or 1/(D + w) (sgn 1) for knots d near w: divided-difference table
+// (principal value across D = w); one out-of-line copy shared by every call site
 template <bool FP64>
-__global__ void __launch_bounds__(kThreads) k_dynamic(Grid g, Tet tet, const double *__restrict__ E, Q q,
-                                                       const void *__restrict__ W2, int cma, float tau,
-                                                       const double *__restrict__ omega, int nw,
-                                                       double *__restrict__ partialR,
-                                                       double *__restrict__ partialI,
-                                                       unsigned long long *__restrict__ counters) {
+__device__ __noinline__ typename std::conditional<FP64, double, float>::type near_term(
+    const typename std::conditional<FP64, double, float>::type *d,
+    const typename std::conditional<FP64, double, float>::type *f,
+    typename std::conditional<FP64, double, float>::type om, int sgn, float tau, int &nfp64) {
   using T = typename std::conditional<FP64, double, float>::type;
-  __shared__ double sR[kWarps][kNWPass], sI[kWarps][kNWPass];
-  __shared__ double sW[kNWPass];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long warp = (long long)blockIdx.x * kWarps + wib;
-  const long long nwarps = (long long)gridDim.x * kWarps;
-  const double *Eq = q.Eq ? q.Eq : E;
-  const int w = q.hi - q.lo;
-  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) sW[iw] = omega[iw];
-  for (int iw = lane; iw < kNWPass; iw += 32) {
-    sR[wib][iw] = 0.0;
-    sI[wib][iw] = 0.0;
+  const T sh = sgn ? om : -om;
+  T x[4] = {d[0] + sh, d[1] + sh, d[2] + sh, d[3] + sh};
+  if constexpr (FP64) {
+    return inv_sum(x, f);
+  } else {
+    return inv_sum_mixed(x, f, tau, &nfp64);
   }
+}
+
+// evaluates a warp's near-field list: entry = 2 * frequency index + term; every entry of one
+// round has a different frequency index or term, and the two terms of one frequency go to
+// different rounds only through the list order, so each round adds to distinct slots
+template <bool FP64>
+__device__ __forceinline__ void near_pass(const typename std::conditional<FP64, double, float>::type d[4],
+                                          const typename std::conditional<FP64, double, float>::type f[4],
+                                          typename std::conditional<FP64, double, float>::type vr,
+                                          const typename std::conditional<FP64, double, float>::type *s_w,
+                                          const short *list, int n,
+                                          typename std::conditional<FP64, double, float>::type *sR,
+                                          typename std::conditional<FP64, double, float>::type *cR,
+                                          typename std::conditional<FP64, double, float>::type *sI,
+                                          typename std::conditional<FP64, double, float>::type *cI, float tau,
+                                          int &nfp64) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    const int k = base + lane;
+    if (k < n) {
+      const int e = list[k];
+      const int iw = e >> 1, sgn = e & 1;
+      const T w = s_w[iw];
+      const T om = w < T(0) ? -w : w;
+      // a frequency and its two terms may both be in this round: add them one term at a time
+      const T re = near_term<FP64>(d, f, om, sgn, tau, nfp64);
+      for (int t2 = 0; t2 < 2; ++t2) {
+        if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
+        __syncwarp(__activemask());
+      }
+      if (sgn == 0 && om > d[0] && om < d[3]) {  // inside the knot range: the delta term too
+        const T im = delta_sum(d, f, om) * T(3.141592653589793);
+        kadd_t(sI[iw], cI[iw], w < T(0) ? -vr * im : vr * im);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const void *__restrict__ Ek,
+                                                          const void *__restrict__ Ekq, Q q,
+                                                          const void *__restrict__ W2, int cma, float tau,
+                                                          const short *__restrict__ occ,
+                                                          const short *__restrict__ empq,
+                                                          const double *__restrict__ omega, int nw, DynBufs db,
+                                                          unsigned long long *__restrict__ counters) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  constexpr int KM = FarK<T>::value;
+  __shared__ int s_c[kDynWarps][32][4], s_cq[kDynWarps][32][4];
+  __shared__ T s_vol[kDynWarps][32];
+  __shared__ int s_nlo[kDynWarps][32], s_nn[kDynWarps][32], s_pre[kDynWarps][33];
+  __shared__ T s_a[kDynWarps][KM];
+  __shared__ T sR[kDynWarps][kNWPass], sI[kDynWarps][kNWPass];
+  __shared__ T cR[kDynWarps][kNWPass], cI[kDynWarps][kNWPass];  // compensation terms
+  __shared__ T s_w[kNWPass];
+  __shared__ short s_near[kDynWarps][kNearCap];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = q.hi - q.lo;
+  const long long nbatch = (g.ntet + 31) / 32;
+  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) s_w[iw] = (T)omega[iw];
   __syncthreads();
   int nfp64 = 0, npieces = 0;
-  for (long long t = warp; t < g.ntet; t += nwarps) {
-    long long c[4], cq[4];
-    double vol;
-    tet_corners(g, tet, q, t, c, cq, vol);
-    int mhi, nlo;
-    band_extent(g, E, Eq, c, cq, q.lo, q.hi, lane, mhi, nlo);
-    const int nm = mhi - q.lo, nn = q.hi - nlo;
-    const int npair = nm > 0 && nn > 0 ? nm * nn : 0;
-    for (int p = 0; p < npair; ++p) {  // warp-uniform
-      const int m = q.lo + p / nn, n = nlo + p % nn;
+  auto kadd = [](T &sum, T &comp, T x) {
+    const T t = sum + x;
+    if (tabs(sum) >= tabs(x)) comp += (sum - t) + x;
+    else comp += (x - t) + sum;
+    sum = t;
+  };
+  for (;;) {
+    int batch = 0;
+    if (lane == 0) batch = atomicAdd(db.next, 1);
+    batch = __shfl_sync(kFull, batch, 0);
+    if (batch >= nbatch) break;
+    for (int iw = lane; iw < nw; iw += 32) {
+      sR[wib][iw] = T(0);
+      sI[wib][iw] = T(0);
+      cR[wib][iw] = T(0);
+      cI[wib][iw] = T(0);
+    }
+    const long long t = (long long)batch * 32 + lane;
+    int cnt = 0;
+    if (t < g.ntet) {
+      long long c[4], cq[4];
+      double vol;
+      tet_corners(g, tet, q, t, c, cq, vol);
+      int mhi = 0, nlo = g.nb;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        s_c[wib][lane][i] = (int)c[i];
+        s_cq[wib][lane][i] = (int)cq[i];
+        mhi = max(mhi, (int)occ[c[i]]);
+        nlo = min(nlo, (int)empq[cq[i]]);
+      }
+      mhi = min(mhi, q.hi);
+      nlo = max(nlo, q.lo);
+      const int nm = mhi - q.lo, nn = q.hi - nlo;
+      cnt = (nm > 0 && nn > 0) ? nm * nn : 0;
+      s_vol[wib][lane] = (T)vol;
+      s_nlo[wib][lane] = nlo;
+      s_nn[wib][lane] = nn;
+    }
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, pre, o);
+      if (lane >= o) pre += v;
+    }
+    s_pre[wib][lane + 1] = pre;
+    if (lane == 0) s_pre[wib][0] = 0;
+    const int total = __shfl_sync(kFull, pre, 31);
+    __syncwarp();
+    int l = 0;
+    for (int it = 0; it < total; ++it) {  // warp-uniform
+      while (s_pre[wib][l + 1] <= it) ++l;
+      const int loc = it - s_pre[wib][l];
+      const int nn = s_nn[wib][l];
+      const int mo = div_small(loc, nn, q.hi - q.lo);
+      const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
       if (q.gamma && m == n) continue;
       T a[4], b[4], f[4];
-      if (!load_pair<T>(g, E, Eq, W2, cma, c, cq, m, n, q.lo, w, a, b, f)) continue;
+      T amin = T(1e30), bmax = T(-1e30);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
+        if constexpr (FP64) {
+          a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
+          b[i] = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
+        } else {
+          a[i] = ((const float *)Ek)[(long long)ck * g.nb + m];
+          b[i] = ((const float *)Ekq)[(long long)cq * g.nb + n];
+        }
+        amin = a[i] < amin ? a[i] : amin;
+        bmax = b[i] > bmax ? b[i] : bmax;
+      }
+      if (!(amin < T(0) && bmax > T(0))) continue;
+      const T *W2t = (const T *)W2;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
+      const T vol = s_vol[wib][l];
       carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) {
         sort4(d, ff);
         ++npieces;
-        const double vr = vol * (double)r;
-#pragma unroll 1
-        for (int iw = lane; iw < nw; iw += 32) {
-          const double omd = sW[iw];
-          const T om = (T)fabs(omd);
-          T xm[4], xp[4];
+        if (!(d[3] > T(0))) return;
+        __syncwarp();
+        int K = 0;
+        if (lane == 0) K = far_moments<T, KM>(d, ff, s_a[wib]);
+        K = __shfl_sync(kFull, K, 0);
+        __syncwarp();
+        const T c = (d[0] + d[3]) * T(0.5), half = (d[3] - d[0]) * T(0.5);
+        const T vr = vol * r;
+        // far field for both terms (Horner on the moments); near-field frequencies are
+        // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
+        unsigned nearm = 0u, nearp = 0u;
+        for (int iw = lane, itn = 0; iw < nw; iw += 32, ++itn) {
+          const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
+          T re = T(0);
+          const T rp = half / (c + om);
+          if (rp <= T(Num<T>::kappa_far)) re += far_eval(s_a[wib], K, c, -om, rp);
+          else nearp |= 1u << itn;
+          const T dm = c - om;
+          const T rm = half / (dm < T(0) ? -dm : dm);
+          if (rm <= T(Num<T>::kappa_far)) re += far_eval(s_a[wib], K, c, om, rm);
+          else nearm |= 1u << itn;
+          if (re != T(0)) kadd(sR[wib][iw], cR[wib][iw], vr * re);
+        }
+        // near field: compact the (frequency, term) pairs of the warp into a list
+        int nlist = 0;
+        const int nit = (nw + 31) >> 5;
+        for (int itn = 0; itn < nit; ++itn) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            xm[i] = d[i] - om;
-            xp[i] = d[i] + om;
+          for (int sgn = 0; sgn < 2; ++sgn) {
+            const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
+            const unsigned bal = __ballot_sync(kFull, mine);
+            if (mine) s_near[wib][nlist + __popc(bal & ((1u << lane) - 1u))] = (short)((itn * 32 + lane) * 2 + sgn);
+            nlist += __popc(bal);
           }
-          T re;
-          if constexpr (FP64) {
-            re = inv_sum(xm, ff) + inv_sum(xp, ff);
-          } else {
-            re = inv_sum_mixed(xm, ff, tau, &nfp64) + inv_sum_mixed(xp, ff, tau, &nfp64);
-          }
-          sR[wib][iw] += vr * (double)re;
-          if (om > T(0)) {
-            const T im = delta_sum(d, ff, om);
-            sI[wib][iw] += (omd < 0.0 ? -vr : vr) * 3.141592653589793 * (double)im;
+          if (nlist > kNearCap - 64) {  // flush a full list
+            __syncwarp();
+            near_pass<FP64>(d, ff, vr, s_w, s_near[wib], nlist, sR[wib], cR[wib], sI[wib], cI[wib], tau, nfp64);
+            nlist = 0;
+            __syncwarp();
           }
         }
+        __syncwarp();
+        near_pass<FP64>(d, ff, vr, s_w, s_near[wib], nlist, sR[wib], cR[wib], sI[wib], cI[wib], tau, nfp64);
+        __syncwarp();
       });
     }
+    __syncwarp();
+    for (int iw = lane; iw < nw; iw += 32) {
+      db.partR[(long long)batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
+      db.partI[(long long)batch * nw + iw] = (double)sI[wib][iw] + (double)cI[wib][iw];
+    }
+    __syncwarp();
   }
   if (counters) {
     unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64;
@@ -592,17 +713,6 @@ __global__ void __launch_bounds__(kThreads) k_dynamic(Grid g, Tet tet, const dou
       atomicAdd(&counters[0], a / 32);  // every lane counted each piece
       atomicAdd(&counters[1], b);
     }
-  }
-  __syncthreads();
-  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
-    double r = 0.0, im = 0.0;
-#pragma unroll
-    for (int k = 0; k < kWarps; ++k) {
-      r += sR[k][iw];
-      im += sI[k][iw];
-    }
-    partialR[(long long)blockIdx.x * nw + iw] = r;
-    partialI[(long long)blockIdx.x * nw + iw] = im;
   }
 }
 
@@ -656,7 +766,6 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const double *__restrict__ 
 
 // ======================================================================= launchers
 int static_blocks() { return kStaticBlocks; }
-int dynamic_blocks(int) { return kDynBlocks; }
 int dynamic_max_nw() { return kNWPass; }
 
 __global__ void __launch_bounds__(kThreads) k_c128_to_c64(const double2 *__restrict__ in, float2 *__restrict__ out,
@@ -751,15 +860,30 @@ cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const v
   return cudaGetLastError();
 }
 
-cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const double *E, const Q &q, const void *W2,
-                           int cma, int fp64, float tau, const double *omega, int nw, double *partialR,
-                           double *partialI, int nblocks, unsigned long long *counters, cudaStream_t s) {
+cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
+                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
+                           const double *omega, int nw, const DynBufs &db, int nblocks,
+                           unsigned long long *counters, cudaStream_t s) {
   if (nw > kNWPass || nw <= 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(db.next, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   if (fp64)
-    k_dynamic<true><<<nblocks, kThreads, 0, s>>>(g, tet, E, q, W2, cma, tau, omega, nw, partialR, partialI, counters);
+    k_dynamic<true><<<nblocks, kDynThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db,
+                                                     counters);
   else
-    k_dynamic<false><<<nblocks, kThreads, 0, s>>>(g, tet, E, q, W2, cma, tau, omega, nw, partialR, partialI, counters);
+    k_dynamic<false><<<nblocks, kDynThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db,
+                                                      counters);
   return cudaGetLastError();
+}
+
+int dynamic_persistent_blocks(int fp64) {
+  int nb = 0;
+  cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<true>, kDynThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<false>, kDynThreads, 0);
+  if (e != cudaSuccess || nb < 1) nb = 1;
+  int dev = 0, sms = kSMs;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return nb * sms;
 }
 
 cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,

@@ -38,6 +38,7 @@ template <> struct Num<double> {
   static constexpr double tol = 1e-17;
   static constexpr double kappa = 0.25;  // series branch: (x3 - x0) <= kappa (x3 + x0)
   static constexpr double kappa_long = 0.25;
+  static constexpr double kappa_far = 0.5;  // far-field expansion of the dynamic PV terms
   static constexpr int kmax = 80;
 };
 template <> struct Num<float> {
@@ -45,6 +46,7 @@ template <> struct Num<float> {
   static constexpr float tol = 2e-8f;
   static constexpr float kappa = 0.5f;       // series branch inside the carving loop
   static constexpr float kappa_long = 0.7f;  // series branch of queued pieces (evaluated together)
+  static constexpr float kappa_far = 0.5f;   // far-field expansion of the dynamic PV terms
   static constexpr int kmax = 64;
 };
 
@@ -295,6 +297,63 @@ __device__ __forceinline__ float inv_sum_mixed(const float d[4], const float f[4
   ++*fp64;
   double xd[4] = {x[0], x[1], x[2], x[3]}, fd[4] = {f[0], f[1], f[2], f[3]};
   return (float)inv_sum_table(xd, fd);
+}
+
+// Far-field moments of a final tetrahedron (sorted knots d >= 0, midpoint c > 0):
+//   a_k = (-1)^k 6 k!/(k+4)! sum_j f_j h_k(e_1..e_4, e_j),  e = (d - c)/c,
+// so that for any frequency w with rho = max|d - c| / |c - w| < 1
+//   (1/V) sum_j f_j int_S lambda_j / (D - w) = (1/(c - w)) sum_k a_k z^k,  z = c / (c - w)
+// (expansion of 1/(D - w) about c; at w = 0 this is the static series).  Writes a_0..a_{K-1}
+// and returns K, the count after which |a_k| (times the largest z used, kappa c / max|d-c|)
+// falls below tol.
+template <typename T, int KMAX> __device__ int far_moments(const T d[4], const T f[4], T *a) {
+  const T c = (d[0] + d[3]) * T(0.5);
+  const T ci = T(1) / c;
+  T e[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) e[l] = (d[l] - c) * ci;
+  const T rmax = (d[3] - d[0]) * T(0.5) * ci;           // max|e|
+  const T zmax = rmax > T(0) ? T(Num<T>::kappa_far) / rmax : T(1);  // largest |z| that uses them
+  T H[4] = {T(1), T(1), T(1), T(1)};
+  T P[4] = {T(1), T(1), T(1), T(1)};
+  a[0] = T(0.25) * (f[0] + f[1] + f[2] + f[3]);
+  const T ref = tabs(a[0]);
+  T zk = T(1), prev = ref;
+  int k = 1;
+  for (; k < KMAX; ++k) {
+    H[0] = e[0] * H[0];
+#pragma unroll
+    for (int l = 1; l < 4; ++l) H[l] = H[l - 1] + e[l] * H[l];
+    T sj = T(0);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      P[jj] = H[3] + e[jj] * P[jj];
+      sj += f[jj] * P[jj];
+    }
+    a[k] = series_coef<T>(k) * sj;
+    zk *= zmax;
+    const T mag = tabs(a[k]) * zk;
+    if (k >= 2 && mag + prev <= Num<T>::tol * ref) {
+      ++k;
+      break;
+    }
+    prev = mag;
+  }
+  return k;
+}
+
+// (1/(c - w)) sum_{k<K} a_k z^k with z = c/(c - w), truncated where rho^k < tol
+template <typename T> __device__ __forceinline__ T far_eval(const T *a, int K, T c, T w, T rho) {
+  const T den = c - w;
+  const T z = c / den;
+  int kk = K;
+  if (rho > T(0)) {
+    const float need = __log2f((float)Num<T>::tol) / __log2f((float)rho);  // rho^need = tol
+    kk = min(K, 2 + (int)need);
+  }
+  T sum = T(0);
+  for (int k = kk - 1; k >= 0; --k) sum = sum * z + a[k];
+  return sum / den;
 }
 
 // Normalised cubic B-spline density M(w; t0..t4) (integral 1) by the de Boor-Cox
