@@ -151,9 +151,11 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-# FP32 flops executed per final tetrahedron by the mixed static weight kernel
-# (ncu instruction counters on this workload; see profiles/k_static_mixed_cr_like.md)
-FLOPS_PER_PIECE_MIXED = None
+# FP32 operations (FFMA counted twice, FADD, FMUL) of the mixed static weight kernels per
+# final tetrahedron on this workload, from the ncu instruction counters of
+# profiles/static_weights_cr_like_48.md; and their DRAM bytes per final tetrahedron.
+FLOPS_PER_PIECE_MIXED = 207.0
+TRAFFIC_PER_PIECE_MIXED = None
 
 
 # ------------------------------------------------------------------------------ main
@@ -212,7 +214,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     dev = chi0.DeviceInputs(W)
     Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev)
-    Pd = chi0.Plan(W, precision="fp64", device=True, profile=False, staged=dev)
+    Pd = chi0.Plan(W, precision="fp64", device=True, profile=False, staged=dev) if args.fp64_steps > 0 else None
     nominal = W.nominal_evals()
     for _ in range(args.warmup):
         Pm.static()
@@ -238,25 +240,37 @@ def run_ours(args):
         ms = float(t.item())
     s1 = Pm.stats()
     value = ws * nominal / (ms * 1e-3)
-    k_static_ms = (s1.time_ms[chi0.CHI0_K_STATIC] - s0.time_ms[chi0.CHI0_K_STATIC]) / max(
-        1, s1.launches[chi0.CHI0_K_STATIC] - s0.launches[chi0.CHI0_K_STATIC])
-    launches = sum(s1.launches[k] - s0.launches[k] for k in range(chi0.CHI0_K_COUNT))
+    def stage_ms(k):
+        n = s1.launches[k] - s0.launches[k]
+        return (s1.time_ms[k] - s0.time_ms[k]) / n if n else None
+
+    k_static_ms = stage_ms(chi0.CHI0_K_STATIC)
+    launches = s1.kernels - s0.kernels
+    pieces_timed = s1.pieces - s0.pieces
+    static_launches = s1.launches[chi0.CHI0_K_STATIC] - s0.launches[chi0.CHI0_K_STATIC]
+    stages = {name: stage_ms(k) for name, k in (("overlap", chi0.CHI0_K_OVERLAP), ("weights", chi0.CHI0_K_STATIC),
+                                                 ("reduce", chi0.CHI0_K_REDUCE), ("bands", chi0.CHI0_K_BANDS),
+                                                 ("dos", chi0.CHI0_K_DOS))}
     counters = Pm.counters()
     mixed = out_m.cpu().numpy()
 
     # all-FP64 GPU form on the same resident inputs
-    Pd.static()
-    torch.cuda.synchronize()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(args.fp64_steps):
-        out_d = Pd.static()
-    f1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = f0.elapsed_time(f1) / args.fp64_steps
-    fp64 = out_d.cpu().numpy()
-    err_mixed = float(np.max(np.abs(mixed - fp64) / np.abs(fp64)))
+    fp64 = None
+    ms64 = None
+    err_mixed = None
+    if Pd is not None:
+        Pd.static()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            out_d = Pd.static()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        fp64 = out_d.cpu().numpy()
+        err_mixed = float(np.max(np.abs(mixed - fp64) / np.abs(fp64)))
 
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
@@ -280,40 +294,52 @@ def run_ours(args):
 
     peaks, kind = measured_peaks()
     smax = float(peaks.get("sm_max_mhz", 2070.0))
-    roof = None
-    if FLOPS_PER_PIECE_MIXED is not None and counters is not None:
-        pieces_per_launch = counters["pieces"] / max(1, counters["static_launches"])
-        ach = FLOPS_PER_PIECE_MIXED * pieces_per_launch / (k_static_ms * 1e-3) / 1e12
-        pk = fp32_peak_tflops(smax)
-        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": None, "kernel": "k_static<mixed>", "kernel_ms": k_static_ms,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": fp32_peak_tflops(smax), "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "kernel": "k_static<mixed>", "kernel_ms": k_static_ms}
+    pieces_per_launch = pieces_timed / max(1, static_launches)
+    pk = fp32_peak_tflops(smax)
+    ach = FLOPS_PER_PIECE_MIXED * pieces_per_launch / (k_static_ms * 1e-3) / 1e12 if k_static_ms else None
+    roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+            "frac": ach / pk if ach is not None else None,
+            "traffic": TRAFFIC_PER_PIECE_MIXED * pieces_per_launch if TRAFFIC_PER_PIECE_MIXED else None,
+            "kernel": "static weights (k_static + k_static_f64 + k_static_tab, mixed)",
+            "kernel_ms": k_static_ms, "units_per_launch": pieces_per_launch,
+            "flops_per_unit": FLOPS_PER_PIECE_MIXED, "unit_name": "final tetrahedron",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % smax}
+    # the overlap kernel is bound by HBM: eigenvector blocks at k (complex64 copy) and at k+q
+    # (complex128 inputs) read once, |M|^2 written once
+    ovl_ms = stages["overlap"]
+    ovl = None
+    if ovl_ms:
+        nc, no, w = W.ncorner, W.norb, W.nb
+        ovl_bytes = nc * no * w * (8 + 16) + nc * w * w * 4
+        ovl = {"bound": "hbm", "achieved": ovl_bytes / (ovl_ms * 1e-3) / 1e9, "peak": float(peaks.get("hbm_gbs", 6800.0)),
+               "unit": "GB/s", "bytes_per_launch": ovl_bytes, "kernel_ms": ovl_ms}
+        ovl["frac"] = ovl["achieved"] / ovl["peak"]
 
     if rank == 0:
         err_oracle = None
         if cpu is not None:
             nq = len(oracle_vals)
-            err_oracle = {"fp64_gpu": float(np.max(np.abs(fp64[1:1 + nq] - oracle_vals) / np.abs(oracle_vals))),
-                          "mixed_gpu": float(np.max(np.abs(mixed[1:1 + nq] - oracle_vals) / np.abs(oracle_vals))),
+            err_oracle = {"mixed_gpu": float(np.max(np.abs(mixed[1:1 + nq] - oracle_vals) / np.abs(oracle_vals))),
                           "q_points": nq}
+            if fp64 is not None:
+                err_oracle["fp64_gpu"] = float(np.max(np.abs(fp64[1:1 + nq] - oracle_vals) / np.abs(oracle_vals)))
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": workload_config(W, args),
-                "fp64_gpu": {"value": nominal / (ms64 * 1e-3), "unit": "evals/s", "ms_per_step": ms64,
-                             "mixed_speedup": ms64 / ms},
+                "fp64_gpu": ({"value": nominal / (ms64 * 1e-3), "unit": "evals/s", "ms_per_step": ms64,
+                              "mixed_speedup": ms64 / ms} if ms64 else None),
                 "error": {"mixed_vs_fp64_gpu_max_rel": err_mixed, "vs_oracle": err_oracle},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "roofline_overlap": ovl, "stage_ms_per_q": stages,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "counters": counters, "clocks": ck, "peaks_source": kind}
         print(json.dumps(line), flush=True)
         if args.profile_out:
             with open(args.profile_out, "w") as f:
                 json.dump(line, f, indent=1)
     Pm.close()
-    Pd.close()
+    if Pd is not None:
+        Pd.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0

@@ -170,6 +170,7 @@ typedef struct {
   long long calls;
   long long pieces;     /* final tetrahedra evaluated (profile mode)                     */
   long long fp64_evals; /* weight evaluations taken by the FP64 branch (mixed, profile)  */
+  long long kernels;    /* kernel launches made by the plan's calls (always counted)     */
 } chi0_stats_t;
 
 /* ---------------------------------------------------------------- entry points */

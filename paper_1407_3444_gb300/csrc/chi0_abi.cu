@@ -40,9 +40,7 @@ struct chi0_plan {
   void *C32_d = nullptr;                      // complex64 copy of complex128 eigenvectors (mixed)
   int *next_d = nullptr;                      // [2] batch counter, FP64 list size
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
-  int *tq_n_d = nullptr, *list64_d = nullptr;
-  double *res64_d = nullptr;
-  int cap64 = 0;
+  int *tq_n_d = nullptr;
   int static_grid = 0, dynamic_grid = 0;
   size_t part_cap = 0;
   chi0_stats_t stats;
@@ -124,8 +122,6 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->next_d);
   cudaFree(p->tq_d);
   cudaFree(p->tq_n_d);
-  cudaFree(p->list64_d);
-  cudaFree(p->res64_d);
 }
 
 extern "C" void chi0_destroy(chi0_plan_t *p) {
@@ -240,9 +236,6 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     const int fp64 = op.precision == CHI0_PREC_FP64;
     CK(p, cudaMalloc(&p->tq_d, static_piece_bytes(fp64) * (size_t)nbatch * static_tab_cap()));
     CK(p, cudaMalloc(&p->tq_n_d, sizeof(int) * (size_t)nbatch));
-    p->cap64 = (int)(nbatch * 8 < (1 << 22) ? (nbatch * 8 > 4096 ? nbatch * 8 : 4096) : (1 << 22));
-    CK(p, cudaMalloc(&p->list64_d, sizeof(int) * (size_t)p->cap64));
-    CK(p, cudaMalloc(&p->res64_d, sizeof(double) * (size_t)p->cap64));
   }
   if (op.precision == CHI0_PREC_MIXED) {
     CK(p, cudaMalloc(&p->E32_d, sizeof(float) * (size_t)g.nc * g.nb));
@@ -416,12 +409,14 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     if (!op.cma) {
       tm.start(CHI0_K_OVERLAP);
       CK(p, launch_overlap(p->g, p->E_d, p->C_d, p->dtype, q, p->W2_d, fp64, s, p->C32_d));
+      p->stats.kernels += 1;
       tm.stop();
     }
     const int ndos = static_blocks();
     if (q.gamma) {
       tm.start(CHI0_K_DOS);
       CK(p, launch_dos(p->g, p->tet, p->E_d, q.lo, q.hi, p->dos_d, ndos, s));
+      p->stats.kernels += 1;
       tm.stop();
     }
     const int nb = (int)static_batches(p->g.ntet);
@@ -431,18 +426,21 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     if (q.Eq) {
       tm.start(CHI0_K_BANDS);
       CK(p, launch_bands(q.Eq, p->g.nc, p->g.nb, p->g.ef, p->occq_d, p->empq_d, fp64 ? nullptr : p->Eq32_d, s));
+      p->stats.kernels += 1;
       tm.stop();
       empq = p->empq_d;
       Ekq = fp64 ? (const void *)q.Eq : (const void *)p->Eq32_d;
     }
     if (!dyn) {
-      StaticBufs sb{p->tq_d, p->tq_n_d, p->list64_d, p->res64_d, p->cap64, p->partR, p->next_d, static_tab_cap()};
+      StaticBufs sb{p->tq_d, p->tq_n_d, p->partR, p->next_d, static_tab_cap()};
       tm.start(CHI0_K_STATIC);
       CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq, sb,
                           p->static_grid, p->counters_d, s));
+      p->stats.kernels += 2;
       tm.stop();
       tm.start(CHI0_K_REDUCE);
       CK(p, launch_reduce(p->partR, 2 * nb, 1, scale, q.gamma ? p->dos_d : nullptr, ndos, nullptr, outR + iq, s));
+      p->stats.kernels += 1;
       tm.stop();
     } else {
       const int maxw = dynamic_max_nw();
@@ -452,11 +450,13 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
         tm.start(CHI0_K_DYNAMIC);
         CK(p, launch_dynamic(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
                              om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s));
+        p->stats.kernels += 1;
         tm.stop();
         tm.start(CHI0_K_REDUCE);
         CK(p, launch_reduce(p->partR, nb, nwc, scale, q.gamma ? p->dos_d : nullptr, ndos, om_d + w0,
                             outR + (size_t)iq * nw + w0, s));
         CK(p, launch_reduce(p->partI, nb, nwc, scale, nullptr, 0, nullptr, outI + (size_t)iq * nw + w0, s));
+        p->stats.kernels += 2;
         tm.stop();
       }
     }

@@ -72,11 +72,8 @@ cudaError_t launch_bands(const double *E, long long nc, int nb, double ef, short
 struct StaticBufs {
   void *tq;        // queued final tetrahedra: [nbatch][static_tab_cap()] pieces
   int *tq_n;       // [nbatch] queued per batch
-  int *list64;     // FP64-branch list: queue positions
-  double *res64;   // FP64-branch results
-  int cap64;       // list capacity
   double *partial; // [2 * nbatch]: series part, queued part
-  int *next;       // [2]: batch counter, FP64 list size
+  int *next;       // batch counter
   int tcap;        // queue entries per batch (at most static_tab_cap())
 };
 

@@ -236,8 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_bands(const double *__restrict__ E
 //                batch's (m, n) rectangles are flattened into one item list shared by the
 //                lanes; carving; final tetrahedra whose knots fit the short series are
 //                evaluated on the spot (compact hot loop), the others are queued in the
-//                batch's region of a global queue (FP64-branch ones also in a compact list)
-//  k_static_f64  (mixed precision) the FP64-branch list, full warps of FP64
+//                batch's region of a global queue
 //  k_static_tab  one warp per batch region: long series or divided-difference table
 // Every batch has its own partial sums (series part, queued part), added in a fixed
 // order, so the result does not depend on which warp took which batch.
@@ -245,7 +244,7 @@ constexpr int kTabCap = 64;  // queued final tetrahedra per batch (plans; Static
 
 template <typename T> struct Piece {
   T d[4], f[4], w;
-  int i64;  // index in the FP64 list, -1 if none
+  int i64;  // 1: evaluate in FP64 (near-degenerate knots), -1: FP32
 };
 
 // compensated (Neumaier) accumulator in the kernel's precision
@@ -392,17 +391,10 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
 #pragma unroll
         for (int i = 0; i < 4; ++i) pc.f[i] = ff[i];
         pc.w = vol2 * r;
-        pc.i64 = -1;
+        pc.i64 = fp ? 1 : -1;
         const int slot = atomicAdd(&s_qn[wib], 1);
         if (slot < sb.tcap) {
-          if (fp) {
-            const int idx = atomicAdd(sb.next + 1, 1);
-            if (idx < sb.cap64) {
-              pc.i64 = idx;
-              sb.list64[idx] = batch * sb.tcap + slot;
-              ++nfp64;
-            }
-          }
+          nfp64 += fp;
           tq[(long long)batch * sb.tcap + slot] = pc;
         } else {
           acc_q += piece_eval<FP64>(pc, tau, nfp64);
@@ -431,17 +423,6 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
   }
 }
 
-// FP64 branch of the mixed path: every listed piece's table in FP64, full warps
-__global__ void __launch_bounds__(kThreads) k_static_f64(StaticBufs sb) {
-  const Piece<float> *tq = (const Piece<float> *)sb.tq;
-  const int n = min(sb.next[1], sb.cap64);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const Piece<float> pc = tq[sb.list64[i]];
-    double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
-    sb.res64[i] = (double)pc.w * inv_sum_table(xd, fd);
-  }
-}
-
 // one warp per batch region: queued pieces in slot order
 template <bool FP64>
 __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, StaticBufs sb) {
@@ -456,8 +437,11 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
       const Piece<T> pc = tq[b * sb.tcap + slot];
       if constexpr (FP64) {
         acc += pc.w * inv_sum_table(pc.d, pc.f);
+      } else if (pc.i64 >= 0) {  // near-degenerate knots: the table in FP64 (rare)
+        double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
+        acc += (double)pc.w * inv_sum_table(xd, fd);
       } else {
-        acc += pc.i64 >= 0 ? sb.res64[pc.i64] : (double)(pc.w * inv_sum_long(pc.d, pc.f));
+        acc += (double)(pc.w * inv_sum_long(pc.d, pc.f));
       }
     }
     const double v = warp_sum(acc);
@@ -738,28 +722,34 @@ __global__ void __launch_bounds__(kThreads) k_dos(Grid g, Tet tet, const double 
 }
 
 // ---------------------------------------------------------------- reduction
-__global__ void __launch_bounds__(kThreads) k_reduce(const double *__restrict__ partial, int nblocks, int nw,
-                                                      double scale, const double *__restrict__ dos, int ndos,
-                                                      const double *__restrict__ omega,
-                                                      double *__restrict__ out) {
+constexpr int kRedThreads = 1024;
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict__ partial, int nblocks, int nw,
+                                                         double scale, const double *__restrict__ dos, int ndos,
+                                                         const double *__restrict__ omega,
+                                                         double *__restrict__ out) {
   const int k = blockIdx.x;
-  double s = 0.0, sd = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(long long)b * nw + k];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, sd = 0.0;
+  int b = threadIdx.x;
+  for (; b + 3 * kRedThreads < nblocks; b += 4 * kRedThreads) {  // independent loads in flight
+    s0 += partial[(long long)b * nw + k];
+    s1 += partial[(long long)(b + kRedThreads) * nw + k];
+    s2 += partial[(long long)(b + 2 * kRedThreads) * nw + k];
+    s3 += partial[(long long)(b + 3 * kRedThreads) * nw + k];
+  }
+  for (; b < nblocks; b += kRedThreads) s0 += partial[(long long)b * nw + k];
   const bool add_dos = dos && (omega == nullptr || omega[k] == 0.0);
   if (add_dos)
-    for (int b = threadIdx.x; b < ndos; b += blockDim.x) sd += dos[b];
-  __shared__ double r1[kThreads], r2[kThreads];
-  r1[threadIdx.x] = s;
-  r2[threadIdx.x] = sd;
+    for (int i = threadIdx.x; i < ndos; i += kRedThreads) sd += dos[i];
+  double v = ((s0 + s1) + (s2 + s3)) + sd;
+  __shared__ double red[kRedThreads / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      r1[threadIdx.x] += r1[threadIdx.x + o];
-      r2[threadIdx.x] += r2[threadIdx.x + o];
-    }
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    v = red[threadIdx.x];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[k] = scale * v;
   }
-  if (threadIdx.x == 0) out[k] = scale * (r1[0] + r2[0]);
 }
 
 }  // namespace
@@ -841,7 +831,7 @@ size_t static_piece_bytes(int fp64) { return fp64 ? sizeof(Piece<double>) : size
 cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
                           const StaticBufs &sb, int nblocks, unsigned long long *counters, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(sb.next, 0, 2 * sizeof(int), s);  // batch counter, FP64 list size
+  cudaError_t e = cudaMemsetAsync(sb.next, 0, sizeof(int), s);  // batch counter
   if (e != cudaSuccess) return e;
   const long long nbatch = static_batches(g.ntet);
   if (fp64)
@@ -849,10 +839,6 @@ cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const v
   else
     k_static<false><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (!fp64) {
-    k_static_f64<<<kSMs * 4, kThreads, 0, s>>>(sb);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
   long long tb = (nbatch * 32 + kThreads - 1) / kThreads;
   const int tblocks = (int)(tb < kSMs * 16 ? tb : kSMs * 16);
   if (fp64) k_static_tab<true><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
@@ -894,7 +880,7 @@ cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, i
 
 cudaError_t launch_reduce(const double *partial, int nblocks, int nw, double scale, const double *dos,
                           int ndos, const double *omega, double *out, cudaStream_t s) {
-  k_reduce<<<nw, kThreads, 0, s>>>(partial, nblocks, nw, scale, dos, ndos, omega, out);
+  k_reduce<<<nw, kRedThreads, 0, s>>>(partial, nblocks, nw, scale, dos, ndos, omega, out);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,22 @@ template <typename T> __device__ __forceinline__ T pick5(const T t[5], int idx) 
   return r;
 }
 
+// 6 (-1)^m / ((m+4)(m+3)(m+2)(m+1)): coefficients of the Taylor series below (k = m + 4)
+template <typename T, int N> struct TaylorCoef {
+  T v[N];
+  constexpr TaylorCoef() : v() {
+    for (int m = 0; m < N; ++m) {
+      const T c = T(6) / (T(m + 4) * T(m + 3) * T(m + 2) * T(m + 1));
+      v[m] = (m & 1) ? -c : c;
+    }
+  }
+};
+__constant__ constexpr TaylorCoef<float, Num<float>::kmax + 4> kTayF{};
+__constant__ constexpr TaylorCoef<double, Num<double>::kmax + 4> kTayD{};
+template <typename T> __device__ __forceinline__ T taylor_coef(int m);
+template <> __device__ __forceinline__ float taylor_coef<float>(int m) { return kTayF.v[m]; }
+template <> __device__ __forceinline__ double taylor_coef<double>(int m) { return kTayD.v[m]; }
+
 // Taylor series of the divided difference g[t_i..t_j] (n = j - i) of knots clustered about
 // their mean c != 0, in the scaled offsets e = (t - c)/c (no powers of 1/c that could
 // overflow):  g[t_i..t_j] = sum_{k=n}^{3} g^(k)(c)/k! c^(k-n) h_{k-n}(e)
@@ -126,9 +142,7 @@ template <typename T> __device__ __noinline__ T dd_taylor(const T t[5], int i, i
 #pragma unroll
       for (int l = 1; l < 5; ++l) h[l] = h[l - 1] + e[l] * h[l];
     }
-    const T kk = T(k);
-    T coef = T(6) / (kk * (kk - T(1)) * (kk - T(2)) * (kk - T(3)));
-    if ((k - 4) & 1) coef = -coef;
+    const T coef = taylor_coef<T>(k - 4);  // 6 (-1)^(k-4) / (k (k-1) (k-2) (k-3))
     const T term = coef * h[4];
     high += term;
     big = tabs(term) > big ? tabs(term) : big;

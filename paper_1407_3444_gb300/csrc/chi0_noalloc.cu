@@ -68,10 +68,10 @@ int scratch_base(unsigned char **out) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t occ, emp, occq, empq, E32, Eq32, C32, W2, next, counters, tq, tq_n, list64, res64, part, dos, total;
+  size_t occ, emp, occq, empq, E32, Eq32, C32, W2, next, counters, tq, tq_n, part, dos, total;
 };
 
-Layout layout(const Grid &g, int w, int fp64, int cma, int dtype, int cap64) {
+Layout layout(const Grid &g, int w, int fp64, int cma, int dtype) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -88,12 +88,10 @@ Layout layout(const Grid &g, int w, int fp64, int cma, int dtype, int cap64) {
   L.Eq32 = take(fp64 ? 0 : sizeof(float) * g.nc * g.nb);
   L.C32 = take((!fp64 && !cma && dtype == CHI0_C128) ? 8 * (size_t)g.nc * g.norb * g.nb : 0);
   L.W2 = take(cma ? 0 : (fp64 ? 8 : 4) * (size_t)g.nc * w * w);
-  L.next = take(2 * sizeof(int));
+  L.next = take(sizeof(int));
   L.counters = take(4 * sizeof(unsigned long long));
   L.tq = take(static_piece_bytes(fp64) * (size_t)nbatch * kNoallocTabCap);
   L.tq_n = take(sizeof(int) * (size_t)nbatch);
-  L.list64 = take(sizeof(int) * (size_t)cap64);
-  L.res64 = take(sizeof(double) * (size_t)cap64);
   L.part = take(sizeof(double) * (size_t)(2 * nbatch));
   L.dos = take(sizeof(double) * (size_t)static_blocks());
   L.total = o;
@@ -137,8 +135,7 @@ extern "C" int chi0_static_noalloc(const chi0_kgrid_t *kg, chi0_band_window_t wi
   const int dtype = op.cma ? CHI0_C128 : kg->evec_dtype;
   const int w = win.hi - win.lo;
   const long long nbatch = static_batches(g.ntet);
-  const int cap64 = (int)(nbatch < 4096 ? 4096 : nbatch);
-  const Layout L = layout(g, w, fp64, op.cma, dtype, cap64);
+  const Layout L = layout(g, w, fp64, op.cma, dtype);
   if (L.total > (size_t)CHI0_NOALLOC_SCRATCH_BYTES)
     return err(CHI0_EINVAL, "this mesh needs %zu bytes of scratch; chi0_static_noalloc has %zu", L.total,
                (size_t)CHI0_NOALLOC_SCRATCH_BYTES);
@@ -163,8 +160,7 @@ extern "C" int chi0_static_noalloc(const chi0_kgrid_t *kg, chi0_band_window_t wi
   int *next = (int *)(base + L.next);
   unsigned long long *counters = (unsigned long long *)(base + L.counters);
   double *part = (double *)(base + L.part), *dos = (double *)(base + L.dos);
-  StaticBufs sb{base + L.tq, (int *)(base + L.tq_n), (int *)(base + L.list64), (double *)(base + L.res64),
-                cap64, part, next, kNoallocTabCap};
+  StaticBufs sb{base + L.tq, (int *)(base + L.tq_n), part, next, kNoallocTabCap};
   Tet tet{nullptr, nullptr, 1.0 / (6.0 * g.n[0] * g.n[1] * g.n[2])};
   const double scale = op.sign == CHI0_SIGN_PAPER ? -2.0 : 2.0;
   cudaError_t e;
