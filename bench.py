@@ -39,8 +39,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--nq", type=int, default=256)
-    ap.add_argument("--n", type=int, default=48)
+    ap.add_argument("--workload", default="cr", choices=["cr", "free", "fese", "sweep", "large"],
+                    help="cr: Cr-like 9-orbital static (default); free: free-electron Lindhard; fese: "
+                         "FeSe-like dynamic; sweep: 40-band window sweep (static); large: 80-band 72^3 dynamic")
+    ap.add_argument("--nq", type=int, default=None, help="q points per step (default: the workload's)")
+    ap.add_argument("--n", type=int, default=None, help="k mesh cubes per axis (cubic workloads)")
+    ap.add_argument("--cpu-sample-w", type=int, default=16, help="frequencies in the CPU sample (dynamic)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-q", type=int, default=1)
@@ -56,31 +60,76 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float) -> float:
+    """Maximum of a host value over the ranks of the default process group (the timing rule:
+    the whole job is as slow as its slowest rank); identity without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world_size: int, units_per_rank: float, max_ms: float) -> float:
+    """Units all ranks processed per second (every rank runs its own replica)."""
+    return world_size * units_per_rank / (max_ms * 1e-3)
+
+
 def make_workload(args, nproc):
-    return wl.cr_like(n=args.n, nq=args.nq, nproc=nproc)
+    """The selected workload (the five synthetic stand-ins of the paper's materials)."""
+    k = args.workload
+    if k == "cr":
+        return wl.cr_like(n=args.n or 48, nq=args.nq or 256, nproc=nproc)
+    if k == "free":
+        return wl.free_electron(n=args.n or 16, nq=args.nq or 32)
+    if k == "fese":
+        nq = args.nq or 64
+        n = (args.n, args.n, max(1, args.n // 4)) if args.n else (64, 64, 16)
+        return wl.fese_like(n=n, nq=64, nproc=nproc,
+                            qfracs=[np.array([0.5, 0.5, 0.0]) * (j + 1) / 64 for j in range(64)][:nq])
+    if k == "sweep":
+        W = wl.band_sweep(n=args.n or 32, nq=args.nq or 128, nproc=nproc)
+        W.omega = None  # the static sweep (the dynamic one: chi0_dynamic on the same plan)
+        return W
+    W = wl.large_mixed(n=args.n or 72, nq=args.nq or 128, nproc=nproc)
+    return W
 
 
 def workload_config(W, args):
+    names = {"cr": "Cr-like 9-orbital static chi0 (Gamma-X-M-Gamma, explicit k+q eigen-data, E_F at 6/9)",
+             "free": "free-electron static Lindhard chi0 (open [-pi,pi]^3 mesh, |M|^2 = 1, 32 q along (100))",
+             "fese": "FeSe-like 10-orbital dynamic chi0 (Gamma-M, explicit k+q, 512 w in [0,2] eV, E_F at 6/10)",
+             "sweep": "40-band random model, static chi0, on-grid q with per-q band windows 4..40",
+             "large": "80-band random model, dynamic chi0, on-grid q, 256 w in [0,2] eV"}
+    nw = 1 if W.omega is None else len(W.omega)
+    inb = sum((q.Cq.nbytes if q.Cq is not None else 0) + (q.Eq.nbytes if q.Eq is not None else 0) for q in W.qs)
+    inb += W.E.nbytes + (W.C.nbytes if W.C is not None else 0)
     return {
-        "workload": "Cr-like 9-orbital static chi0: %d^3 k mesh (%d tetrahedra), 9 bands, %d q on "
-                    "Gamma-X-M-Gamma with explicit k+q eigen-data, E_F at 6/9 filling" % (args.n, W.ntet, len(W.qs)),
-        "ntet": W.ntet, "nbands": W.nb, "nq": len(W.qs), "nomega": 1,
+        "workload": "%s: %s k mesh (%d tetrahedra), %d bands, %d q, %d w" % (
+            names[args.workload], "x".join(str(x) for x in W.n), W.ntet, W.nb, len(W.qs), nw),
+        "ntet": W.ntet, "nbands": W.nb, "nq": len(W.qs), "nomega": nw,
         "nominal_evals_per_step": W.nominal_evals(),
-        "evec_dtype": str(W.C.dtype),
-        "l2": "inputs larger than L2 (explicit k+q eigen-data %.1f GB per step)" % (
-            sum(q.Cq.nbytes + q.Eq.nbytes for q in W.qs) / 1e9),
+        "evec_dtype": str(W.C.dtype) if W.C is not None else None,
+        "l2": "inputs larger than L2 (%.1f GB of eigen-data read per step)" % (inb / 1e9),
     }
 
 
-def cpu_sample(W, nq_sample, nthreads):
-    """Oracle on q points 1 .. nq_sample (whole tetrahedron set; q 0 is Gamma)."""
+def cpu_sample(W, nq_sample, nthreads, nw_sample=16):
+    """Oracle on q points 1 .. nq_sample (whole tetrahedron set; q 0 is Gamma on the paths);
+    dynamic workloads: the first nw_sample frequencies."""
     import oracle
     oracle.build()
+    qs = W.qs[1:1 + nq_sample] if len(W.qs) > 1 else W.qs[:1]
+    om = None if W.omega is None else W.omega[:nw_sample]
     t0 = time.perf_counter()
-    vals = [oracle.chi0_q(W, q, nthreads=nthreads) for q in W.qs[1:1 + nq_sample]]
+    vals = [oracle.chi0_q(W, q, omega=om, nthreads=nthreads) for q in qs]
     dt = time.perf_counter() - t0
-    evals = W.ntet * (W.window[1] - W.window[0]) ** 2 * nq_sample
-    return np.array(vals), dt, evals
+    evals = sum(W.ntet * ((q.window or W.window)[1] - (q.window or W.window)[0]) ** 2 for q in qs) * (
+        1 if om is None else len(om))
+    return vals, dt, evals
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -154,8 +203,33 @@ def fp32_peak_tflops(sm_mhz):
 # FP32 operations (FFMA counted twice, FADD, FMUL) of the mixed static weight kernels per
 # final tetrahedron on this workload, from the ncu instruction counters of
 # profiles/static_weights_cr_like_48.md; and their DRAM bytes per final tetrahedron.
-FLOPS_PER_PIECE_MIXED = 207.0
-TRAFFIC_PER_PIECE_MIXED = None
+FLOPS_PER_PIECE_MIXED = 205.5
+TRAFFIC_PER_PIECE_MIXED = 3.74
+
+
+def run_step(P, W):
+    """One pass of the whole path over the step's q points (static or dynamic)."""
+    return P.static() if W.omega is None else P.dynamic(W.omega)
+
+
+def to_host(out):
+    if isinstance(out, tuple):
+        return tuple(o.cpu().numpy() if hasattr(o, "cpu") else o for o in out)
+    return out.cpu().numpy() if hasattr(out, "cpu") else out
+
+
+def rel_err(a, b):
+    """Normwise error per q (max over w of |a - b| / max over w of |b|), max over q; Re and Im
+    separately for dynamic results (the larger of the two is returned)."""
+    if isinstance(a, tuple):
+        return max(rel_err(x, y) for x, y in zip(a, b))
+    a = np.atleast_2d(np.asarray(a, dtype=np.float64).T).T if np.ndim(a) == 1 else np.asarray(a)
+    b = np.atleast_2d(np.asarray(b, dtype=np.float64).T).T if np.ndim(b) == 1 else np.asarray(b)
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    scale = np.max(np.abs(b), axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return float(np.max(np.max(np.abs(a - b), axis=1) / scale))
 
 
 # ------------------------------------------------------------------------------ main
@@ -169,7 +243,7 @@ def run_reference(args):
     times = []
     evals = 0
     for s in range(args.warmup + args.steps):
-        _, dt, ev = cpu_sample(W, args.cpu_sample_q, cores)
+        _, dt, ev = cpu_sample(W, args.cpu_sample_q, cores, args.cpu_sample_w)
         if s >= args.warmup:
             times.append(dt)
             evals = ev
@@ -180,7 +254,8 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(W, args),
             "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": "q points 1..%d of the workload, all tetrahedra" % args.cpu_sample_q},
+                             "sample": "q points 1..%d of the workload, all tetrahedra%s" % (
+                                 args.cpu_sample_q, "" if W.omega is None else ", first %d w" % args.cpu_sample_w)},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -194,10 +269,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cores = len(os.sched_getaffinity(0))
-        vals, dt, ev = cpu_sample(W, args.cpu_sample_q, cores)
+        vals, dt, ev = cpu_sample(W, args.cpu_sample_q, cores, args.cpu_sample_w)
         cpu = {"value": ev / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
-               "sample": "q points 1..%d of the workload (all %d tetrahedra, 81 pairs), %.1f s"
-                         % (args.cpu_sample_q, W.ntet, dt)}
+               "sample": "q points 1..%d of the workload (all %d tetrahedra%s), %.1f s"
+                         % (args.cpu_sample_q, W.ntet, "" if W.omega is None else ", first %d w" % args.cpu_sample_w,
+                            dt)}
         oracle_vals = vals
     import torch
     import torch.distributed as dist
@@ -217,7 +293,7 @@ def run_ours(args):
     Pd = chi0.Plan(W, precision="fp64", device=True, profile=False, staged=dev) if args.fp64_steps > 0 else None
     nominal = W.nominal_evals()
     for _ in range(args.warmup):
-        Pm.static()
+        run_step(Pm, W)
     torch.cuda.synchronize()
     s0 = Pm.stats()
     clocks = Clocks(local)
@@ -228,18 +304,14 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        out_m = Pm.static()
+        out_m = run_step(Pm, W)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps)
     s1 = Pm.stats()
-    value = ws * nominal / (ms * 1e-3)
+    value = whole_job_rate(ws, nominal, ms)
     def stage_ms(k):
         n = s1.launches[k] - s0.launches[k]
         return (s1.time_ms[k] - s0.time_ms[k]) / n if n else None
@@ -249,28 +321,29 @@ def run_ours(args):
     pieces_timed = s1.pieces - s0.pieces
     static_launches = s1.launches[chi0.CHI0_K_STATIC] - s0.launches[chi0.CHI0_K_STATIC]
     stages = {name: stage_ms(k) for name, k in (("overlap", chi0.CHI0_K_OVERLAP), ("weights", chi0.CHI0_K_STATIC),
+                                                 ("dynamic", chi0.CHI0_K_DYNAMIC),
                                                  ("reduce", chi0.CHI0_K_REDUCE), ("bands", chi0.CHI0_K_BANDS),
                                                  ("dos", chi0.CHI0_K_DOS))}
     counters = Pm.counters()
-    mixed = out_m.cpu().numpy()
+    mixed = to_host(out_m)
 
     # all-FP64 GPU form on the same resident inputs
     fp64 = None
     ms64 = None
     err_mixed = None
     if Pd is not None:
-        Pd.static()
+        run_step(Pd, W)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.fp64_steps):
-            out_d = Pd.static()
+            out_d = run_step(Pd, W)
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1) / args.fp64_steps
-        fp64 = out_d.cpu().numpy()
-        err_mixed = float(np.max(np.abs(mixed - fp64) / np.abs(fp64)))
+        fp64 = to_host(out_d)
+        err_mixed = rel_err(mixed, fp64)
 
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
@@ -281,26 +354,28 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             Ph = chi0.Plan(W, precision="mixed", device=False, staged=host)
-            out_h = Ph.static()
+            out_h = run_step(Ph, W)
             Ph.close()
             t1 = time.perf_counter()
             if s > 0:
                 t_e2e.append(t1 - t0)
         T = sum(t_e2e) / len(t_e2e)
         e2e = {"value": nominal / T, "unit": "evals/s", "h2d_bytes_per_step": host.nbytes(),
-               "d2h_bytes_per_step": int(out_h.nbytes), "ms_per_step": T * 1e3,
-               "max_abs_diff_vs_device": float(np.max(np.abs(out_h - mixed)))}
+               "d2h_bytes_per_step": int(sum(o.nbytes for o in out_h) if isinstance(out_h, tuple) else out_h.nbytes),
+               "ms_per_step": T * 1e3, "rel_diff_vs_device": rel_err(out_h, mixed)}
         del host
 
     peaks, kind = measured_peaks()
     smax = float(peaks.get("sm_max_mhz", 2070.0))
     pieces_per_launch = pieces_timed / max(1, static_launches)
     pk = fp32_peak_tflops(smax)
-    ach = FLOPS_PER_PIECE_MIXED * pieces_per_launch / (k_static_ms * 1e-3) / 1e12 if k_static_ms else None
+    ach = (FLOPS_PER_PIECE_MIXED * pieces_per_launch / (k_static_ms * 1e-3) / 1e12
+           if k_static_ms and args.workload == "cr" else None)
     roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
             "frac": ach / pk if ach is not None else None,
-            "traffic": TRAFFIC_PER_PIECE_MIXED * pieces_per_launch if TRAFFIC_PER_PIECE_MIXED else None,
-            "kernel": "static weights (k_static + k_static_f64 + k_static_tab, mixed)",
+            "traffic": (TRAFFIC_PER_PIECE_MIXED * pieces_per_launch
+                        if TRAFFIC_PER_PIECE_MIXED and args.workload == "cr" else None),
+            "kernel": "static weights (k_static + k_static_tab, mixed)",
             "kernel_ms": k_static_ms, "units_per_launch": pieces_per_launch,
             "flops_per_unit": FLOPS_PER_PIECE_MIXED, "unit_name": "final tetrahedron",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % smax}
@@ -308,9 +383,10 @@ def run_ours(args):
     # (complex128 inputs) read once, |M|^2 written once
     ovl_ms = stages["overlap"]
     ovl = None
-    if ovl_ms:
+    if ovl_ms and W.C is not None:
         nc, no, w = W.ncorner, W.norb, W.nb
-        ovl_bytes = nc * no * w * (8 + 16) + nc * w * w * 4
+        kq = W.qs[0].Cq.itemsize if W.qs[0].Cq is not None else 8
+        ovl_bytes = nc * no * w * (8 + kq) + nc * w * w * 4
         ovl = {"bound": "hbm", "achieved": ovl_bytes / (ovl_ms * 1e-3) / 1e9, "peak": float(peaks.get("hbm_gbs", 6800.0)),
                "unit": "GB/s", "bytes_per_launch": ovl_bytes, "kernel_ms": ovl_ms}
         ovl["frac"] = ovl["achieved"] / ovl["peak"]
@@ -319,10 +395,18 @@ def run_ours(args):
         err_oracle = None
         if cpu is not None:
             nq = len(oracle_vals)
-            err_oracle = {"mixed_gpu": float(np.max(np.abs(mixed[1:1 + nq] - oracle_vals) / np.abs(oracle_vals))),
-                          "q_points": nq}
+            i0 = 1 if len(W.qs) > 1 else 0
+
+            def sample(x):
+                if isinstance(x, tuple):
+                    return tuple(y[i0:i0 + nq, :args.cpu_sample_w] for y in x)
+                return x[i0:i0 + nq]
+
+            ref = (tuple(np.array([v[k] for v in oracle_vals]) for k in (0, 1))
+                   if W.omega is not None else np.array(oracle_vals))
+            err_oracle = {"mixed_gpu": rel_err(sample(mixed), ref), "q_points": nq}
             if fp64 is not None:
-                err_oracle["fp64_gpu"] = float(np.max(np.abs(fp64[1:1 + nq] - oracle_vals) / np.abs(oracle_vals)))
+                err_oracle["fp64_gpu"] = rel_err(sample(fp64), ref)
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",

@@ -433,15 +433,32 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
        b += ((long long)gridDim.x * blockDim.x) >> 5) {
     const int n = sb.tq_n[b];
     double acc = 0.0;
+    unsigned any64 = 0u;
     for (int slot = lane; slot < n; slot += 32) {
       const Piece<T> pc = tq[b * sb.tcap + slot];
       if constexpr (FP64) {
         acc += pc.w * inv_sum_table(pc.d, pc.f);
-      } else if (pc.i64 >= 0) {  // near-degenerate knots: the table in FP64 (rare)
-        double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
-        acc += (double)pc.w * inv_sum_table(xd, fd);
+      } else if (pc.i64 >= 0) {
+        any64 = 1u;  // near-degenerate knots: the FP64 table, below
       } else {
         acc += (double)(pc.w * inv_sum_long(pc.d, pc.f));
+      }
+    }
+    if constexpr (!FP64) {
+      // FP64 entries (rare): four lanes, one vertex j each, to cut the FP64 latency
+      if (__any_sync(kFull, any64)) {
+        for (int slot = 0; slot < n; ++slot) {
+          const Piece<T> pc = tq[b * sb.tcap + slot];
+          if (pc.i64 < 0) continue;
+          double t = 0.0;
+          if (lane < 4) {
+            double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
+            t = inv_term_table(xd, fd, lane);
+          }
+          t += __shfl_xor_sync(kFull, t, 1);
+          t += __shfl_xor_sync(kFull, t, 2);
+          if (lane == 0) acc += (double)pc.w * t;
+        }
       }
     }
     const double v = warp_sum(acc);

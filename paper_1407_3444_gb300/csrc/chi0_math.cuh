@@ -235,6 +235,29 @@ template <typename T> __device__ T series_sum(const T x[4], const T f[4]) {
   return sum * ci;
 }
 
+// f_j (1/V) int lambda_j / X for one vertex j (sorted knots, any signs; PV across X = 0)
+template <typename T> __device__ T inv_term_table(const T xin[4], const T f[4], int jj) {
+  T x[4] = {xin[0], xin[1], xin[2], xin[3]};
+  T s = tabs(x[0]) > tabs(x[3]) ? tabs(x[0]) : tabs(x[3]);
+  if (s == T(0)) return T(0);
+  const int nz = (x[0] == T(0)) + (x[1] == T(0)) + (x[2] == T(0)) + (x[3] == T(0));
+  if (nz >= 3) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) x[l] = x[l] == T(0) ? T(kFloor) * s : x[l];
+    T dummy[4] = {T(0), T(0), T(0), T(0)};
+    sort4(x, dummy);
+  }
+  const T si = T(1) / s;
+  T t5[5];
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const int src = l <= jj ? l : l - 1;
+    t5[l] = (src == 0 ? x[0] : src == 1 ? x[1] : src == 2 ? x[2] : x[3]) * si;
+  }
+  const T fj = jj == 0 ? f[0] : jj == 1 ? f[1] : jj == 2 ? f[2] : f[3];
+  return fj * dd5(t5) * si;
+}
+
 // sum_j f_j (1/V) int lambda_j / X for sorted knots x (any signs; PV across X = 0)
 template <typename T> __device__ T inv_sum_table(const T xin[4], const T f[4]) {
   T x[4] = {xin[0], xin[1], xin[2], xin[3]};

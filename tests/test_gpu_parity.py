@@ -169,3 +169,32 @@ def test_dynamic_free_electron_open_grid(C, O):
     gr, gi = run_dynamic(C, W, "fp64", omega)
     assert nerr(gr, np.array(ref_r)) < 1e-12
     assert nerr(gi[1:], np.array(ref_i)[1:]) < 1e-12
+
+
+# ------------------------------------------------------------------------ full sizes (sampled)
+def test_cr_like_full_size_sampled_q(C, O):
+    """The bench workload's mesh and bands (48^3, 663,552 tetrahedra, 9 bands) at two of its
+    q points (one on Gamma-X, one on M-Gamma), FP64 and mixed, against the oracle."""
+    import os
+    qs = wl.path_points([(0, 0, 0), (0.5, 0, 0), (0.5, 0.5, 0), (0, 0, 0)], 256)[[37, 201]]
+    W = wl.cr_like(n=48, nq=2, qfracs=qs, nproc=min(16, os.cpu_count() or 1))
+    ref = np.array([O.chi0_q(W, q) for q in W.qs])
+    for prec in ("fp64", "mixed"):
+        got = run_static(C, W, prec)
+        assert nerr(got[:, None], ref[:, None]) < TOL[prec], (prec, got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_band_sweep_40_bands_windows(C, O, prec):
+    """40-band random model (the band-truncation sweep's generator) on a 10^3 mesh: on-grid
+    shifts with per-q windows of 4..40 bands around E_F, static and dynamic."""
+    W = wl.band_sweep(n=10, nb=40, nq=4, nw=24)
+    omega, W.omega = W.omega, None
+    ref = O.chi0(W)
+    got = run_static(C, W, prec)
+    assert nerr(got[:, None], ref[:, None]) < TOL[prec]
+    W.qs = W.qs[:2]
+    ref_r, ref_i = zip(*[O.chi0_q(W, q, omega=omega) for q in W.qs])
+    gr, gi = run_dynamic(C, W, prec, omega)
+    assert nerr(gr, np.array(ref_r)) < TOL[prec]
+    assert nerr(gi, np.array(ref_i)) < TOL[prec]
