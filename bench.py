@@ -201,10 +201,15 @@ def fp32_peak_tflops(sm_mhz):
 
 
 # FP32 operations (FFMA counted twice, FADD, FMUL) of the mixed static weight kernels per
-# final tetrahedron on this workload, from the ncu instruction counters of
-# profiles/static_weights_cr_like_48.md; and their DRAM bytes per final tetrahedron.
+# final tetrahedron on the Cr-like 48^3 workload, from ncu's instruction counters of
+# k_static + k_static_tab (8 q, 13.65 M final tetrahedra per launch); and their DRAM bytes
+# per final tetrahedron.
 FLOPS_PER_PIECE_MIXED = 205.5
 TRAFFIC_PER_PIECE_MIXED = 3.74
+# The same for k_dynamic per (final tetrahedron, frequency) on the FeSe-like workload
+# (None until counted).
+FLOPS_PER_PIECE_W_DYN = None
+TRAFFIC_PER_PIECE_W_DYN = None
 
 
 def run_step(P, W):
@@ -367,18 +372,37 @@ def run_ours(args):
 
     peaks, kind = measured_peaks()
     smax = float(peaks.get("sm_max_mhz", 2070.0))
-    pieces_per_launch = pieces_timed / max(1, static_launches)
     pk = fp32_peak_tflops(smax)
-    ach = (FLOPS_PER_PIECE_MIXED * pieces_per_launch / (k_static_ms * 1e-3) / 1e12
-           if k_static_ms and args.workload == "cr" else None)
-    roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-            "frac": ach / pk if ach is not None else None,
-            "traffic": (TRAFFIC_PER_PIECE_MIXED * pieces_per_launch
-                        if TRAFFIC_PER_PIECE_MIXED and args.workload == "cr" else None),
-            "kernel": "static weights (k_static + k_static_tab, mixed)",
-            "kernel_ms": k_static_ms, "units_per_launch": pieces_per_launch,
-            "flops_per_unit": FLOPS_PER_PIECE_MIXED, "unit_name": "final tetrahedron",
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % smax}
+    peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % smax
+    if W.omega is None:
+        pieces_per_launch = pieces_timed / max(1, static_launches)
+        ach = (FLOPS_PER_PIECE_MIXED * pieces_per_launch / (k_static_ms * 1e-3) / 1e12
+               if k_static_ms and args.workload == "cr" else None)
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk if ach is not None else None,
+                "traffic": (TRAFFIC_PER_PIECE_MIXED * pieces_per_launch
+                            if TRAFFIC_PER_PIECE_MIXED and args.workload == "cr" else None),
+                "kernel": "static weights (k_static + k_static_tab, mixed)",
+                "kernel_ms": k_static_ms, "units_per_launch": pieces_per_launch,
+                "flops_per_unit": FLOPS_PER_PIECE_MIXED, "unit_name": "final tetrahedron",
+                "peak_source": peak_src}
+    else:
+        # k_dynamic: one launch = one pass of <= 256 frequencies over every final tetrahedron
+        dyn_launches = s1.launches[chi0.CHI0_K_DYNAMIC] - s0.launches[chi0.CHI0_K_DYNAMIC]
+        k_dyn_ms = stage_ms(chi0.CHI0_K_DYNAMIC)
+        pieces_per_launch = pieces_timed / max(1, dyn_launches)
+        w_per_launch = len(W.omega) / max(1, -(-len(W.omega) // chi0.DYNAMIC_MAX_NW))
+        units = pieces_per_launch * w_per_launch
+        ach = (FLOPS_PER_PIECE_W_DYN * units / (k_dyn_ms * 1e-3) / 1e12
+               if k_dyn_ms and FLOPS_PER_PIECE_W_DYN and args.workload == "fese" else None)
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk if ach is not None else None,
+                "traffic": (TRAFFIC_PER_PIECE_W_DYN * units
+                            if TRAFFIC_PER_PIECE_W_DYN and args.workload == "fese" else None),
+                "kernel": "dynamic weights (k_dynamic, mixed)",
+                "kernel_ms": k_dyn_ms, "units_per_launch": units,
+                "flops_per_unit": FLOPS_PER_PIECE_W_DYN, "unit_name": "(final tetrahedron, w)",
+                "peak_source": peak_src}
     # the overlap kernel is bound by HBM: eigenvector blocks at k (complex64 copy) and at k+q
     # (complex128 inputs) read once, |M|^2 written once
     ovl_ms = stages["overlap"]

@@ -36,7 +36,7 @@ struct chi0_plan {
   void *Cq_stage = nullptr;
   unsigned long long *counters_d = nullptr;
   short *occ_d = nullptr, *emp_d = nullptr, *occq_d = nullptr, *empq_d = nullptr;
-  float *E32_d = nullptr, *Eq32_d = nullptr;  // energies - eF in FP32 (mixed precision)
+  float *E32_d = nullptr, *Eq32_d = nullptr;  // energies - eF in FP32 (mixed precision): hi, then lo
   void *C32_d = nullptr;                      // complex64 copy of complex128 eigenvectors (mixed)
   int *next_d = nullptr;                      // [2] batch counter, FP64 list size
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
@@ -238,10 +238,11 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     CK(p, cudaMalloc(&p->tq_n_d, sizeof(int) * (size_t)nbatch));
   }
   if (op.precision == CHI0_PREC_MIXED) {
-    CK(p, cudaMalloc(&p->E32_d, sizeof(float) * (size_t)g.nc * g.nb));
-    CK(p, cudaMalloc(&p->Eq32_d, sizeof(float) * (size_t)g.nc * g.nb));
+    CK(p, cudaMalloc(&p->E32_d, 2 * sizeof(float) * (size_t)g.nc * g.nb));
+    CK(p, cudaMalloc(&p->Eq32_d, 2 * sizeof(float) * (size_t)g.nc * g.nb));
   }
-  CK(p, launch_bands(p->E_d, g.nc, g.nb, g.ef, p->occ_d, p->emp_d, p->E32_d, p->stream));
+  CK(p, launch_bands(p->E_d, g.nc, g.nb, g.ef, p->occ_d, p->emp_d, p->E32_d, p->stream,
+                     p->E32_d ? p->E32_d + (size_t)g.nc * g.nb : nullptr));
   if (op.precision == CHI0_PREC_MIXED && !op.cma && p->dtype == CHI0_C128) {
     const long long ne = g.nc * (long long)g.norb * g.nb;
     CK(p, cudaMalloc(&p->C32_d, 8 * (size_t)ne));
@@ -423,13 +424,17 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     const short *empq = p->emp_d;
     const void *Ek = fp64 ? (const void *)p->E_d : (const void *)p->E32_d;
     const void *Ekq = Ek;
+    const size_t ncb = (size_t)p->g.nc * p->g.nb;
+    const float *Eklo = fp64 ? nullptr : p->E32_d + ncb, *Ekqlo = Eklo;
     if (q.Eq) {
       tm.start(CHI0_K_BANDS);
-      CK(p, launch_bands(q.Eq, p->g.nc, p->g.nb, p->g.ef, p->occq_d, p->empq_d, fp64 ? nullptr : p->Eq32_d, s));
+      CK(p, launch_bands(q.Eq, p->g.nc, p->g.nb, p->g.ef, p->occq_d, p->empq_d, fp64 ? nullptr : p->Eq32_d, s,
+                         fp64 ? nullptr : p->Eq32_d + ncb));
       p->stats.kernels += 1;
       tm.stop();
       empq = p->empq_d;
       Ekq = fp64 ? (const void *)q.Eq : (const void *)p->Eq32_d;
+      if (!fp64) Ekqlo = p->Eq32_d + ncb;
     }
     if (!dyn) {
       StaticBufs sb{p->tq_d, p->tq_n_d, p->partR, p->next_d, static_tab_cap()};
@@ -449,7 +454,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
         DynBufs db{p->partR, p->partI, p->next_d};
         tm.start(CHI0_K_DYNAMIC);
         CK(p, launch_dynamic(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
-                             om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s));
+                             om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s, Eklo, Ekqlo));
         p->stats.kernels += 1;
         tm.stop();
         tm.start(CHI0_K_REDUCE);

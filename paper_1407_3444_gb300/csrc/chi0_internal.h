@@ -64,9 +64,10 @@ cudaError_t launch_overlap(const Grid &g, const double *E, const void *C, int dt
 cudaError_t launch_c128_to_c64(const void *in, void *out, long long n, cudaStream_t s);
 
 // band bounds per corner: occ[c] (1 + highest occupied band), emp[c] (lowest empty band);
-// E32 (optional) receives (float)(E - ef)
+// E32 (optional) receives (float)(E - ef); E32lo (optional) the remainder
+// (float)((E - ef) - E32), so that E32 + E32lo carries E - ef to ~2^-48 relative
 cudaError_t launch_bands(const double *E, long long nc, int nb, double ef, short *occ, short *emp, float *E32,
-                         cudaStream_t s);
+                         cudaStream_t s, float *E32lo = nullptr);
 
 // Work buffers of the static kernels (device memory owned by the plan).
 struct StaticBufs {
@@ -101,7 +102,8 @@ struct DynBufs {
 cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                            const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
                            const double *omega, int nw, const DynBufs &db, int nblocks,
-                           unsigned long long *counters, cudaStream_t s);
+                           unsigned long long *counters, cudaStream_t s, const float *Eklo,
+                           const float *Ekqlo);
 int dynamic_persistent_blocks(int fp64);
 
 // Gamma: intraband q -> 0 limit, tetrahedron DOS at eF: partial[nblocks]

@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(kThreads) k_overlap_small(Grid g, const CT *__
 // E32 (optional) receives the energies relative to eF in FP32 for the mixed-precision path.
 __global__ void __launch_bounds__(kThreads) k_bands(const double *__restrict__ E, long long nc, int nb,
                                                     double ef, short *__restrict__ occ,
-                                                    short *__restrict__ emp, float *__restrict__ E32) {
+                                                    short *__restrict__ emp, float *__restrict__ E32,
+                                                    float *__restrict__ E32lo) {
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
        c += (long long)gridDim.x * blockDim.x) {
     int o = 0, e = nb;
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_bands(const double *__restrict__ E
       if (x < 0.0) o = b + 1;
       if (x > 0.0 && e == nb) e = b;
       if (E32) E32[c * nb + b] = (float)x;
+      if (E32lo) E32lo[c * nb + b] = (float)(x - (double)(float)x);
     }
     occ[c] = (short)o;
     emp[c] = (short)e;
@@ -490,31 +492,44 @@ template <typename T> __device__ __forceinline__ void kadd_t(T &sum, T &comp, T 
   sum = t;
 }
 
-// 1/(D - w) (sgn 0) or 1/(D + w) (sgn 1) for knots d near w: divided-difference table
-// (principal value across D = w); one out-of-line copy shared by every call site
+// sum_j f_j (1/V) int lambda_j / X for knots x of X near 0: divided-difference table (principal
+// value across X = 0); one out-of-line copy shared by every call site
 template <bool FP64>
 __device__ __noinline__ typename std::conditional<FP64, double, float>::type near_term(
-    const typename std::conditional<FP64, double, float>::type *d,
-    const typename std::conditional<FP64, double, float>::type *f,
-    typename std::conditional<FP64, double, float>::type om, int sgn, float tau, int &nfp64) {
+    const typename std::conditional<FP64, double, float>::type *x,
+    const typename std::conditional<FP64, double, float>::type *f, float tau, int &nfp64) {
   using T = typename std::conditional<FP64, double, float>::type;
-  const T sh = sgn ? om : -om;
-  T x[4] = {d[0] + sh, d[1] + sh, d[2] + sh, d[3] + sh};
+  T xx[4] = {x[0], x[1], x[2], x[3]};
   if constexpr (FP64) {
-    return inv_sum(x, f);
+    return inv_sum(xx, f);
   } else {
-    return inv_sum_mixed(x, f, tau, &nfp64);
+    return inv_sum_mixed(xx, f, tau, &nfp64);
   }
 }
 
+// D0 - w for a frequency near the knots: with D0 = D0h + D0l and w = wh + wl split into
+// FP32 parts the difference keeps full relative precision however close D0 is to w
+__device__ __forceinline__ float near_shift(float D0h, float D0l, float wh, float wl) {
+  float sv, tv;
+  two_diff(D0h, wh, sv, tv);
+  return sv + (tv + (D0l - wl));
+}
+__device__ __forceinline__ double near_shift(double D0h, double, double wh, double) { return D0h - wh; }
+
 // evaluates a warp's near-field list: entry = 2 * frequency index + term; every entry of one
 // round has a different frequency index or term, and the two terms of one frequency go to
-// different rounds only through the list order, so each round adds to distinct slots
+// different rounds only through the list order, so each round adds to distinct slots.
+// Knots of the piece: d = D0 + e (sorted), D0 = D0h + D0l; term 0 is 1/(D - |w|) with knots
+// (D0 - |w|) + e, term 1 is 1/(D + |w|) with knots d + |w|.
 template <bool FP64>
 __device__ __forceinline__ void near_pass(const typename std::conditional<FP64, double, float>::type d[4],
+                                          const typename std::conditional<FP64, double, float>::type e[4],
+                                          typename std::conditional<FP64, double, float>::type D0h,
+                                          typename std::conditional<FP64, double, float>::type D0l,
                                           const typename std::conditional<FP64, double, float>::type f[4],
                                           typename std::conditional<FP64, double, float>::type vr,
                                           const typename std::conditional<FP64, double, float>::type *s_w,
+                                          const typename std::conditional<FP64, double, float>::type *s_wl,
                                           const short *list, int n,
                                           typename std::conditional<FP64, double, float>::type *sR,
                                           typename std::conditional<FP64, double, float>::type *cR,
@@ -526,19 +541,29 @@ __device__ __forceinline__ void near_pass(const typename std::conditional<FP64, 
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
     if (k < n) {
-      const int e = list[k];
-      const int iw = e >> 1, sgn = e & 1;
+      const int ent = list[k];
+      const int iw = ent >> 1, sgn = ent & 1;
       const T w = s_w[iw];
-      const T om = w < T(0) ? -w : w;
+      const bool neg = w < T(0);
+      const T om = neg ? -w : w;
+      T x[4];
+      if (sgn) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = d[i] + om;
+      } else {
+        const T sh = near_shift(D0h, D0l, om, FP64 ? T(0) : (neg ? -s_wl[iw] : s_wl[iw]));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = sh + e[i];
+      }
       // a frequency and its two terms may both be in this round: add them one term at a time
-      const T re = near_term<FP64>(d, f, om, sgn, tau, nfp64);
+      const T re = near_term<FP64>(x, f, tau, nfp64);
       for (int t2 = 0; t2 < 2; ++t2) {
         if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
         __syncwarp(__activemask());
       }
-      if (sgn == 0 && om > d[0] && om < d[3]) {  // inside the knot range: the delta term too
-        const T im = delta_sum(d, f, om) * T(3.141592653589793);
-        kadd_t(sI[iw], cI[iw], w < T(0) ? -vr * im : vr * im);
+      if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {  // |w| inside the knot range: the delta term too
+        const T im = delta_sum(x, f, T(0)) * T(3.141592653589793);
+        kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
       }
     }
     __syncwarp();
@@ -552,6 +577,8 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
                                                           const short *__restrict__ occ,
                                                           const short *__restrict__ empq,
                                                           const double *__restrict__ omega, int nw, DynBufs db,
+                                                          const float *__restrict__ Eklo,
+                                                          const float *__restrict__ Ekqlo,
                                                           unsigned long long *__restrict__ counters) {
   using T = typename std::conditional<FP64, double, float>::type;
   constexpr int KM = FarK<T>::value;
@@ -562,11 +589,15 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
   __shared__ T sR[kDynWarps][kNWPass], sI[kDynWarps][kNWPass];
   __shared__ T cR[kDynWarps][kNWPass], cI[kDynWarps][kNWPass];  // compensation terms
   __shared__ T s_w[kNWPass];
+  __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
   __shared__ short s_near[kDynWarps][kNearCap];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = q.hi - q.lo;
   const long long nbatch = (g.ntet + 31) / 32;
-  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) s_w[iw] = (T)omega[iw];
+  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
+    s_w[iw] = (T)omega[iw];
+    if constexpr (!FP64) s_wl[iw] = (float)(omega[iw] - (double)s_w[iw]);
+  }
   __syncthreads();
   int nfp64 = 0, npieces = 0;
   auto kadd = [](T &sum, T &comp, T x) {
@@ -626,20 +657,47 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
       const int mo = div_small(loc, nn, q.hi - q.lo);
       const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
       if (q.gamma && m == n) continue;
-      T a[4], b[4], f[4];
+      // band pair: a = e^m_k - eF, D = D0 + e (e_0 = 0).  Mixed path: energies as FP32
+      // hi + lo pairs, so that D0 (hi + lo) and the corner offsets e come out to full FP32
+      // relative precision whatever the size of a and b
+      T a[4], e[4], f[4];
+      T D0h = T(0), D0l = T(0);
       T amin = T(1e30), bmax = T(-1e30);
+      if constexpr (FP64) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
-        if constexpr (FP64) {
+        for (int i = 0; i < 4; ++i) {
+          const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
           a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
-          b[i] = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
-        } else {
-          a[i] = ((const float *)Ek)[(long long)ck * g.nb + m];
-          b[i] = ((const float *)Ekq)[(long long)cq * g.nb + n];
+          const double b = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
+          e[i] = b - a[i];
+          amin = a[i] < amin ? a[i] : amin;
+          bmax = b > bmax ? b : bmax;
         }
-        amin = a[i] < amin ? a[i] : amin;
-        bmax = b[i] > bmax ? b[i] : bmax;
+      } else {
+        float al[4], bh[4], bl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const long long ik = (long long)s_c[wib][l][i] * g.nb + m, iq = (long long)s_cq[wib][l][i] * g.nb + n;
+          a[i] = ((const float *)Ek)[ik];
+          al[i] = Eklo[ik];
+          bh[i] = ((const float *)Ekq)[iq];
+          bl[i] = Ekqlo[iq];
+          amin = a[i] < amin ? a[i] : amin;
+          bmax = bh[i] > bmax ? bh[i] : bmax;
+        }
+        float sv, tv;
+        two_diff(bh[0], a[0], sv, tv);
+        const float corr = tv + (bl[0] - al[0]);
+        D0h = sv + corr;
+        D0l = corr - (D0h - sv);
+        e[0] = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 4; ++i) {
+          float sa, ta, sb, tb;
+          two_diff(a[i], a[0], sa, ta);
+          two_diff(bh[i], bh[0], sb, tb);
+          e[i] = (sb - sa) + ((tb - ta) + ((bl[i] - bl[0]) - (al[i] - al[0])));
+        }
       }
       if (!(amin < T(0) && bmax > T(0))) continue;
       const T *W2t = (const T *)W2;
@@ -647,16 +705,19 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
       for (int i = 0; i < 4; ++i)
         f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
       const T vol = s_vol[wib][l];
-      carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) {
-        sort4(d, ff);
+      carve2_off<T>(a, e, D0h, f, [&](T r, T ee[4], T ff[4]) {
+        sort4(ee, ff);
         ++npieces;
+        T d[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
         if (!(d[3] > T(0))) return;
         __syncwarp();
         int K = 0;
         if (lane == 0) K = far_moments<T, KM>(d, ff, s_a[wib]);
         K = __shfl_sync(kFull, K, 0);
         __syncwarp();
-        const T c = (d[0] + d[3]) * T(0.5), half = (d[3] - d[0]) * T(0.5);
+        const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
         const T vr = vol * r;
         // far field for both terms (Horner on the moments); near-field frequencies are
         // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
@@ -686,13 +747,15 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
           }
           if (nlist > kNearCap - 64) {  // flush a full list
             __syncwarp();
-            near_pass<FP64>(d, ff, vr, s_w, s_near[wib], nlist, sR[wib], cR[wib], sI[wib], cI[wib], tau, nfp64);
+            near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
+                            cI[wib], tau, nfp64);
             nlist = 0;
             __syncwarp();
           }
         }
         __syncwarp();
-        near_pass<FP64>(d, ff, vr, s_w, s_near[wib], nlist, sR[wib], cR[wib], sI[wib], cI[wib], tau, nfp64);
+        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
+                            cI[wib], tau, nfp64);
         __syncwarp();
       });
     }
@@ -824,10 +887,10 @@ cudaError_t launch_overlap(const Grid &g, const double *, const void *C, int dty
 }
 
 cudaError_t launch_bands(const double *E, long long nc, int nb, double ef, short *occ, short *emp, float *E32,
-                         cudaStream_t s) {
+                         cudaStream_t s, float *E32lo) {
   long long nb_ = (nc + kThreads - 1) / kThreads;
   const int blocks = (int)(nb_ < kSMs * 8 ? nb_ : kSMs * 8);
-  k_bands<<<blocks, kThreads, 0, s>>>(E, nc, nb, ef, occ, emp, E32);
+  k_bands<<<blocks, kThreads, 0, s>>>(E, nc, nb, ef, occ, emp, E32, E32lo);
   return cudaGetLastError();
 }
 
@@ -866,16 +929,18 @@ cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const v
 cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                            const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
                            const double *omega, int nw, const DynBufs &db, int nblocks,
-                           unsigned long long *counters, cudaStream_t s) {
+                           unsigned long long *counters, cudaStream_t s, const float *Eklo,
+                           const float *Ekqlo) {
   if (nw > kNWPass || nw <= 0) return cudaErrorInvalidValue;
+  if (!fp64 && (!Eklo || !Ekqlo)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(db.next, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (fp64)
     k_dynamic<true><<<nblocks, kDynThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db,
-                                                     counters);
+                                                     Eklo, Ekqlo, counters);
   else
     k_dynamic<false><<<nblocks, kDynThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db,
-                                                      counters);
+                                                      Eklo, Ekqlo, counters);
   return cudaGetLastError();
 }
 

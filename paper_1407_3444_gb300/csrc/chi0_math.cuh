@@ -590,4 +590,58 @@ __device__ __forceinline__ void carve2(const T a[4], const T b[4], const T f[4],
   }
 }
 
+
+// Carving with the D attribute as an offset: every vertex carries e = D - D0 for one
+// reference value D0 per band pair (passed as koff = D0 rounded to T), so that knots near a
+// frequency w can be formed as (D0 - w) + e without the rounding of D0 itself (the
+// dynamic kernel's mixed path).  First cut on a, second on b = a + koff + e; the emitted
+// pieces carry offsets e (clamped to D >= 0).
+template <typename T, typename Emit>
+__device__ __forceinline__ void carve2_off(const T a[4], const T e[4], T koff, const T f[4], Emit &&emit) {
+  const T amax = fmax(fmax(a[0], a[1]), fmax(a[2], a[3]));
+  const T bmin = fmin(fmin(a[0] + koff + e[0], a[1] + koff + e[1]), fmin(a[2] + koff + e[2], a[3] + koff + e[3]));
+  if (amax < T(0) && bmin > T(0)) {
+    T ee[4] = {e[0], e[1], e[2], e[3]};
+    T ff[4] = {f[0], f[1], f[2], f[3]};
+    emit(T(1), ee, ff);
+    return;
+  }
+  Vt<T> V[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) V[i] = Vt<T>{a[i], e[i], f[i]};
+#pragma unroll 1
+  for (int i1 = 0; i1 < 3; ++i1) {
+    Vt<T> P[4];
+    T r1 = T(0);
+    const int n1 = cut_piece<0>(V, i1, P, r1);
+    if (i1 >= n1) break;
+    if (r1 <= T(0)) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) P[i].a += koff;  // second-cut key -(a + e) is now -b
+#pragma unroll 1
+    for (int i2 = 0; i2 < 3; ++i2) {
+      Vt<T> Qv[4];
+      T r2 = T(0);
+      const int n2 = cut_piece<1>(P, i2, Qv, r2);
+      if (i2 >= n2) break;
+      const T r = r1 * r2;
+      if (r <= T(0)) continue;
+      T ee[4], ff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ee[i] = Qv[i].D > -koff ? Qv[i].D : -koff;
+        ff[i] = Qv[i].f;
+      }
+      emit(r, ee, ff);
+    }
+  }
+}
+
+// x - y = s + t exactly (Knuth's two-difference; any order of magnitudes)
+__device__ __forceinline__ void two_diff(float x, float y, float &s, float &t) {
+  s = x - y;
+  const float bb = s - x;
+  t = (x - (s - bb)) - (y + bb);
+}
+
 }  // namespace chi0dev
