@@ -35,6 +35,8 @@ CHI0_SIGN_POSITIVE = 0
 CHI0_SIGN_PAPER = 1
 CHI0_K_OVERLAP, CHI0_K_STATIC, CHI0_K_DYNAMIC, CHI0_K_REDUCE, CHI0_K_DOS, CHI0_K_BANDS = 0, 1, 2, 3, 4, 5
 CHI0_K_COUNT = 8
+# frequencies per k_dynamic launch: chi0_dynamic splits longer grids into passes of this size
+DYNAMIC_MAX_NW = 256
 
 
 class chi0_kgrid_t(ct.Structure):
