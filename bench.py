@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--overlap", default="fp32", choices=["fp32", "bf16x3", "bf16x6", "tf32"],
+                    help="matrix elements of the mixed form: FP32 on the CUDA cores (default) or the "
+                         "tensor cores (BF16 split in two pieces / three pieces, or one TF32 product)")
     ap.add_argument("--workload", default="cr", choices=["cr", "free", "fese", "sweep", "large"],
                     help="cr: Cr-like 9-orbital static (default); free: free-electron Lindhard; fese: "
                          "FeSe-like dynamic; sweep: 40-band window sweep (static); large: 80-band 72^3 dynamic")
@@ -113,6 +116,8 @@ def workload_config(W, args):
         "ntet": W.ntet, "nbands": W.nb, "nq": len(W.qs), "nomega": nw,
         "nominal_evals_per_step": W.nominal_evals(),
         "evec_dtype": str(W.C.dtype) if W.C is not None else None,
+        "overlap": {"fp32": "FP32 on the CUDA cores", "bf16x3": "tensor cores, BF16 2 pieces, 3 products",
+                    "bf16x6": "tensor cores, BF16 3 pieces, 6 products", "tf32": "tensor cores, TF32"}[args.overlap],
         "l2": "inputs larger than L2 (%.1f GB of eigen-data read per step)" % (inb / 1e9),
     }
 
@@ -294,7 +299,7 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream()
     dev = chi0.DeviceInputs(W)
-    Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev)
+    Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev, overlap=args.overlap)
     Pd = chi0.Plan(W, precision="fp64", device=True, profile=False, staged=dev) if args.fp64_steps > 0 else None
     nominal = W.nominal_evals()
     for _ in range(args.warmup):

@@ -58,8 +58,16 @@ extern "C" {
                              FP64 accumulation                                            */
 
 #define CHI0_OVL_FP32 0   /* mixed precision: overlaps with FP32 FMA on the CUDA cores     */
-#define CHI0_OVL_BF16X3 1 /* mixed precision: overlaps on the tensor cores, 3-piece BF16
-                             split of each operand, FP32 accumulate (nbands >= 16)        */
+#define CHI0_OVL_BF16X3 1 /* mixed precision: overlaps on the tensor cores (tcgen05), each
+                             operand split x = hi + lo into two BF16 pieces, products
+                             hi*hi + hi*lo + lo*hi, FP32 accumulate (band window <= 128)  */
+#define CHI0_OVL_TF32 2   /* mixed precision: overlaps on the tensor cores, one product of
+                             round-to-nearest TF32 operands, FP32 accumulate (window
+                             <= 128)                                                      */
+#define CHI0_OVL_BF16X6 3 /* mixed precision: overlaps on the tensor cores, three-piece BF16
+                             split x = p0 + p1 + p2, the six products pa*pb with a + b <= 2,
+                             FP32 accumulate (band window <= 128; the tile must fit in
+                             227 KB of shared memory: 3 (128 + 2w) (4 norb) bytes)        */
 
 #define CHI0_SIGN_POSITIVE 0 /* return -(Eq. 1) and -(Eq. 2): static chi0 > 0, Im >= 0 (w>0) */
 #define CHI0_SIGN_PAPER 1    /* return Eq. 1 and Eq. 2 exactly as printed                    */
@@ -137,7 +145,11 @@ typedef struct {
  *   outputs_on_device  1: chi/re/im are device pointers; 0: host pointers.
  *   stream        cudaStream_t (NULL = legacy default stream) for every copy and launch.
  *   profile       1: time each kernel with CUDA events on the stream (chi0_plan_stats).
- *   wait_budget   reserved for bounded device waits (cycles; 0 = library default). */
+ *   wait_budget   clock cycles one bounded device-side wait may take before the call
+ *                 fails with CHI0_ETIMEOUT (0 = 2^31, about one second).
+ *   test_stall    error-path test hook: 1 makes the tensor-core overlap kernel issue no
+ *                 MMA, so that its bounded wait runs out and the call returns
+ *                 CHI0_ETIMEOUT; 0 in normal use. */
 typedef struct {
   int precision;
   int overlap;
@@ -149,7 +161,8 @@ typedef struct {
   void *stream;
   int profile;
   long long wait_budget;
-  int reserved[8];
+  int test_stall;
+  int reserved[7];
 } chi0_opts_t;
 
 typedef struct chi0_plan chi0_plan_t;
@@ -190,7 +203,8 @@ int chi0_plan(const chi0_kgrid_t *kgrid, const chi0_tetra_t *tetra, chi0_band_wi
 
 /* Static chi0(q, w = 0) (Eq. 1 at w = 0, Sec. III) for nq q points: chi[iq].
  * Errors: CHI0_EINVAL (nq <= 0, NULL pointers, shift on a non-periodic grid, window
- * outside the plan's), CHI0_ECUDA, CHI0_ETIMEOUT. */
+ * outside the plan's), CHI0_ECUDA, CHI0_ETIMEOUT (a tensor-core overlap wait ran out of
+ * opts.wait_budget; the results of the call are then undefined, the plan stays usable). */
 int chi0_static(chi0_plan_t *plan, const chi0_q_t *q, int nq, double *chi);
 
 /* Dynamic chi0(q, w) (Eqs. 1-3) on nw frequencies: re[iq*nw + iw], im[iq*nw + iw].

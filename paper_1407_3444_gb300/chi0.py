@@ -31,6 +31,9 @@ CHI0_PREC_FP64 = 0
 CHI0_PREC_MIXED = 1
 CHI0_OVL_FP32 = 0
 CHI0_OVL_BF16X3 = 1
+CHI0_OVL_TF32 = 2
+CHI0_OVL_BF16X6 = 3
+OVERLAP_MODES = {"fp32": CHI0_OVL_FP32, "bf16x3": CHI0_OVL_BF16X3, "tf32": CHI0_OVL_TF32, "bf16x6": CHI0_OVL_BF16X6}
 CHI0_SIGN_POSITIVE = 0
 CHI0_SIGN_PAPER = 1
 CHI0_K_OVERLAP, CHI0_K_STATIC, CHI0_K_DYNAMIC, CHI0_K_REDUCE, CHI0_K_DOS, CHI0_K_BANDS = 0, 1, 2, 3, 4, 5
@@ -62,7 +65,7 @@ class chi0_opts_t(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("overlap", ct.c_int), ("cma", ct.c_int), ("sign", ct.c_int),
                 ("tau", ct.c_double), ("inputs_on_device", ct.c_int), ("outputs_on_device", ct.c_int),
                 ("stream", ct.c_void_p), ("profile", ct.c_int), ("wait_budget", ct.c_longlong),
-                ("reserved", ct.c_int * 8)]
+                ("test_stall", ct.c_int), ("reserved", ct.c_int * 7)]
 
 
 class chi0_stats_t(ct.Structure):
@@ -253,7 +256,8 @@ class Plan:
 
     def __init__(self, W, precision: str = "fp64", device: bool = True, stream=None, profile: bool = False,
                  tau: float = 9.5367431640625e-07, sign: int = CHI0_SIGN_POSITIVE, tetra=None, window=None, cma=None,
-                 qs: Optional[Sequence] = None, staged: Optional[Staged] = None):
+                 qs: Optional[Sequence] = None, staged: Optional[Staged] = None, overlap: str = "fp32",
+                 wait_budget: int = 0, test_stall: bool = False):
         self.W = W
         self.device = device
         self.keep = []
@@ -266,6 +270,9 @@ class Plan:
         o.cma = 1 if self.cma else 0
         o.sign = sign
         o.tau = tau
+        o.overlap = OVERLAP_MODES[overlap]
+        o.wait_budget = int(wait_budget)
+        o.test_stall = 1 if test_stall else 0
         o.profile = 1 if profile else 0
         o.inputs_on_device = 1 if device else 0
         o.outputs_on_device = 1 if device else 0

@@ -39,6 +39,7 @@ struct chi0_plan {
   float *E32_d = nullptr, *Eq32_d = nullptr;  // energies - eF in FP32 (mixed precision): hi, then lo
   void *C32_d = nullptr;                      // complex64 copy of complex128 eigenvectors (mixed)
   int *next_d = nullptr;                      // [2] batch counter, FP64 list size
+  int *err_d = nullptr;                       // error word of the bounded device waits
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
   int static_grid = 0, dynamic_grid = 0;
@@ -71,6 +72,11 @@ static int fail(chi0_plan_t *p, int code, const char *fmt, ...) {
   } while (0)
 
 static size_t cplx_size(int dtype) { return dtype == CHI0_C64 ? 8 : 16; }
+
+// tensor-core precision form of a CHI0_OVL_* mode (not CHI0_OVL_FP32)
+static int tc_mode(int overlap) {
+  return overlap == CHI0_OVL_TF32 ? TC_TF32 : (overlap == CHI0_OVL_BF16X3 ? TC_BF16X3 : TC_BF16X6);
+}
 
 extern "C" void chi0_opts_default(chi0_opts_t *o) {
   if (!o) return;
@@ -120,6 +126,7 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->C32_d);
   cudaFree(p->Eq32_d);
   cudaFree(p->next_d);
+  cudaFree(p->err_d);
   cudaFree(p->tq_d);
   cudaFree(p->tq_n_d);
 }
@@ -140,10 +147,13 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
   const chi0_opts_t &op = p->opts;
   if (op.precision != CHI0_PREC_FP64 && op.precision != CHI0_PREC_MIXED)
     return fail(p, CHI0_EINVAL, "precision %d unknown", op.precision);
-  if (op.overlap != CHI0_OVL_FP32 && op.overlap != CHI0_OVL_BF16X3)
+  if (op.overlap != CHI0_OVL_FP32 && op.overlap != CHI0_OVL_BF16X3 && op.overlap != CHI0_OVL_TF32 &&
+      op.overlap != CHI0_OVL_BF16X6)
     return fail(p, CHI0_EINVAL, "overlap mode %d unknown", op.overlap);
-  if (op.overlap == CHI0_OVL_BF16X3)
-    return fail(p, CHI0_ENOTSUP, "tensor-core overlap mode not available in this build");
+  if (op.overlap != CHI0_OVL_FP32 && op.precision != CHI0_PREC_MIXED)
+    return fail(p, CHI0_ENOTSUP, "tensor-core overlaps belong to the mixed-precision form");
+  if (op.test_stall && op.overlap == CHI0_OVL_FP32)
+    return fail(p, CHI0_EINVAL, "test_stall needs a tensor-core overlap mode");
   if (!(op.tau >= 0.0 && op.tau < 1.0)) return fail(p, CHI0_EINVAL, "tau must lie in [0, 1)");
   for (int d = 0; d < 3; ++d)
     if (kg->n[d] < 1 || kg->n[d] > (1 << 12)) return fail(p, CHI0_EINVAL, "n[%d] = %d out of range", d, kg->n[d]);
@@ -213,6 +223,12 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
   }
   // scratch: |M|^2 at the plan's window, block partials, counters
   const int w = win.hi - win.lo;
+  if (op.overlap != CHI0_OVL_FP32 && !op.cma &&
+      overlap_tc_smem(w, g.norb, tc_mode(op.overlap)) > kTcSmemMax)
+    return fail(p, CHI0_ENOTSUP, "tensor-core overlaps: a band window of %d with %d orbitals exceeds one tile", w,
+                g.norb);
+  CK(p, cudaMalloc(&p->err_d, sizeof(int)));
+  CK(p, cudaMemsetAsync(p->err_d, 0, sizeof(int), p->stream));
   if (!op.cma) {
     const size_t es = op.precision == CHI0_PREC_FP64 ? sizeof(double) : sizeof(float);
     CK(p, cudaMalloc(&p->W2_d, es * (size_t)g.nc * w * w));
@@ -403,13 +419,19 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     }
   }
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, s));
+  const bool tc = op.overlap != CHI0_OVL_FP32 && !op.cma && !fp64;
   for (int iq = 0; iq < nq; ++iq) {
     Q q;
     int rc = prepare_q(p, qs[iq], q);
     if (rc) return rc;
     if (!op.cma) {
       tm.start(CHI0_K_OVERLAP);
-      CK(p, launch_overlap(p->g, p->E_d, p->C_d, p->dtype, q, p->W2_d, fp64, s, p->C32_d));
+      if (tc)
+        CK(p, launch_overlap_tc(p->g, p->C32_d ? p->C32_d : p->C_d, p->dtype, q, (float *)p->W2_d,
+                                tc_mode(op.overlap), op.wait_budget, op.test_stall,
+                                p->err_d, s));
+      else
+        CK(p, launch_overlap(p->g, p->E_d, p->C_d, p->dtype, q, p->W2_d, fp64, s, p->C32_d));
       p->stats.kernels += 1;
       tm.stop();
     }
@@ -464,6 +486,16 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
         p->stats.kernels += 2;
         tm.stop();
       }
+    }
+  }
+  if (tc) {  // the tensor-core overlap's bounded waits report through the error word
+    int herr = 0;
+    CK(p, cudaMemcpyAsync(&herr, p->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(p, cudaStreamSynchronize(s));
+    if (herr) {
+      CK(p, cudaMemsetAsync(p->err_d, 0, sizeof(int), s));
+      CK(p, cudaStreamSynchronize(s));
+      return fail(p, CHI0_ETIMEOUT, "tensor-core overlap: a bounded wait ran out of its budget");
     }
   }
   if (!op.outputs_on_device) {

@@ -117,4 +117,37 @@ cudaError_t launch_reduce(const double *partial, int nblocks, int nw, double sca
 int static_blocks();
 int dynamic_max_nw();
 
+// |M_mn|^2 on the tensor cores (mixed precision): k side from the plan's complex64 copy C32,
+// k+q side from q.Cq (complex64 or complex128, explicit) or C32 at the shifted corner.
+// W2[c][m-lo][n-lo] FP32.  budget: clock cycles a bounded wait may take (<= 0: 2^31);
+// test_stall: issue no MMA, so that the first wait runs out (error-path test).  A wait that
+// runs out sets *err to 1.
+enum { TC_TF32 = 0, TC_BF16X3 = 1, TC_BF16X6 = 2 };
+constexpr size_t kTcSmemMax = 227 * 1024;
+size_t overlap_tc_smem(int w, int norb, int mode);  // bytes of shared memory ((size_t)-1: w > 128)
+cudaError_t launch_overlap_tc(const Grid &g, const void *C32, int dtype, const Q &q, float *W2, int mode,
+                              long long budget, int test_stall, int *err, cudaStream_t s);
+
+#ifdef __CUDACC__
+// corner index with periodic wrap (32-bit: the plan checks that the mesh has fewer than 2^31
+// corners), and the corner at integer offset s from corner c
+__device__ __forceinline__ int wrap_idx(int i, int N) { return i >= N ? i - N : i; }
+__device__ __forceinline__ long long cid(const Grid &g, int i0, int i1, int i2) {
+  if (g.periodic) {
+    i0 = wrap_idx(i0, g.N[0]);
+    i1 = wrap_idx(i1, g.N[1]);
+    i2 = wrap_idx(i2, g.N[2]);
+  }
+  return (long long)(unsigned)((i0 * g.N[1] + i1) * g.N[2] + i2);
+}
+__device__ __forceinline__ long long shift_corner(const Grid &g, long long c, const int s[3]) {
+  const unsigned cu = (unsigned)c;
+  const unsigned r = fdiv(cu, g.fN2);
+  const int i2 = (int)(cu - r * (unsigned)g.N[2]);
+  const unsigned i0 = fdiv(r, g.fN1);
+  const int i1 = (int)(r - i0 * (unsigned)g.N[1]);
+  return cid(g, (int)i0 + s[0], i1 + s[1], i2 + s[2]);
+}
+#endif
+
 }  // namespace chi0int

@@ -30,27 +30,6 @@ constexpr int kSMs = 152;
 constexpr int kStaticBlocks = kSMs * 8;
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ int wrap(int i, int N) { return i >= N ? i - N : i; }
-
-// corner index (32-bit: the plan checks that the mesh has fewer than 2^31 corners)
-__device__ __forceinline__ long long cid(const Grid &g, int i0, int i1, int i2) {
-  if (g.periodic) {
-    i0 = wrap(i0, g.N[0]);
-    i1 = wrap(i1, g.N[1]);
-    i2 = wrap(i2, g.N[2]);
-  }
-  return (long long)(unsigned)((i0 * g.N[1] + i1) * g.N[2] + i2);
-}
-
-__device__ __forceinline__ long long shift_corner(const Grid &g, long long c, const int s[3]) {
-  const unsigned cu = (unsigned)c;
-  const unsigned r = fdiv(cu, g.fN2);
-  const int i2 = (int)(cu - r * (unsigned)g.N[2]);
-  const unsigned i0 = fdiv(r, g.fN1);
-  const int i1 = (int)(r - i0 * (unsigned)g.N[1]);
-  return cid(g, (int)i0 + s[0], i1 + s[1], i2 + s[2]);
-}
-
 // x / d for 0 <= x < qmax * d (small quotients): binary search, no division sequence
 __device__ __forceinline__ int div_small(int x, int d, int qmax) {
   int lo = 0, hi = qmax;

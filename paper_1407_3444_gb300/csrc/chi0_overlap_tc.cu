@@ -1,0 +1,375 @@
+// chi0_overlap_tc.cu -- |M_mn(k,q)|^2 (the Eq. 1 matrix elements in the tight-binding form
+// of the Sec. III footnote) on the 5th-generation tensor cores: tcgen05.mma with shared-memory
+// operands and an FP32 accumulator in tensor memory.
+//
+// Per k corner c the overlap O = A^H B, A = C[c][:, lo:hi] (norb x w, complex), B the same
+// block at k+q, is one real GEMM with K = 2 norb:
+//   row m of the A operand:        [Re A[:, m], Im A[:, m]]
+//   row n of the B operand (Re):   [Re B[:, n], Im B[:, n]]       -> Re O[m][n]
+//   row NW + n (Im):               [Im B[:, n], -Re B[:, n]]      -> Im O[m][n]
+// so that one accumulator row (one tensor-memory lane) holds both Re O[m][:] and Im O[m][:]
+// and the epilogue forms |O|^2 without exchanging data between lanes.  Several corners share
+// one MMA round: corner g's A rows sit at g*w .. g*w + w - 1 of the M = 128 tile and its B
+// rows at g*2NW .. of the N <= 256 tile; the off-diagonal corner blocks of the product are
+// computed and never read.
+//
+// Accumulation.  The tensor core adds each MMA's products to its FP32 accumulator with
+// truncation, so every MMA accumulated into one place moves the result toward zero by a
+// fraction of an ulp: measured on chi0, 6e-8 relative per MMA (3.2e-7 with 6 MMAs per
+// element, 1.8e-6 with 30), a bias that the sum over k does not average away.  The K steps
+// are therefore spread round-robin over NACC accumulators (tensor-memory column blocks of
+// N), each accumulator takes its smallest products first and the leading piece product last,
+// and the epilogue adds the NACC partial results on the CUDA cores (round to nearest).  With
+// NACC equal to the number of K steps each accumulator sees one leading-order MMA.
+//
+// Precision forms (FP32 accumulation in all):
+//   TF32    one product of round-to-nearest TF32 operands
+//   BF16X3  x = p0 + p1 with p0 = bf16(x), p1 = bf16(x - p0); products p0 p0 + p0 p1 + p1 p0
+//   BF16X6  x = p0 + p1 + p2 (p2 = bf16(x - p0 - p1)); the six products pa pb with a + b <= 2
+//
+// Operands are staged by the CTA's threads (conversion to TF32/BF16 and the real form above)
+// into the K-major, non-swizzled tcgen05 layout: core matrices of 8 rows x 16 bytes stored as
+// 128 contiguous bytes, core matrix (row group rb, 16-byte column kb) at (rb * KB + kb) * 128
+// bytes (KB = 16-byte columns per row), so the descriptor strides are 128 bytes along K and
+// KB * 128 bytes along M/N.  One thread issues the MMAs and commits them to an mbarrier; every
+// wait on it is bounded (the plan's wait budget, in clock cycles) and a wait that runs out
+// sets the error word, frees the tensor memory and ends the kernel.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "chi0_internal.h"
+
+namespace chi0int {
+namespace {
+
+constexpr int kTcThreads = 256;  // 8 warps: warp i reads tensor-memory lanes 32(i%4) .. +31
+constexpr int kTcM = 128;        // MMA rows (cta_group::1)
+constexpr int kTcMaxN = 256;     // MMA columns
+constexpr int kTcCols = 512;           // tensor-memory columns of an SM
+constexpr int kTcMinSmem = 80 * 1024;  // at most 2 CTAs per SM when a CTA takes <= 256 columns
+constexpr int kTcOneSmem = 116 * 1024; // one CTA per SM when it takes all 512 columns
+
+struct TcShape {
+  int w, NW, G, N, Kpad, Kbytes, ES, P, nks, NACC, ncols;
+  size_t smem;
+};
+
+__host__ __device__ inline TcShape tc_shape(int w, int norb, int mode) {
+  TcShape s{};
+  s.w = w;
+  s.NW = (w + 7) & ~7;
+  s.ES = mode == TC_TF32 ? 4 : 2;
+  s.P = mode == TC_TF32 ? 1 : (mode == TC_BF16X3 ? 2 : 3);
+  const int kstep = 32 / s.ES;  // K elements per MMA instruction (32 bytes of K)
+  s.Kpad = (2 * norb + kstep - 1) / kstep * kstep;
+  s.Kbytes = s.Kpad * s.ES;
+  s.nks = s.Kbytes / 32;
+  const int g1 = kTcM / (w > 0 ? w : 1), g2 = kTcMaxN / (2 * s.NW);
+  s.G = g1 < g2 ? g1 : g2;
+  if (s.G < 1) s.G = 0;  // window too wide for one tile
+  if (mode != TC_TF32 && s.G > 1) {
+    // fewer corners per round when that lets every K step have its own accumulator
+    const int g3 = kTcCols / (2 * s.NW * s.nks);
+    s.G = g3 < 1 ? 1 : (g3 < s.G ? g3 : s.G);
+  }
+  s.N = s.G * 2 * s.NW;
+  s.NACC = mode == TC_TF32 ? 1 : (s.N > 0 ? kTcCols / s.N : 1);
+  if (s.NACC > s.nks) s.NACC = s.nks;
+  if (s.NACC < 1) s.NACC = 1;
+  int nc = 32;
+  while (nc < s.NACC * s.N) nc <<= 1;
+  s.ncols = nc;
+  s.smem = (size_t)s.P * (kTcM + s.N) * s.Kbytes + 64;
+  return s;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+// instruction descriptor: FP32 accumulator, TF32 or BF16 operands, both K-major, M = 128
+__device__ __forceinline__ uint32_t idesc(int mode, int N) {
+  const uint32_t ab = mode == TC_TF32 ? 2u : 1u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc, int mode) {
+  if (mode == TC_TF32)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+// 8 consecutive FP32 columns of this thread's tensor-memory lane (load and wait in one block)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// byte offset of element (row r, column k) in a K-major core-matrix tile
+__device__ __forceinline__ uint32_t tile_off(int r, int k, int ES, int KB) {
+  const int kb = k * ES;
+  return (uint32_t)(((r >> 3) * KB + (kb >> 4)) * 128 + (r & 7) * 16 + (kb & 15));
+}
+
+// store x at (r, k) of every piece of a tile (pieces are `stride` bytes apart)
+template <int MODE>
+__device__ __forceinline__ void put(unsigned char *base, size_t stride, int r, int k, int KB, float x) {
+  if constexpr (MODE == TC_TF32) {
+    *(uint32_t *)(base + tile_off(r, k, 4, KB)) = tf32_rn(x);
+  } else {
+    const uint32_t off = tile_off(r, k, 2, KB);
+    constexpr int P = MODE == TC_BF16X3 ? 2 : 3;
+    float rem = x;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(rem);
+      *(unsigned short *)(base + p * stride + off) = __bfloat16_as_ushort(h);
+      rem -= __bfloat162float(h);
+    }
+  }
+}
+
+// Bounded wait on an mbarrier phase; false when the budget (clock cycles) ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > budget) return false;
+  }
+}
+
+template <int MODE, typename CTq>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_overlap_tc(Grid g, const float2 *__restrict__ C, const CTq *__restrict__ Cb, int explicit_q, Q q,
+                 float *__restrict__ W2, long long budget, int test_stall, int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const TcShape sh = tc_shape(q.hi - q.lo, g.norb, MODE);
+  const int w = sh.w, NW = sh.NW, G = sh.G, KB = sh.Kbytes / 16, no = g.norb;
+  const size_t a_piece = (size_t)kTcM * sh.Kbytes, b_piece = (size_t)sh.N * sh.Kbytes;
+  unsigned char *sA = smem;
+  unsigned char *sB = smem + sh.P * a_piece;
+  unsigned char *tail = sB + sh.P * b_piece;
+  uint64_t *bar = (uint64_t *)tail;
+  uint32_t *tslot = (uint32_t *)(tail + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // operand memory starts at zero: padding rows and K columns are never written again
+  const size_t nz = (sh.P * (a_piece + b_piece)) / 16;
+  for (size_t i = tid; i < nz; i += blockDim.x) ((uint4 *)smem)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(sh.ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t id = idesc(MODE, sh.N);
+  const long long nround = (g.nc + G - 1) / G;
+  uint32_t parity = 0;
+  bool ok = true;
+  for (long long rd = blockIdx.x; rd < nround && ok; rd += gridDim.x) {
+    const long long c0 = rd * G;
+    // stage the round's corners: element (g, o, band) -> A row g*w + m, B rows g*2NW + n, + NW.
+    // kUnroll elements per thread and pass: all their loads are issued before the first store
+    const int per = no * w, tot = G * per;
+    constexpr int kUnroll = 4;
+    for (int i0 = tid; i0 < tot; i0 += kUnroll * kTcThreads) {
+      float2 xv[kUnroll];
+      CTq yv[kUnroll];
+      int ra[kUnroll], rb[kUnroll], oo[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * kTcThreads;
+        const int gg = i / per, rem = i - gg * per;
+        const long long c = c0 + gg;
+        ra[u] = -1;
+        if (i >= tot || c >= g.nc) continue;
+        const int o = rem / w, mm = rem - o * w;
+        const long long ck = explicit_q ? c : shift_corner(g, c, q.shift);
+        xv[u] = C[(c * no + o) * g.nb + q.lo + mm];
+        yv[u] = Cb[(ck * no + o) * g.nb + q.lo + mm];
+        ra[u] = gg * w + mm;
+        rb[u] = gg * 2 * NW + mm;
+        oo[u] = o;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (ra[u] < 0) continue;
+        const float yr = (float)yv[u].x, yi = (float)yv[u].y;
+        const int o = oo[u];
+        put<MODE>(sA, a_piece, ra[u], o, KB, xv[u].x);
+        put<MODE>(sA, a_piece, ra[u], no + o, KB, xv[u].y);
+        put<MODE>(sB, b_piece, rb[u], o, KB, yr);
+        put<MODE>(sB, b_piece, rb[u], no + o, KB, yi);
+        put<MODE>(sB, b_piece, rb[u] + NW, o, KB, yi);
+        put<MODE>(sB, b_piece, rb[u] + NW, no + o, KB, -yr);
+      }
+    }
+    // generic-proxy stores must be visible to the tensor core's (async-proxy) reads
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && !test_stall) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int ia = 0; ia < sh.NACC; ++ia) {
+        uint32_t acc = 0;
+        // products of pieces a, b with a + b = lvl < P, smallest level first
+        for (int lvl = sh.P - 1; lvl >= 0; --lvl)
+          for (int pa = 0; pa <= lvl; ++pa)
+            for (int s = ia; s < sh.nks; s += sh.NACC) {
+              const uint64_t da = sdesc(smem_u32(sA + pa * a_piece) + s * 256, 128, KB * 128);
+              const uint64_t db = sdesc(smem_u32(sB + (lvl - pa) * b_piece) + s * 256, 128, KB * 128);
+              mma(tmem + (uint32_t)(ia * sh.N), da, db, id, acc, MODE);
+              acc = 1;
+            }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(bar))
+                   : "memory");
+    }
+    // test_stall: nothing arrives, so the bounded wait below runs out (error path test).  The
+    // CTA agrees on the outcome before any warp-wide tensor-memory load.
+    const int got = mbar_wait(smem_u32(bar), parity, budget) ? 1 : 0;
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 1);
+      break;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: lane r = gg*w + m of the tile holds Re O (columns gg*2NW + n) and Im O (+ NW);
+    // warps i and i + 4 share lane quarter i%4 and split the 8-column chunks between them
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;
+    const int gg = r / (w > 0 ? w : 1), m = r - gg * w;
+    const long long c = c0 + gg;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    for (int blk = 0; blk < G; ++blk) {  // warp-uniform loops: every lane takes part in tcgen05.ld
+      for (int n0 = half * 8; n0 < NW; n0 += 16) {
+        float re[8], im[8];
+        tmem_ld8(trow + blk * 2 * NW + n0, re);
+        tmem_ld8(trow + blk * 2 * NW + NW + n0, im);
+        for (int ia = 1; ia < sh.NACC; ++ia) {  // partial accumulators, added in FP32
+          float r2[8], i2[8];
+          tmem_ld8(trow + ia * sh.N + blk * 2 * NW + n0, r2);
+          tmem_ld8(trow + ia * sh.N + blk * 2 * NW + NW + n0, i2);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            re[j] += r2[j];
+            im[j] += i2[j];
+          }
+        }
+        if (blk == gg && gg < G && c < g.nc) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (n0 + j < w) W2[(c * w + m) * w + n0 + j] = re[j] * re[j] + im[j] * im[j];
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok) {
+    // the MMAs this CTA issued (if any) may still be running: wait for them once more,
+    // bounded, before the tensor memory is released
+    mbar_wait(smem_u32(bar), parity, budget);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.ncols) : "memory");
+}
+
+template <int MODE, typename CTq>
+cudaError_t launch_tc(const Grid &g, const float2 *Ck, const CTq *Cb, int explicit_q, const Q &q, float *W2,
+                      long long budget, int test_stall, int *err, cudaStream_t s) {
+  const TcShape sh = tc_shape(q.hi - q.lo, g.norb, MODE);
+  const size_t floor_smem = sh.ncols > 256 ? (size_t)kTcOneSmem : (size_t)kTcMinSmem;
+  const size_t smem = sh.smem < floor_smem ? floor_smem : sh.smem;
+  cudaError_t e = cudaFuncSetAttribute(k_overlap_tc<MODE, CTq>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long nround = (g.nc + sh.G - 1) / sh.G;
+  const int per_sm = smem > (size_t)113 * 1024 ? 1 : 2;
+  long long blocks = (long long)sms * per_sm;
+  if (blocks > nround) blocks = nround;
+  k_overlap_tc<MODE, CTq><<<(int)blocks, kTcThreads, smem, s>>>(g, Ck, Cb, explicit_q, q, W2, budget, test_stall,
+                                                                err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t overlap_tc_smem(int w, int norb, int mode) {
+  const TcShape sh = tc_shape(w, norb, mode);
+  if (sh.G < 1) return (size_t)-1;
+  return sh.smem;
+}
+
+cudaError_t launch_overlap_tc(const Grid &g, const void *C32, int dtype, const Q &q, float *W2, int mode,
+                              long long budget, int test_stall, int *err, cudaStream_t s) {
+  const int w = q.hi - q.lo;
+  if (w < 1 || overlap_tc_smem(w, g.norb, mode) > kTcSmemMax || !err) return cudaErrorInvalidValue;
+  const float2 *Ck = (const float2 *)C32;
+  if (budget <= 0) budget = 1LL << 31;
+  if (mode == TC_BF16X6) {
+    if (q.Cq && dtype == DT_C128)
+      return launch_tc<TC_BF16X6, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
+    if (q.Cq)
+      return launch_tc<TC_BF16X6, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
+    return launch_tc<TC_BF16X6, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, err, s);
+  }
+  if (mode == TC_TF32) {
+    if (q.Cq && dtype == DT_C128)
+      return launch_tc<TC_TF32, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
+    if (q.Cq) return launch_tc<TC_TF32, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
+    return launch_tc<TC_TF32, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, err, s);
+  }
+  if (q.Cq && dtype == DT_C128)
+    return launch_tc<TC_BF16X3, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
+  if (q.Cq) return launch_tc<TC_BF16X3, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
+  return launch_tc<TC_BF16X3, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, err, s);
+}
+
+}  // namespace chi0int

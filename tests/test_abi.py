@@ -105,6 +105,20 @@ def test_plan_validation_before_any_launch(lib):
     with pytest.raises(lib.Chi0Error):
         lib.chi0_plan(_kgrid(lib, E, 3), None, lib.chi0_band_window_t(0, 3), o3)
     assert lib.chi0_last_error(None) != ""
+    # tensor-core overlaps are a mixed-precision form; the stall hook needs one of them
+    o4 = lib.chi0_opts_default()
+    o4.cma = 1
+    o4.overlap = lib.CHI0_OVL_BF16X3
+    with pytest.raises(lib.Chi0Error) as ei:
+        lib.chi0_plan(_kgrid(lib, E, 3), None, lib.chi0_band_window_t(0, 3), o4)
+    assert ei.value.code == lib.CHI0_ENOTSUP
+    o5 = lib.chi0_opts_default()
+    o5.cma = 1
+    o5.precision = lib.CHI0_PREC_MIXED
+    o5.test_stall = 1
+    with pytest.raises(lib.Chi0Error) as ei:
+        lib.chi0_plan(_kgrid(lib, E, 3), None, lib.chi0_band_window_t(0, 3), o5)
+    assert ei.value.code == lib.CHI0_EINVAL
 
 
 def test_destroy_null_is_safe(lib):
