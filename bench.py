@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--workload", default="cr", choices=["cr", "free", "fese", "sweep", "large"],
                     help="cr: Cr-like 9-orbital static (default); free: free-electron Lindhard; fese: "
                          "FeSe-like dynamic; sweep: 40-band window sweep (static); large: 80-band 72^3 dynamic")
+    ap.add_argument("--nw", type=int, default=0,
+                    help="dynamic workloads: use the first NW frequencies of the workload's grid "
+                         "(a bounded sample of the 80-band 72^3 run)")
     ap.add_argument("--nq", type=int, default=None, help="q points per step (default: the workload's)")
     ap.add_argument("--n", type=int, default=None, help="k mesh cubes per axis (cubic workloads)")
     ap.add_argument("--cpu-sample-w", type=int, default=16, help="frequencies in the CPU sample (dynamic)")
@@ -98,6 +101,8 @@ def make_workload(args, nproc):
         W.omega = None  # the static sweep (the dynamic one: chi0_dynamic on the same plan)
         return W
     W = wl.large_mixed(n=args.n or 72, nq=args.nq or 128, nproc=nproc)
+    if args.nw:
+        W.omega = W.omega[:args.nw]
     return W
 
 
@@ -211,10 +216,11 @@ def fp32_peak_tflops(sm_mhz):
 # per final tetrahedron.
 FLOPS_PER_PIECE_MIXED = 205.5
 TRAFFIC_PER_PIECE_MIXED = 3.74
-# The same for k_dynamic per (final tetrahedron, frequency) on the FeSe-like workload
-# (None until counted).
-FLOPS_PER_PIECE_W_DYN = None
-TRAFFIC_PER_PIECE_W_DYN = None
+# The same for k_dynamic per (final tetrahedron, frequency) on the FeSe-like model (ncu
+# counters of the four k_dynamic launches of one step on its 32x32x8 mesh, 2 q x 512 w:
+# 1.40 M final tetrahedra x 256 w per launch).
+FLOPS_PER_PIECE_W_DYN = 169.3
+TRAFFIC_PER_PIECE_W_DYN = 0.0139
 
 
 def run_step(P, W):

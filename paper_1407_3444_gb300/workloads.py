@@ -191,8 +191,10 @@ class TBModel:
             H = H + ph[:, None, None] * t[None, :, :]
         return H
 
-    def eig(self, kfrac: np.ndarray, nproc: int = 1, cdtype=np.complex128, chunk: int = 1 << 16, grid=None):
+    def eig(self, kfrac: np.ndarray, nproc: int = 1, cdtype=np.complex128, chunk: int = 0, grid=None):
         B = kfrac.shape[0] if grid is None else grid[0].shape[0]
+        if chunk <= 0:  # k points per worker and batch: ~64 MB of Hamiltonians per worker
+            chunk = max(256, (1 << 22) // (self.norb * self.norb))
         w = np.empty((B, self.norb), dtype=np.float64)
         v = np.empty((B, self.norb, self.norb), dtype=cdtype)
         for s in range(0, B, chunk * max(1, nproc)):
