@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip chi0_tune (launch-shape autotuner) before the warm-up steps")
     ap.add_argument("--overlap", default="fp32", choices=["fp32", "bf16x3", "bf16x6", "tf32"],
                     help="matrix elements of the mixed form: FP32 on the CUDA cores (default) or the "
                          "tensor cores (BF16 split in two pieces / three pieces, or one TF32 product)")
@@ -53,7 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample-w", type=int, default=16, help="frequencies in the CPU sample (dynamic)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-q", type=int, default=1)
+    ap.add_argument("--cpu-sample-q", type=int, default=8,
+                    help="q points of the oracle's timed sample (8 q of the Cr-like run: ~10-15 s on 16 cores)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-out", default="")
     return ap.parse_args()
@@ -212,10 +215,10 @@ def fp32_peak_tflops(sm_mhz):
 
 # FP32 operations (FFMA counted twice, FADD, FMUL) of the mixed static weight kernels per
 # final tetrahedron on the Cr-like 48^3 workload, from ncu's instruction counters of
-# k_static + k_static_tab (8 q, 13.65 M final tetrahedra per launch); and their DRAM bytes
-# per final tetrahedron.
-FLOPS_PER_PIECE_MIXED = 205.5
-TRAFFIC_PER_PIECE_MIXED = 3.74
+# k_static + k_static_tab (one q of an 8-q run, 13.65 M final tetrahedra per launch); and
+# their DRAM bytes per final tetrahedron.
+FLOPS_PER_PIECE_MIXED = 202.6
+TRAFFIC_PER_PIECE_MIXED = 3.58
 # The same for k_dynamic per (final tetrahedron, frequency) on the FeSe-like model (ncu
 # counters of the four k_dynamic launches of one step on its 32x32x8 mesh, 2 q x 512 w:
 # 1.40 M final tetrahedra x 256 w per launch).
@@ -308,6 +311,9 @@ def run_ours(args):
     Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev, overlap=args.overlap)
     Pd = chi0.Plan(W, precision="fp64", device=True, profile=False, staged=dev) if args.fp64_steps > 0 else None
     nominal = W.nominal_evals()
+    tuned = None
+    if not args.no_tune:  # untimed: picks the weight kernel's block shape and grid, and the
+        tuned = Pm.tune(W.omega)  # tensor-core corner packing, on one call of the step
     for _ in range(args.warmup):
         run_step(Pm, W)
     torch.cuda.synchronize()
@@ -450,7 +456,7 @@ def run_ours(args):
                               "mixed_speedup": ms64 / ms} if ms64 else None),
                 "error": {"mixed_vs_fp64_gpu_max_rel": err_mixed, "vs_oracle": err_oracle},
                 "roofline": roof, "roofline_overlap": ovl, "stage_ms_per_q": stages,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "tuned": tuned,
                 "counters": counters, "clocks": ck, "peaks_source": kind}
         print(json.dumps(line), flush=True)
         if args.profile_out:

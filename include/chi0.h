@@ -149,7 +149,13 @@ typedef struct {
  *                 fails with CHI0_ETIMEOUT (0 = 2^31, about one second).
  *   test_stall    error-path test hook: 1 makes the tensor-core overlap kernel issue no
  *                 MMA, so that its bounded wait runs out and the call returns
- *                 CHI0_ETIMEOUT; 0 in normal use. */
+ *                 CHI0_ETIMEOUT; 0 in normal use.
+ *   graph         1: each chi0_static / chi0_dynamic call's launches (every q, every
+ *                 frequency pass) are captured once into a CUDA graph and replayed by later
+ *                 calls with the same q descriptors, frequency and output pointers (a
+ *                 different call is captured anew).  Explicit k+q data must then be device
+ *                 pointers (inputs_on_device); with profile, time_ms[CHI0_K_GRAPH] holds the
+ *                 graph launches. */
 typedef struct {
   int precision;
   int overlap;
@@ -162,7 +168,8 @@ typedef struct {
   int profile;
   long long wait_budget;
   int test_stall;
-  int reserved[7];
+  int graph;
+  int reserved[6];
 } chi0_opts_t;
 
 typedef struct chi0_plan chi0_plan_t;
@@ -176,6 +183,7 @@ typedef struct chi0_plan chi0_plan_t;
 #define CHI0_K_REDUCE 3
 #define CHI0_K_DOS 4
 #define CHI0_K_BANDS 5
+#define CHI0_K_GRAPH 6 /* graph mode: one replay of a captured call */
 #define CHI0_K_COUNT 8
 typedef struct {
   double time_ms[CHI0_K_COUNT];
@@ -212,6 +220,33 @@ int chi0_static(chi0_plan_t *plan, const chi0_q_t *q, int nq, double *chi);
  * (Eq. 3) for w < 0.  Errors as chi0_static, plus CHI0_EINVAL for nw <= 0. */
 int chi0_dynamic(chi0_plan_t *plan, const chi0_q_t *q, int nq, const double *omega, int nw,
                  double *re, double *im);
+
+/* Autotuner.  Times the call (static when omega == NULL, else dynamic on nw frequencies)
+ * once per candidate launch shape, with CUDA events on the plan's stream, and keeps the
+ * fastest shape in the plan for its later calls.  Candidates, tuned one after the other:
+ *   - block shape of the static weight kernel (threads and the register budget they
+ *     leave) with its persistent CTAs per SM (1 .. the occupancy limit), or the persistent
+ *     CTAs per SM of the dynamic weight kernel;
+ *   - corners per MMA round of the tensor-core overlap (CHI0_OVL_BF16X3, BF16X6 or TF32 only;
+ *     1, 2, 3, 4, 8, ... up to the most that fit one tile).
+ * Every candidate computes the same chi0 up to rounding: the k-batch partials and their
+ * summation order do not depend on the grid, and the corner grouping only changes how the
+ * tensor-core FP32 accumulators are split.  Each timed call writes its results to chi / re,
+ * im like chi0_static / chi0_dynamic.  *result: the chosen shape, the candidates timed, the
+ * best and the untuned call times (ms).  Errors as chi0_static / chi0_dynamic. */
+typedef struct {
+  int static_variant;       /* block shape of the static weight kernel: FP32 0 = 256
+                               threads x 2 blocks per SM (128 registers), 1 = 128 x 3,
+                               2 = 256 x 1; FP64 always 0                           */
+  int static_threads;       /* its threads per block                                */
+  int static_ctas_per_sm;   /* persistent CTAs per SM of the static weight kernel  */
+  int dynamic_ctas_per_sm;  /* ... of the dynamic weight kernel                     */
+  int tc_corners_per_round; /* tensor-core overlap corner cap (0: most that fit)    */
+  int candidates;           /* timed calls, the untuned one included                */
+  double best_ms, default_ms;
+} chi0_tune_t;
+int chi0_tune(chi0_plan_t *plan, const chi0_q_t *q, int nq, const double *omega, int nw, double *re,
+              double *im, chi0_tune_t *result);
 
 /* Static chi0 without any device allocation (the paper has no counterpart: this is a
  * deployment variant of chi0_static).

@@ -37,6 +37,7 @@ OVERLAP_MODES = {"fp32": CHI0_OVL_FP32, "bf16x3": CHI0_OVL_BF16X3, "tf32": CHI0_
 CHI0_SIGN_POSITIVE = 0
 CHI0_SIGN_PAPER = 1
 CHI0_K_OVERLAP, CHI0_K_STATIC, CHI0_K_DYNAMIC, CHI0_K_REDUCE, CHI0_K_DOS, CHI0_K_BANDS = 0, 1, 2, 3, 4, 5
+CHI0_K_GRAPH = 6
 CHI0_K_COUNT = 8
 # frequencies per k_dynamic launch: chi0_dynamic splits longer grids into passes of this size
 DYNAMIC_MAX_NW = 256
@@ -65,13 +66,20 @@ class chi0_opts_t(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("overlap", ct.c_int), ("cma", ct.c_int), ("sign", ct.c_int),
                 ("tau", ct.c_double), ("inputs_on_device", ct.c_int), ("outputs_on_device", ct.c_int),
                 ("stream", ct.c_void_p), ("profile", ct.c_int), ("wait_budget", ct.c_longlong),
-                ("test_stall", ct.c_int), ("reserved", ct.c_int * 7)]
+                ("test_stall", ct.c_int), ("graph", ct.c_int), ("reserved", ct.c_int * 6)]
 
 
 class chi0_stats_t(ct.Structure):
     _fields_ = [("time_ms", ct.c_double * CHI0_K_COUNT), ("launches", ct.c_longlong * CHI0_K_COUNT),
                 ("calls", ct.c_longlong), ("pieces", ct.c_longlong), ("fp64_evals", ct.c_longlong),
                 ("kernels", ct.c_longlong)]
+
+
+class chi0_tune_t(ct.Structure):
+    _fields_ = [("static_variant", ct.c_int), ("static_threads", ct.c_int),
+                ("static_ctas_per_sm", ct.c_int), ("dynamic_ctas_per_sm", ct.c_int),
+                ("tc_corners_per_round", ct.c_int), ("candidates", ct.c_int), ("best_ms", ct.c_double),
+                ("default_ms", ct.c_double)]
 
 
 class Chi0Error(RuntimeError):
@@ -84,7 +92,7 @@ _lib = None
 
 # every entry point declared in include/chi0.h (checked by the ABI test)
 EXPORTS = ["chi0_opts_default", "chi0_plan", "chi0_static", "chi0_dynamic", "chi0_plan_stats",
-           "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc"]
+           "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune"]
 CHI0_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -116,6 +124,9 @@ def lib():
         L.chi0_static_noalloc.argtypes = [ct.POINTER(chi0_kgrid_t), chi0_band_window_t, ct.POINTER(chi0_opts_t),
                                           ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p]
         L.chi0_static_noalloc.restype = ct.c_int
+        L.chi0_tune.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
+                                ct.c_void_p, ct.POINTER(chi0_tune_t)]
+        L.chi0_tune.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -148,6 +159,12 @@ def chi0_static(plan, q, nq: int, chi_ptr: int) -> None:
 
 def chi0_dynamic(plan, q, nq: int, omega_ptr: int, nw: int, re_ptr: int, im_ptr: int) -> None:
     _check(lib().chi0_dynamic(plan, q, nq, omega_ptr, nw, re_ptr, im_ptr), plan)
+
+
+def chi0_tune(plan, q, nq: int, omega_ptr, nw: int, re_ptr: int, im_ptr) -> chi0_tune_t:
+    r = chi0_tune_t()
+    _check(lib().chi0_tune(plan, q, nq, omega_ptr, nw, re_ptr, im_ptr, ct.byref(r)), plan)
+    return r
 
 
 def chi0_plan_stats(plan) -> chi0_stats_t:
@@ -257,7 +274,7 @@ class Plan:
     def __init__(self, W, precision: str = "fp64", device: bool = True, stream=None, profile: bool = False,
                  tau: float = 9.5367431640625e-07, sign: int = CHI0_SIGN_POSITIVE, tetra=None, window=None, cma=None,
                  qs: Optional[Sequence] = None, staged: Optional[Staged] = None, overlap: str = "fp32",
-                 wait_budget: int = 0, test_stall: bool = False):
+                 wait_budget: int = 0, test_stall: bool = False, graph: bool = False):
         self.W = W
         self.device = device
         self.keep = []
@@ -273,6 +290,9 @@ class Plan:
         o.overlap = OVERLAP_MODES[overlap]
         o.wait_budget = int(wait_budget)
         o.test_stall = 1 if test_stall else 0
+        o.graph = 1 if graph else 0
+        self.graph = bool(graph)
+        self._gout = {}
         o.profile = 1 if profile else 0
         o.inputs_on_device = 1 if device else 0
         o.outputs_on_device = 1 if device else 0
@@ -326,6 +346,13 @@ class Plan:
         nq = len(qarr)
         if self.device:
             t = self.torch
+            if out is None and self.graph:
+                # graph mode replays a call only with the same output pointers: one buffer per
+                # call shape, overwritten by the next call
+                key = ("s", nq)
+                if key not in self._gout:
+                    self._gout[key] = t.empty(nq, dtype=t.float64, device="cuda")
+                out = self._gout[key]
             o = out if out is not None else t.empty(nq, dtype=t.float64, device="cuda")
             chi0_static(self.h, qarr, nq, o.data_ptr())
             return o
@@ -343,6 +370,12 @@ class Plan:
             if getattr(self, "_om_host", None) is None or not np.array_equal(self._om_host, om):
                 self._om = t.from_numpy(om).to("cuda")
                 self._om_host = om.copy()
+            if out is None and self.graph:
+                key = ("d", nq, nw)
+                if key not in self._gout:
+                    self._gout[key] = (t.empty(nq * nw, dtype=t.float64, device="cuda"),
+                                       t.empty(nq * nw, dtype=t.float64, device="cuda"))
+                out = self._gout[key]
             re, im = out if out is not None else (t.empty(nq * nw, dtype=t.float64, device="cuda"),
                                                   t.empty(nq * nw, dtype=t.float64, device="cuda"))
             chi0_dynamic(self.h, qarr, nq, self._om.data_ptr(), nw, re.data_ptr(), im.data_ptr())
@@ -354,6 +387,24 @@ class Plan:
 
     def stats(self):
         return chi0_plan_stats(self.h)
+
+    def tune(self, omega=None, qarr=None) -> dict:
+        """chi0_tune on this plan's q points (static, or dynamic on ``omega``); returns the
+        chosen launch shape and the timings.  Device plans only."""
+        if not self.device:
+            raise ValueError("tune() runs on device-resident plans")
+        t = self.torch
+        qarr = self.qarr if qarr is None else qarr
+        nq = len(qarr)
+        if omega is None:
+            o = t.empty(nq, dtype=t.float64, device="cuda")
+            r = chi0_tune(self.h, qarr, nq, None, 0, o.data_ptr(), None)
+        else:
+            om = t.from_numpy(np.ascontiguousarray(omega, dtype=np.float64)).to("cuda")
+            re = t.empty(nq * om.numel(), dtype=t.float64, device="cuda")
+            im = t.empty_like(re)
+            r = chi0_tune(self.h, qarr, nq, om.data_ptr(), om.numel(), re.data_ptr(), im.data_ptr())
+        return {k: getattr(r, k) for k, _ in chi0_tune_t._fields_}
 
     def counters(self):
         s = self.stats()

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <stdint.h>
 #include <vector>
 
 #include "../../include/chi0.h"
@@ -40,15 +41,24 @@ struct chi0_plan {
   void *C32_d = nullptr;                      // complex64 copy of complex128 eigenvectors (mixed)
   int *next_d = nullptr;                      // [2] batch counter, FP64 list size
   int *err_d = nullptr;                       // error word of the bounded device waits
+  cudaStream_t cap_s = nullptr;               // graph mode: private stream the graph runs on,
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // ordered after / before the plan's stream
+  cudaGraph_t graph = nullptr;                // graph mode: the captured call and its key
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> gkey;
+  long long gkernels = 0;
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
-  int static_grid = 0, dynamic_grid = 0;
+  int static_grid = 0, dynamic_grid = 0;  // persistent CTAs of the weight kernels
+  int static_variant = 0;                  // block shape of the static weight kernel
+  int tc_gcap = 0;                         // corners per tensor-core round (0: most that fit)
   size_t part_cap = 0;
   chi0_stats_t stats;
   char err[512];
 };
 
 static char g_plan_err[512] = "";
+static void drop_graph(chi0_plan_t *p);
 
 namespace chi0int {
 void set_global_error(const char *msg) { snprintf(g_plan_err, sizeof(g_plan_err), "%s", msg); }
@@ -105,6 +115,7 @@ extern "C" int chi0_plan_stats(const chi0_plan_t *p, chi0_stats_t *s) {
 
 static void release(chi0_plan_t *p) {
   if (!p) return;
+  drop_graph(p);
   if (p->own_E) cudaFree(p->E_d);
   if (p->own_C) cudaFree(p->C_d);
   cudaFree(p->tet_d);
@@ -154,6 +165,7 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     return fail(p, CHI0_ENOTSUP, "tensor-core overlaps belong to the mixed-precision form");
   if (op.test_stall && op.overlap == CHI0_OVL_FP32)
     return fail(p, CHI0_EINVAL, "test_stall needs a tensor-core overlap mode");
+  if (op.graph && op.test_stall) return fail(p, CHI0_EINVAL, "graph mode and test_stall exclude each other");
   if (!(op.tau >= 0.0 && op.tau < 1.0)) return fail(p, CHI0_EINVAL, "tau must lie in [0, 1)");
   for (int d = 0; d < 3; ++d)
     if (kg->n[d] < 1 || kg->n[d] > (1 << 12)) return fail(p, CHI0_EINVAL, "n[%d] = %d out of range", d, kg->n[d]);
@@ -302,8 +314,9 @@ struct Timer {
   chi0_plan_t *p;
   std::vector<cudaEvent_t> ev;
   std::vector<int> kind;
+  bool on = true;  // off while a graph is being captured
   int start(int k) {
-    if (!p->opts.profile) return 0;
+    if (!p->opts.profile || !on) return 0;
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1;
     ev.push_back(a);
@@ -312,7 +325,7 @@ struct Timer {
     return cudaEventRecord(a, p->stream) == cudaSuccess ? 0 : -1;
   }
   int stop() {
-    if (!p->opts.profile) return 0;
+    if (!p->opts.profile || !on) return 0;
     return cudaEventRecord(ev.back(), p->stream) == cudaSuccess ? 0 : -1;
   }
   void collect() {
@@ -383,43 +396,15 @@ int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q) {
 
 }  // namespace
 
-static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, int nw, double *re,
-               double *im) {
-  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
-  if (nq <= 0 || !qs) return fail(p, CHI0_EINVAL, "nq = %d or q NULL", nq);
-  const bool dyn = omega != nullptr;
-  if (dyn && (nw <= 0 || !re || !im)) return fail(p, CHI0_EINVAL, "dynamic call needs nw > 0, re and im");
-  if (!dyn && !re) return fail(p, CHI0_EINVAL, "chi is NULL");
+// Every launch and device-side copy of one call, in stream order (the part a CUDA graph
+// captures): counters, then per q the overlap, DOS, band bounds, weights and reductions.
+static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *om_d, int nw, bool dyn,
+                        double *outR, double *outI, Timer &tm, bool tc) {
   const chi0_opts_t &op = p->opts;
   const int fp64 = op.precision == CHI0_PREC_FP64;
   const double scale = op.sign == CHI0_SIGN_PAPER ? -2.0 : 2.0;
   cudaStream_t s = p->stream;
-  Timer tm{p, {}, {}};
-  const int nwo = dyn ? nw : 1;
-  const size_t outn = (size_t)nq * nwo * (dyn ? 2 : 1);
-  double *outR = nullptr, *outI = nullptr;
-  const double *om_d = nullptr;
-  if (op.outputs_on_device) {
-    outR = re;
-    outI = dyn ? im : nullptr;
-  } else {
-    int rc = ensure(p, (void **)&p->out_d, &p->out_cap, sizeof(double) * outn);
-    if (rc) return rc;
-    outR = p->out_d;
-    outI = dyn ? p->out_d + (size_t)nq * nw : nullptr;
-  }
-  if (dyn) {
-    if (op.inputs_on_device) {
-      om_d = omega;
-    } else {
-      int rc = ensure(p, (void **)&p->omega_d, &p->omega_cap, sizeof(double) * nw);
-      if (rc) return rc;
-      CK(p, cudaMemcpyAsync(p->omega_d, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
-      om_d = p->omega_d;
-    }
-  }
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, s));
-  const bool tc = op.overlap != CHI0_OVL_FP32 && !op.cma && !fp64;
   for (int iq = 0; iq < nq; ++iq) {
     Q q;
     int rc = prepare_q(p, qs[iq], q);
@@ -428,7 +413,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
       tm.start(CHI0_K_OVERLAP);
       if (tc)
         CK(p, launch_overlap_tc(p->g, p->C32_d ? p->C32_d : p->C_d, p->dtype, q, (float *)p->W2_d,
-                                tc_mode(op.overlap), op.wait_budget, op.test_stall,
+                                tc_mode(op.overlap), op.wait_budget, op.test_stall, p->tc_gcap,
                                 p->err_d, s));
       else
         CK(p, launch_overlap(p->g, p->E_d, p->C_d, p->dtype, q, p->W2_d, fp64, s, p->C32_d));
@@ -462,7 +447,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
       StaticBufs sb{p->tq_d, p->tq_n_d, p->partR, p->next_d, static_tab_cap()};
       tm.start(CHI0_K_STATIC);
       CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq, sb,
-                          p->static_grid, p->counters_d, s));
+                          p->static_grid, p->counters_d, s, p->static_variant));
       p->stats.kernels += 2;
       tm.stop();
       tm.start(CHI0_K_REDUCE);
@@ -487,6 +472,120 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
         tm.stop();
       }
     }
+  }
+  return CHI0_OK;
+}
+
+// graph key: everything the captured sequence depends on besides the plan itself
+static std::vector<unsigned char> call_key(const chi0_q_t *qs, int nq, const double *om_d, int nw, bool dyn,
+                                           const double *outR, const double *outI) {
+  std::vector<unsigned char> k(sizeof(chi0_q_t) * (size_t)nq + 64, 0);
+  memcpy(k.data(), qs, sizeof(chi0_q_t) * (size_t)nq);
+  unsigned char *t = k.data() + sizeof(chi0_q_t) * (size_t)nq;
+  const long long v[5] = {(long long)nq, (long long)nw, (long long)dyn, (long long)(uintptr_t)om_d,
+                          (long long)(uintptr_t)outR};
+  memcpy(t, v, sizeof(v));
+  const long long w = (long long)(uintptr_t)outI;
+  memcpy(t + sizeof(v), &w, sizeof(w));
+  return k;
+}
+
+static void drop_graph(chi0_plan_t *p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap_s) cudaStreamDestroy(p->cap_s);
+  if (p->ev_in) cudaEventDestroy(p->ev_in);
+  if (p->ev_out) cudaEventDestroy(p->ev_out);
+  p->cap_s = nullptr;
+  p->ev_in = p->ev_out = nullptr;
+  p->gexec = nullptr;
+  p->graph = nullptr;
+  p->gkey.clear();
+  p->gkernels = 0;
+}
+
+static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, int nw, double *re,
+               double *im) {
+  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
+  if (nq <= 0 || !qs) return fail(p, CHI0_EINVAL, "nq = %d or q NULL", nq);
+  const bool dyn = omega != nullptr;
+  if (dyn && (nw <= 0 || !re || !im)) return fail(p, CHI0_EINVAL, "dynamic call needs nw > 0, re and im");
+  if (!dyn && !re) return fail(p, CHI0_EINVAL, "chi is NULL");
+  const chi0_opts_t &op = p->opts;
+  const int fp64 = op.precision == CHI0_PREC_FP64;
+  cudaStream_t s = p->stream;
+  Timer tm{p, {}, {}};
+  const int nwo = dyn ? nw : 1;
+  const size_t outn = (size_t)nq * nwo * (dyn ? 2 : 1);
+  double *outR = nullptr, *outI = nullptr;
+  const double *om_d = nullptr;
+  if (op.outputs_on_device) {
+    outR = re;
+    outI = dyn ? im : nullptr;
+  } else {
+    int rc = ensure(p, (void **)&p->out_d, &p->out_cap, sizeof(double) * outn);
+    if (rc) return rc;
+    outR = p->out_d;
+    outI = dyn ? p->out_d + (size_t)nq * nw : nullptr;
+  }
+  if (dyn) {
+    if (op.inputs_on_device) {
+      om_d = omega;
+    } else {
+      int rc = ensure(p, (void **)&p->omega_d, &p->omega_cap, sizeof(double) * nw);
+      if (rc) return rc;
+      CK(p, cudaMemcpyAsync(p->omega_d, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
+      om_d = p->omega_d;
+    }
+  }
+  const bool tc = op.overlap != CHI0_OVL_FP32 && !op.cma && !fp64;
+  if (op.graph) {
+    // replay the captured sequence when the call matches the one captured, else capture anew
+    std::vector<unsigned char> key = call_key(qs, nq, om_d, nw, dyn, outR, outI);
+    if (!p->gexec || key != p->gkey) {
+      drop_graph(p);
+      for (int iq = 0; iq < nq; ++iq)
+        if ((qs[iq].e_kq || qs[iq].c_kq) && !op.inputs_on_device)
+          return fail(p, CHI0_ENOTSUP, "graph mode needs device-resident inputs");
+      // the graph is captured on (and later launched on) a private stream: the plan's stream
+      // may be the legacy default stream, which cannot be captured
+      CK(p, cudaStreamCreateWithFlags(&p->cap_s, cudaStreamNonBlocking));
+      CK(p, cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+      CK(p, cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
+      Timer off{p, {}, {}, false};
+      const long long k0 = p->stats.kernels;
+      CK(p, cudaStreamBeginCapture(p->cap_s, cudaStreamCaptureModeThreadLocal));
+      p->stream = p->cap_s;
+      const int rc = enqueue_call(p, qs, nq, om_d, nw, dyn, outR, outI, off, tc);
+      p->stream = s;
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(p->cap_s, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ec != cudaSuccess) return fail(p, CHI0_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+      p->graph = g;
+      const cudaError_t ei = cudaGraphInstantiate(&p->gexec, g, 0);
+      if (ei != cudaSuccess) {
+        drop_graph(p);
+        return fail(p, CHI0_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+      }
+      p->gkey = key;
+      p->gkernels = p->stats.kernels - k0;
+      p->stats.kernels = k0;
+    }
+    tm.start(CHI0_K_GRAPH);
+    CK(p, cudaEventRecord(p->ev_in, s));
+    CK(p, cudaStreamWaitEvent(p->cap_s, p->ev_in, 0));
+    CK(p, cudaGraphLaunch(p->gexec, p->cap_s));
+    CK(p, cudaEventRecord(p->ev_out, p->cap_s));
+    CK(p, cudaStreamWaitEvent(s, p->ev_out, 0));
+    tm.stop();
+    p->stats.kernels += p->gkernels;
+  } else {
+    const int rc = enqueue_call(p, qs, nq, om_d, nw, dyn, outR, outI, tm, tc);
+    if (rc) return rc;
   }
   if (tc) {  // the tensor-core overlap's bounded waits report through the error word
     int herr = 0;
@@ -523,4 +622,98 @@ extern "C" int chi0_dynamic(chi0_plan_t *p, const chi0_q_t *q, int nq, const dou
                             double *im) {
   if (!omega) return fail(p, CHI0_EINVAL, "omega is NULL");
   return run(p, q, nq, omega, nw, re, im);
+}
+
+// ---------------------------------------------------------------- autotuner
+// Wall time of one call on the plan's stream (CUDA events; the call itself may synchronize).
+static int timed_call(chi0_plan_t *p, const chi0_q_t *q, int nq, const double *omega, int nw, double *re,
+                      double *im, float *ms) {
+  cudaEvent_t a, b;
+  CK(p, cudaEventCreate(&a));
+  CK(p, cudaEventCreate(&b));
+  CK(p, cudaEventRecord(a, p->stream));
+  const int rc = run(p, q, nq, omega, nw, re, im);
+  if (rc) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+  }
+  CK(p, cudaEventRecord(b, p->stream));
+  CK(p, cudaEventSynchronize(b));
+  CK(p, cudaEventElapsedTime(ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return CHI0_OK;
+}
+
+extern "C" int chi0_tune(chi0_plan_t *p, const chi0_q_t *q, int nq, const double *omega, int nw, double *re,
+                         double *im, chi0_tune_t *res) {
+  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
+  if (!res) return fail(p, CHI0_EINVAL, "result is NULL");
+  memset(res, 0, sizeof(*res));
+  const chi0_opts_t &op = p->opts;
+  const int fp64 = op.precision == CHI0_PREC_FP64;
+  const bool dyn = omega != nullptr;
+  const int sms = device_sms();
+  const int graph = p->opts.graph;
+  p->opts.graph = 0;  // every candidate runs its own launch sequence
+  float ms = 0.f;
+  int rc = run(p, q, nq, omega, nw, re, im);  // warm-up (first-touch, module load)
+  if (!rc) rc = timed_call(p, q, nq, omega, nw, re, im, &ms);
+  if (rc) {
+    p->opts.graph = graph;
+    return rc;
+  }
+  res->default_ms = ms;
+  float best = ms;
+  int cand = 1;
+  // 1. block shape (static) and persistent CTAs per SM of the weight kernel this call uses
+  int *grid = dyn ? &p->dynamic_grid : &p->static_grid;
+  int best_grid = *grid, best_var = p->static_variant;
+  const int nvar = dyn ? 1 : static_variants(fp64);
+  for (int v = 0; v < nvar && !rc; ++v) {
+    const int maxc = dyn ? dynamic_max_ctas_per_sm(fp64) : static_max_ctas_per_sm(fp64, v);
+    for (int c = 1; c <= maxc; ++c) {
+      if (c * sms == best_grid && (dyn || v == best_var)) continue;  // the untuned shape
+      *grid = c * sms;
+      if (!dyn) p->static_variant = v;
+      rc = timed_call(p, q, nq, omega, nw, re, im, &ms);
+      if (rc) break;
+      ++cand;
+      if (ms < best) {
+        best = ms;
+        best_grid = *grid;
+        best_var = v;
+      }
+    }
+  }
+  *grid = best_grid;
+  if (!dyn) p->static_variant = best_var;
+  // 2. corners per tensor-core round (the tile's M/N packing)
+  const bool tc = op.overlap != CHI0_OVL_FP32 && !op.cma && !fp64;
+  int best_g = p->tc_gcap;
+  if (!rc && tc) {
+    const int gmax = overlap_tc_max_corners(p->win.hi - p->win.lo, p->g.norb, tc_mode(op.overlap));
+    for (int gc = 1; gc <= gmax; gc = gc < 4 ? gc + 1 : gc * 2) {
+      p->tc_gcap = gc;
+      rc = timed_call(p, q, nq, omega, nw, re, im, &ms);
+      if (rc) break;
+      ++cand;
+      if (ms < best) {
+        best = ms;
+        best_g = gc;
+      }
+    }
+    p->tc_gcap = best_g;
+  }
+  p->opts.graph = graph;
+  if (rc) return rc;
+  res->static_variant = p->static_variant;
+  res->static_threads = static_variant_threads(fp64, p->static_variant);
+  res->static_ctas_per_sm = p->static_grid / sms;
+  res->dynamic_ctas_per_sm = p->dynamic_grid / sms;
+  res->tc_corners_per_round = p->tc_gcap;
+  res->candidates = cand;
+  res->best_ms = best;
+  return CHI0_OK;
 }

@@ -83,7 +83,7 @@ struct StaticBufs {
 // energies, empq from the k+q energies
 cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
-                          const StaticBufs &sb, int nblocks, unsigned long long *counters, cudaStream_t s);
+                          const StaticBufs &sb, int nblocks, unsigned long long *counters, cudaStream_t s, int variant = 0);
 int static_persistent_blocks(int fp64);
 long long static_batches(long long ntet);
 int static_tab_cap();
@@ -125,8 +125,16 @@ int dynamic_max_nw();
 enum { TC_TF32 = 0, TC_BF16X3 = 1, TC_BF16X6 = 2 };
 constexpr size_t kTcSmemMax = 227 * 1024;
 size_t overlap_tc_smem(int w, int norb, int mode);  // bytes of shared memory ((size_t)-1: w > 128)
+int overlap_tc_max_corners(int w, int norb, int mode);  // corners per MMA round, untuned
+// gcap > 0: at most gcap corners per MMA round (autotuner candidates)
 cudaError_t launch_overlap_tc(const Grid &g, const void *C32, int dtype, const Q &q, float *W2, int mode,
-                              long long budget, int test_stall, int *err, cudaStream_t s);
+                              long long budget, int test_stall, int gcap, int *err, cudaStream_t s);
+// resident CTAs per SM of the weight kernels (occupancy limit) and SMs of the device
+int static_max_ctas_per_sm(int fp64, int variant);
+int static_variants(int fp64);                      // block shapes of the static weight kernel
+int static_variant_threads(int fp64, int variant);  // threads per block of a shape
+int dynamic_max_ctas_per_sm(int fp64);
+int device_sms();
 
 #ifdef __CUDACC__
 // corner index with periodic wrap (32-bit: the plan checks that the mesh has fewer than 2^31

@@ -255,24 +255,22 @@ __device__ __noinline__ double piece_eval(const Piece<typename std::conditional<
   }
 }
 
-// resident blocks per SM the register allocation of the static kernel must allow
-#ifndef CHI0_STATIC_MINB_F32
-#define CHI0_STATIC_MINB_F32 2
-#endif
-#ifndef CHI0_STATIC_MINB_F64
-#define CHI0_STATIC_MINB_F64 1
-#endif
 
-template <bool FP64>
-__global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_STATIC_MINB_F32)
+// Block shapes of k_static (threads, resident blocks per SM the register allocation must
+// allow): the autotuner picks one per plan.  FP32: 256 x 2 (128 registers), 128 x 3 (170),
+// 256 x 1 (255); FP64: 256 x 1.
+template <bool FP64, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_static(Grid g, Tet tet, const void *__restrict__ Ek, const void *__restrict__ Ekq, Q q,
              const void *__restrict__ W2, int cma, float tau, const short *__restrict__ occ,
              const short *__restrict__ empq, StaticBufs sb, unsigned long long *__restrict__ counters) {
   using T = typename std::conditional<FP64, double, float>::type;
+  constexpr int kWarps = NT / 32;  // warps of this block shape
   __shared__ int s_c[kWarps][32][4], s_cq[kWarps][32][4];
   __shared__ T s_vol[kWarps][32];
   __shared__ int s_nlo[kWarps][32], s_nn[kWarps][32], s_pre[kWarps][33];
   __shared__ int s_qn[kWarps];
+  __shared__ int s_list[kWarps][2][64], s_nl[kWarps][2];  // items l << 24 | m << 12 | n
   Piece<T> *tq = (Piece<T> *)sb.tq;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = q.hi - q.lo;
@@ -319,22 +317,36 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
     if (lane == 0) s_pre[wib][0] = 0;
     const int total = __shfl_sync(kFull, pre, 31);
     __syncwarp();
-    for (int it = lane; it < total; it += 32) {
-      int lo_ = 0, hi_ = 32;  // owner: largest l with s_pre[l] <= it
-#pragma unroll
-      for (int step = 0; step < 5; ++step) {
-        const int mid = (lo_ + hi_) >> 1;
-        if (s_pre[wib][mid] <= it) lo_ = mid;
-        else hi_ = mid;
+    // final tetrahedron -> series on the spot, or the batch's queue region
+    auto emit = [&](T r, T d[4], T ff[4], T vol2) {
+      sort4(d, ff);
+      ++npieces;
+      if (series_ok(d, T(Num<T>::kappa))) {
+        acc.add(vol2 * r * series_sum(d, ff));
+        return;
       }
-      const int l = lo_;
-      const int loc = it - s_pre[wib][l];
-      const int nn = s_nn[wib][l];
-      const int mo = div_small(loc, nn, q.hi - q.lo);
-      const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
-      if (q.gamma && m == n) continue;  // intraband at Gamma: replaced by the DOS limit
-      T a[4], b[4], f[4];
-      T amin = T(1e30), bmax = T(-1e30);
+      Piece<T> pc;
+      int fp = 0;
+      if constexpr (FP64) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pc.d[i] = d[i];
+      } else {
+        fp = mixed_knots(pc.d, d, tau) ? 1 : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) pc.f[i] = ff[i];
+      pc.w = vol2 * r;
+      pc.i64 = fp ? 1 : -1;
+      const int slot = atomicAdd(&s_qn[wib], 1);
+      if (slot < sb.tcap) {
+        nfp64 += fp;
+        tq[(long long)batch * sb.tcap + slot] = pc;
+      } else {
+        acc_q += piece_eval<FP64>(pc, tau, nfp64);
+      }
+    };
+    // corner data of item (tetrahedron l of the batch, bands m, n)
+    auto load = [&](int l, int m, int n, T a[4], T b[4]) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
@@ -345,42 +357,91 @@ __global__ void __launch_bounds__(kThreads, FP64 ? CHI0_STATIC_MINB_F64 : CHI0_S
           a[i] = ((const float *)Ek)[(long long)ck * g.nb + m];
           b[i] = ((const float *)Ekq)[(long long)cq * g.nb + n];
         }
-        amin = a[i] < amin ? a[i] : amin;
-        bmax = b[i] > bmax ? b[i] : bmax;
       }
-      if (!(amin < T(0) && bmax > T(0))) continue;
+    };
+    auto load_f = [&](int l, int m, int n, T f[4]) {
       const T *W2t = (const T *)W2;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
-      const T vol2 = s_vol[wib][l];
-      carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) {
-        sort4(d, ff);
-        ++npieces;
-        if (series_ok(d, T(Num<T>::kappa))) {
-          acc.add(vol2 * r * series_sum(d, ff));
-          return;
+    };
+    // Items are sorted into two per-warp lists, whole-tetrahedron items (most of them: one
+    // final tetrahedron, no cut) and items whose tetrahedron a Fermi surface cuts, and each
+    // list is evaluated 32 items at a time, so that the lanes of a warp run the same path
+    // (the few carving lanes no longer hold up the rest).  One call site of the carving.
+    auto drain = [&](bool final) {
+      for (;;) {  // warp-uniform
+        const int nf = s_nl[wib][0], nc = s_nl[wib][1];
+        int which;
+        if (nf >= 32) which = 0;
+        else if (nc >= 32) which = 1;
+        else if (final && nf > 0) which = 0;
+        else if (final && nc > 0) which = 1;
+        else break;
+        const int cnt = which ? nc : nf;
+        const int take = cnt < 32 ? cnt : 32;
+        int e = 0;
+        if (lane < take) e = s_list[wib][which][cnt - take + lane];
+        __syncwarp();
+        if (lane == 0) s_nl[wib][which] = cnt - take;
+        __syncwarp();
+        if (lane < take) {
+          const unsigned u = (unsigned)e;
+          const int l = (int)(u >> 24), m = (int)((u >> 12) & 0xFFFu), n = (int)(u & 0xFFFu);
+          T a[4], b[4], f[4];
+          load(l, m, n, a, b);
+          load_f(l, m, n, f);
+          const T vol2 = s_vol[wib][l];
+          carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) { emit(r, d, ff, vol2); });
         }
-        Piece<T> pc;
-        int fp = 0;
-        if constexpr (FP64) {
+      }
+    };
+    if (lane < 2) s_nl[wib][lane] = 0;
+    __syncwarp();
+    for (int base = 0;; base += 32) {  // warp-uniform; the pass after the last items drains
+      const bool last = base >= total;
+      const int it = base + lane;
+      int kind = -1, code = 0;  // 0: whole tetrahedron, 1: cut, -1: nothing to do
+      if (it < total) {
+        int lo_ = 0, hi_ = 32;  // owner: largest l with s_pre[l] <= it
 #pragma unroll
-          for (int i = 0; i < 4; ++i) pc.d[i] = d[i];
-        } else {
-          fp = mixed_knots(pc.d, d, tau) ? 1 : 0;
+        for (int step = 0; step < 5; ++step) {
+          const int mid = (lo_ + hi_) >> 1;
+          if (s_pre[wib][mid] <= it) lo_ = mid;
+          else hi_ = mid;
         }
+        const int l = lo_;
+        const int loc = it - s_pre[wib][l];
+        const int nn = s_nn[wib][l];
+        const int mo = div_small(loc, nn, q.hi - q.lo);
+        const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
+        if (!(q.gamma && m == n)) {  // intraband at Gamma: replaced by the DOS limit
+          T a[4], b[4];
+          load(l, m, n, a, b);
+          T amin = a[0], amax = a[0], bmin = b[0], bmax = b[0];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) pc.f[i] = ff[i];
-        pc.w = vol2 * r;
-        pc.i64 = fp ? 1 : -1;
-        const int slot = atomicAdd(&s_qn[wib], 1);
-        if (slot < sb.tcap) {
-          nfp64 += fp;
-          tq[(long long)batch * sb.tcap + slot] = pc;
-        } else {
-          acc_q += piece_eval<FP64>(pc, tau, nfp64);
+          for (int i = 1; i < 4; ++i) {
+            amin = a[i] < amin ? a[i] : amin;
+            amax = a[i] > amax ? a[i] : amax;
+            bmin = b[i] < bmin ? b[i] : bmin;
+            bmax = b[i] > bmax ? b[i] : bmax;
+          }
+          if (amin < T(0) && bmax > T(0)) {
+            kind = (amax < T(0) && bmin > T(0)) ? 0 : 1;
+            code = (l << 24) | (m << 12) | n;
+          }
         }
-      });
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const unsigned bal = __ballot_sync(kFull, kind == k);
+        if (kind == k) s_list[wib][k][s_nl[wib][k] + __popc(bal & ((1u << lane) - 1u))] = code;
+        __syncwarp();
+        if (lane == 0) s_nl[wib][k] += __popc(bal);
+        __syncwarp();
+      }
+      drain(last);
+      if (last) break;
     }
     __syncwarp();
     const double v = warp_sum(acc.value() + acc_q);
@@ -873,15 +934,26 @@ cudaError_t launch_bands(const double *E, long long nc, int nb, double ef, short
   return cudaGetLastError();
 }
 
-int static_persistent_blocks(int fp64) {
-  int nb = 0;
-  cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<true>, kThreads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<false>, kThreads, 0);
-  if (e != cudaSuccess || nb < 1) nb = 1;
+int device_sms() {
   int dev = 0, sms = kSMs;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return nb * sms;
+  return sms;
 }
+
+int static_max_ctas_per_sm(int fp64, int variant) {
+  int nb = 0;
+  cudaError_t e;
+  if (fp64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<true, 256, 1>, 256, 0);
+  else if (variant == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<false, 128, 3>, 128, 0);
+  else if (variant == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<false, 256, 1>, 256, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_static<false, 256, 2>, 256, 0);
+  return (e != cudaSuccess || nb < 1) ? 1 : nb;
+}
+
+int static_variants(int fp64) { return fp64 ? 1 : 3; }
+int static_variant_threads(int fp64, int variant) { return !fp64 && variant == 1 ? 128 : 256; }
+
+int static_persistent_blocks(int fp64) { return static_max_ctas_per_sm(fp64, 0) * device_sms(); }
 
 long long static_batches(long long ntet) { return (ntet + 31) / 32; }
 int static_tab_cap() { return kTabCap; }
@@ -889,14 +961,19 @@ size_t static_piece_bytes(int fp64) { return fp64 ? sizeof(Piece<double>) : size
 
 cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
-                          const StaticBufs &sb, int nblocks, unsigned long long *counters, cudaStream_t s) {
+                          const StaticBufs &sb, int nblocks, unsigned long long *counters, cudaStream_t s,
+                          int variant) {
   cudaError_t e = cudaMemsetAsync(sb.next, 0, sizeof(int), s);  // batch counter
   if (e != cudaSuccess) return e;
   const long long nbatch = static_batches(g.ntet);
   if (fp64)
-    k_static<true><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
+    k_static<true, 256, 1><<<nblocks, 256, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
+  else if (variant == 1)
+    k_static<false, 128, 3><<<nblocks, 128, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
+  else if (variant == 2)
+    k_static<false, 256, 1><<<nblocks, 256, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
   else
-    k_static<false><<<nblocks, kThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
+    k_static<false, 256, 2><<<nblocks, 256, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   long long tb = (nbatch * 32 + kThreads - 1) / kThreads;
   const int tblocks = (int)(tb < kSMs * 16 ? tb : kSMs * 16);
@@ -923,15 +1000,14 @@ cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const 
   return cudaGetLastError();
 }
 
-int dynamic_persistent_blocks(int fp64) {
+int dynamic_max_ctas_per_sm(int fp64) {
   int nb = 0;
   cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<true>, kDynThreads, 0)
                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<false>, kDynThreads, 0);
-  if (e != cudaSuccess || nb < 1) nb = 1;
-  int dev = 0, sms = kSMs;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return nb * sms;
+  return (e != cudaSuccess || nb < 1) ? 1 : nb;
 }
+
+int dynamic_persistent_blocks(int fp64) { return dynamic_max_ctas_per_sm(fp64) * device_sms(); }
 
 cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,
                        int nblocks, cudaStream_t s) {

@@ -55,7 +55,8 @@ struct TcShape {
   size_t smem;
 };
 
-__host__ __device__ inline TcShape tc_shape(int w, int norb, int mode) {
+// gcap > 0 caps the corners per round (the autotuner's candidates)
+__host__ __device__ inline TcShape tc_shape(int w, int norb, int mode, int gcap) {
   TcShape s{};
   s.w = w;
   s.NW = (w + 7) & ~7;
@@ -68,6 +69,7 @@ __host__ __device__ inline TcShape tc_shape(int w, int norb, int mode) {
   const int g1 = kTcM / (w > 0 ? w : 1), g2 = kTcMaxN / (2 * s.NW);
   s.G = g1 < g2 ? g1 : g2;
   if (s.G < 1) s.G = 0;  // window too wide for one tile
+  if (gcap > 0 && s.G > gcap) s.G = gcap;
   if (mode != TC_TF32 && s.G > 1) {
     // fewer corners per round when that lets every K step have its own accumulator
     const int g3 = kTcCols / (2 * s.NW * s.nks);
@@ -173,9 +175,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 template <int MODE, typename CTq>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_overlap_tc(Grid g, const float2 *__restrict__ C, const CTq *__restrict__ Cb, int explicit_q, Q q,
-                 float *__restrict__ W2, long long budget, int test_stall, int *__restrict__ err) {
+                 float *__restrict__ W2, long long budget, int test_stall, int gcap, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TcShape sh = tc_shape(q.hi - q.lo, g.norb, MODE);
+  const TcShape sh = tc_shape(q.hi - q.lo, g.norb, MODE, gcap);
   const int w = sh.w, NW = sh.NW, G = sh.G, KB = sh.Kbytes / 16, no = g.norb;
   const size_t a_piece = (size_t)kTcM * sh.Kbytes, b_piece = (size_t)sh.N * sh.Kbytes;
   unsigned char *sA = smem;
@@ -321,8 +323,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 template <int MODE, typename CTq>
 cudaError_t launch_tc(const Grid &g, const float2 *Ck, const CTq *Cb, int explicit_q, const Q &q, float *W2,
-                      long long budget, int test_stall, int *err, cudaStream_t s) {
-  const TcShape sh = tc_shape(q.hi - q.lo, g.norb, MODE);
+                      long long budget, int test_stall, int gcap, int *err, cudaStream_t s) {
+  const TcShape sh = tc_shape(q.hi - q.lo, g.norb, MODE, gcap);
   const size_t floor_smem = sh.ncols > 256 ? (size_t)kTcOneSmem : (size_t)kTcMinSmem;
   const size_t smem = sh.smem < floor_smem ? floor_smem : sh.smem;
   cudaError_t e = cudaFuncSetAttribute(k_overlap_tc<MODE, CTq>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -335,41 +337,43 @@ cudaError_t launch_tc(const Grid &g, const float2 *Ck, const CTq *Cb, int explic
   long long blocks = (long long)sms * per_sm;
   if (blocks > nround) blocks = nround;
   k_overlap_tc<MODE, CTq><<<(int)blocks, kTcThreads, smem, s>>>(g, Ck, Cb, explicit_q, q, W2, budget, test_stall,
-                                                                err);
+                                                                gcap, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t overlap_tc_smem(int w, int norb, int mode) {
-  const TcShape sh = tc_shape(w, norb, mode);
+  const TcShape sh = tc_shape(w, norb, mode, 0);
   if (sh.G < 1) return (size_t)-1;
   return sh.smem;
 }
 
+int overlap_tc_max_corners(int w, int norb, int mode) { return tc_shape(w, norb, mode, 0).G; }
+
 cudaError_t launch_overlap_tc(const Grid &g, const void *C32, int dtype, const Q &q, float *W2, int mode,
-                              long long budget, int test_stall, int *err, cudaStream_t s) {
+                              long long budget, int test_stall, int gcap, int *err, cudaStream_t s) {
   const int w = q.hi - q.lo;
   if (w < 1 || overlap_tc_smem(w, g.norb, mode) > kTcSmemMax || !err) return cudaErrorInvalidValue;
   const float2 *Ck = (const float2 *)C32;
   if (budget <= 0) budget = 1LL << 31;
   if (mode == TC_BF16X6) {
     if (q.Cq && dtype == DT_C128)
-      return launch_tc<TC_BF16X6, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
+      return launch_tc<TC_BF16X6, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, gcap, err, s);
     if (q.Cq)
-      return launch_tc<TC_BF16X6, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
-    return launch_tc<TC_BF16X6, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, err, s);
+      return launch_tc<TC_BF16X6, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, gcap, err, s);
+    return launch_tc<TC_BF16X6, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, gcap, err, s);
   }
   if (mode == TC_TF32) {
     if (q.Cq && dtype == DT_C128)
-      return launch_tc<TC_TF32, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
-    if (q.Cq) return launch_tc<TC_TF32, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
-    return launch_tc<TC_TF32, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, err, s);
+      return launch_tc<TC_TF32, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, gcap, err, s);
+    if (q.Cq) return launch_tc<TC_TF32, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, gcap, err, s);
+    return launch_tc<TC_TF32, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, gcap, err, s);
   }
   if (q.Cq && dtype == DT_C128)
-    return launch_tc<TC_BF16X3, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
-  if (q.Cq) return launch_tc<TC_BF16X3, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, err, s);
-  return launch_tc<TC_BF16X3, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, err, s);
+    return launch_tc<TC_BF16X3, double2>(g, Ck, (const double2 *)q.Cq, 1, q, W2, budget, test_stall, gcap, err, s);
+  if (q.Cq) return launch_tc<TC_BF16X3, float2>(g, Ck, (const float2 *)q.Cq, 1, q, W2, budget, test_stall, gcap, err, s);
+  return launch_tc<TC_BF16X3, float2>(g, Ck, Ck, 0, q, W2, budget, test_stall, gcap, err, s);
 }
 
 }  // namespace chi0int

@@ -118,27 +118,44 @@ def _eigh_chunk(H: np.ndarray):
     return w, v
 
 
-def eigh_batched(H: np.ndarray, nproc: int = 1, cdtype=np.complex128):
+def eigh_batched(H: np.ndarray, nproc: int = 1, cdtype=np.complex128, pool=None):
     """Eigen-decomposition of a stack of Hermitian matrices [B, n, n].
 
-    Returns (w [B, n] ascending, v [B, n, n] with v[b, :, j] the j-th eigenvector)."""
+    Returns (w [B, n] ascending, v [B, n, n] with v[b, :, j] the j-th eigenvector).
+    ``pool``: a process pool to reuse (else one is started for this call when nproc > 1)."""
     B = H.shape[0]
     if nproc <= 1 or B < 4096:
         w, v = _eigh_chunk(H)
         return w, v.astype(cdtype, copy=False)
     import concurrent.futures as cf
-    import multiprocessing as mp
     chunks = np.array_split(np.arange(B), nproc * 4)
     w = np.empty(H.shape[:2], dtype=np.float64)
     v = np.empty(H.shape, dtype=cdtype)
-    with cf.ProcessPoolExecutor(max_workers=nproc, mp_context=mp.get_context("spawn")) as ex:
+    ex = pool if pool is not None else _spawn_pool(nproc)
+    try:
         futs = {ex.submit(_eigh_chunk, H[c]): c for c in chunks if len(c)}
         for f in cf.as_completed(futs):
             c = futs[f]
             wc, vc = f.result()
             w[c] = wc
             v[c] = vc
+    finally:
+        if pool is None:
+            ex.shutdown()
     return w, v
+
+
+def _eig_span(model, kfrac, idx, n, cdtype):
+    """Eigen-data of one span of k points (fractional k, or grid indices idx of mesh n)."""
+    H = model.hamiltonian(kfrac, grid=None if idx is None else (idx, n))
+    w, v = np.linalg.eigh(H)
+    return w, v.astype(cdtype, copy=False)
+
+
+def _spawn_pool(nproc: int):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    return cf.ProcessPoolExecutor(max_workers=nproc, mp_context=mp.get_context("spawn"))
 
 
 def default_nproc() -> int:
@@ -193,15 +210,29 @@ class TBModel:
 
     def eig(self, kfrac: np.ndarray, nproc: int = 1, cdtype=np.complex128, chunk: int = 0, grid=None):
         B = kfrac.shape[0] if grid is None else grid[0].shape[0]
-        if chunk <= 0:  # k points per worker and batch: ~64 MB of Hamiltonians per worker
+        if chunk <= 0:  # k points per batch: ~64 MB of Hamiltonians
             chunk = max(256, (1 << 22) // (self.norb * self.norb))
         w = np.empty((B, self.norb), dtype=np.float64)
         v = np.empty((B, self.norb, self.norb), dtype=cdtype)
-        for s in range(0, B, chunk * max(1, nproc)):
-            e = min(B, s + chunk * max(1, nproc))
-            H = self.hamiltonian(None if grid is not None else kfrac[s:e],
-                                 grid=None if grid is None else (grid[0][s:e], grid[1]))
-            w[s:e], v[s:e] = eigh_batched(H, nproc=nproc, cdtype=cdtype)
+        spans = [(s, min(B, s + chunk)) for s in range(0, B, chunk)]
+        if nproc <= 1 or len(spans) < 2:
+            for s, e in spans:
+                w[s:e], v[s:e] = _eig_span(self, None if grid is not None else kfrac[s:e],
+                                           None if grid is None else grid[0][s:e],
+                                           None if grid is None else grid[1], cdtype)
+            return w, v
+        # workers build their own Hamiltonians from the k indices (only eigen-data travels
+        # back) and run one LAPACK thread each
+        import concurrent.futures as cf
+        for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(var, "1")
+        with _spawn_pool(nproc) as ex:
+            futs = {ex.submit(_eig_span, self, None if grid is not None else kfrac[s:e],
+                              None if grid is None else grid[0][s:e], None if grid is None else grid[1],
+                              cdtype): (s, e) for s, e in spans}
+            for f in cf.as_completed(futs):
+                s, e = futs[f]
+                w[s:e], v[s:e] = f.result()
         return w, v
 
     def eig_grid(self, n, nproc: int = 1, cdtype=np.complex128):

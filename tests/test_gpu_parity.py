@@ -198,3 +198,51 @@ def test_band_sweep_40_bands_windows(C, O, prec):
     gr, gi = run_dynamic(C, W, prec, omega)
     assert nerr(gr, np.array(ref_r)) < TOL[prec]
     assert nerr(gi, np.array(ref_i)) < TOL[prec]
+
+
+# ------------------------------------------------------------------------ graph mode
+def test_graph_mode_replays_and_recaptures(C):
+    """opts.graph: a call is captured into a CUDA graph and replayed by identical calls; a
+    different call (other q list, dynamic instead of static) is captured anew.  Results are
+    bitwise those of the plain launch sequence."""
+    W = wl.tiny_tb(n=8, norb=5, nq=3, seed=wl.SEED_BASE + 64)
+    ref_s = run_static(C, W, "mixed")
+    omega = np.linspace(0.0, 2.0, 300)  # two frequency passes
+    ref_r, ref_i = run_dynamic(C, W, "mixed", omega)
+    P = C.Plan(W, precision="mixed", graph=True)
+    for _ in range(3):
+        got = P.static().cpu().numpy()
+        assert np.array_equal(got, ref_s)
+    for _ in range(2):
+        gr, gi = P.dynamic(omega)
+        assert np.array_equal(gr.cpu().numpy(), ref_r) and np.array_equal(gi.cpu().numpy(), ref_i)
+    got = P.static().cpu().numpy()  # back to the static call: captured again
+    assert np.array_equal(got, ref_s)
+    k = P.counters()["kernels"]
+    assert k > 0
+    P.close()
+
+
+# ------------------------------------------------------------------------ autotuner
+def test_autotuner_picks_a_shape_and_keeps_results(C, O):
+    """chi0_tune times the weight-kernel grids and the tensor-core corner packings on a call,
+    keeps the fastest, and every later call still matches the oracle."""
+    W = wl.band_sweep(n=8, nb=40, nq=3, nw=12)
+    omega, W.omega = W.omega, None
+    ref = O.chi0(W)
+    P = C.Plan(W, precision="mixed", overlap="bf16x6")
+    r = P.tune()
+    assert r["candidates"] >= 3 and 0 < r["best_ms"] <= r["default_ms"]
+    assert r["static_ctas_per_sm"] >= 1 and r["tc_corners_per_round"] >= 0  # 0: the most that fit
+    got = P.static().cpu().numpy()
+    assert nerr(got[:, None], ref[:, None]) < TOL["mixed"]
+    W.qs = W.qs[:1]
+    ref_r, ref_i = zip(*[O.chi0_q(W, q, omega=omega) for q in W.qs])
+    P2 = C.Plan(W, precision="mixed", overlap="bf16x6")
+    r = P2.tune(omega)
+    assert r["dynamic_ctas_per_sm"] >= 1
+    gr, gi = P2.dynamic(omega)
+    assert nerr(gr.cpu().numpy(), np.array(ref_r)) < TOL["mixed"]
+    assert nerr(gi.cpu().numpy(), np.array(ref_i)) < TOL["mixed"]
+    P.close()
+    P2.close()
