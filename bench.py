@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--cpu-sample-w", type=int, default=16, help="frequencies in the CPU sample (dynamic)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-q", type=int, default=8,
-                    help="q points of the oracle's timed sample (8 q of the Cr-like run: ~10-15 s on 16 cores)")
+    ap.add_argument("--cpu-sample-q", type=int, default=None,
+                    help="q points of the oracle's timed sample (default: static workloads 8 for the "
+                         "cpu_baseline, ~10-15 s on 16 cores, and 2 per --impl reference step; dynamic 1)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-out", default="")
     return ap.parse_args()
@@ -258,6 +259,8 @@ def run_reference(args):
         return 0
     nproc = wl.default_nproc()
     W = make_workload(args, nproc)
+    if args.cpu_sample_q is None:
+        args.cpu_sample_q = 2 if W.omega is None else 1
     cores = len(os.sched_getaffinity(0))
     times = []
     evals = 0
@@ -285,6 +288,8 @@ def run_ours(args):
     nproc = max(1, wl.default_nproc() // max(1, ws))
     # inputs (and the oracle sample) before any CUDA call: the generator uses a spawn pool
     W = make_workload(args, nproc)
+    if args.cpu_sample_q is None:
+        args.cpu_sample_q = 8 if W.omega is None else 1
     cpu = None
     if rank == 0 and not args.no_cpu:
         cores = len(os.sched_getaffinity(0))
