@@ -465,3 +465,47 @@ def test_static_vs_dynamic_at_zero_and_kk(oracle_mod):
     _, im = oracle_mod.chi0_q(W, q, omega=ws)
     kk = (2 / math.pi) * np.sum(im / ws) * dmax / nw
     assert abs(kk - stat) < 2e-3 * stat, (kk, stat)
+
+
+def _carved_volume(oracle_mod, n, kF, q, L=1.0):
+    """Volume of {|k|^2 < kF^2, |k+q|^2 > kF^2} in the cube [-L, L]^3 from the oracle's
+    carving of the linear interpolants on n^3 cubes (6 tetrahedra each)."""
+    h = 2.0 * L / n
+    perm = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tot = 0.0
+    for i0 in range(n):
+        for i1 in range(n):
+            for i2 in range(n):
+                base = np.array([i0, i1, i2]) * h - L
+                for p in perm:
+                    o = np.zeros(3)
+                    cs = [base.copy()]
+                    o[p[0]] += h
+                    cs.append(base + o)
+                    o[p[1]] += h
+                    cs.append(base + o)
+                    cs.append(base + h)
+                    cs = np.array(cs)
+                    a = (cs ** 2).sum(1) - kF ** 2
+                    b = ((cs + q) ** 2).sum(1) - kF ** 2
+                    if a.min() >= 0 or b.max() <= 0:
+                        continue
+                    vol, _, _ = oracle_mod.carve(a, b)
+                    tot += vol.sum() * h ** 3 / 6.0
+    return tot
+
+
+def test_fig1_worked_example_carved_volume(oracle_mod):
+    """Sec. II, Fig. 1: parabolic band eps = |k|^2, q = (0.15, 0, 0), k_F = 0.77.  The doubly
+    carved region is the Fermi ball minus its lens-shaped overlap with the shifted ball
+    (closed form stored in tests/golden/fig1_parabolic_carving.json by make_golden.py).  The
+    oracle's carving of the linear interpolants converges to it at second order."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig1_parabolic_carving.json")))
+    kF, q, exact = g["kF"], np.array(g["q"]), g["carved_volume"]
+    v = {n: _carved_volume(oracle_mod, n, kF, q) for n in (12, 24, 48)}
+    e = {n: v[n] - exact for n in v}
+    assert 3.3 < e[12] / e[24] < 4.8 and 3.3 < e[24] / e[48] < 4.8, e
+    rich = (4.0 * v[48] - v[24]) / 3.0
+    assert abs(rich - exact) < 3e-4 * exact, (rich, exact)
