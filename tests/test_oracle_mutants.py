@@ -1,0 +1,63 @@
+"""Planted mistakes: each test copies the oracle, plants one plausible error in its C source
+(a wrong repeated knot, a sign, a cut fraction, a missing conjugate or factor, a transposed
+band index), builds the copy on the CPU and checks that the pins of test_oracle_pins.py
+reject it.  The real oracle is never modified."""
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+import test_oracle_pins as pins
+
+ORACLE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+
+# (name, original text, planted text, pins expected to fail)
+MUTANTS = [
+    ("repeated_knot", "t[4] = x[j] / s;", "t[4] = x[(j + 1) % 4] / s;",
+     ["test_inv_weight_vs_simplex_quadrature", "test_inv_weight_sum_rule"]),
+    ("pv_sign", "r += ff[j] * (oracle_inv_weight(xm, j) + oracle_inv_weight(xp, j));",
+     "r += ff[j] * (oracle_inv_weight(xm, j) - oracle_inv_weight(xp, j));",
+     ["test_tet_dynamic_integrals_identities"]),
+    ("cut_fraction", "double t = kp / (kp - kq);", "double t = kq / (kq - kp);",
+     ["test_carving_volume_all_cases"]),
+    ("second_cut_key", "return which == 0 ? v->a : -(v->a + v->D);", "return which == 0 ? v->a : -(v->D);",
+     ["test_carving_volume_all_cases"]),
+    ("no_conjugate", "re += x[0] * y[0] + x[1] * y[1];\n    im += x[0] * y[1] - x[1] * y[0];",
+     "re += x[0] * y[0] - x[1] * y[1];\n    im += x[0] * y[1] + x[1] * y[0];",
+     ["test_flat_bands_matrix_element_closed_form"]),
+    ("static_factor", "acc += ff[j] * 2.0 * oracle_inv_weight(d, j);", "acc += ff[j] * oracle_inv_weight(d, j);",
+     ["test_free_electron_lindhard_static", "test_tet_static_integral_vs_qmc"]),
+    ("im_pi", "vs * M_PI * m);", "vs * m);",
+     ["test_free_electron_dynamic_im", "test_tet_dynamic_integrals_identities"]),
+]
+
+
+def _mutant_module(tmp_path, name, old, new):
+    src = open(os.path.join(ORACLE_DIR, "chi0_oracle.c")).read()
+    assert src.count(old) == 1, "planting site not unique: %r" % old
+    d = tmp_path / ("oracle_mut_" + name)
+    d.mkdir()
+    shutil.copy(os.path.join(ORACLE_DIR, "__init__.py"), d / "__init__.py")
+    (d / "chi0_oracle.c").write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("oracle_mut_" + name, str(d / "__init__.py"),
+                                                  submodule_search_locations=[str(d)])
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("name,old,new,checks", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_planted_mistake(tmp_path, name, old, new, checks):
+    mod = _mutant_module(tmp_path, name, old, new)
+    for check in checks:
+        with pytest.raises(AssertionError):
+            getattr(pins, check)(mod)
+
+
+def test_unmodified_copy_passes_the_same_pins(tmp_path):
+    """Control: a copy built the same way without a planted mistake passes every pin used
+    above, so the failures come from the mistakes."""
+    mod = _mutant_module(tmp_path, "control", "t[4] = x[j] / s;", "t[4] = x[j] / s;")
+    for check in sorted({c for m in MUTANTS for c in m[3]}):
+        getattr(pins, check)(mod)
