@@ -519,6 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
 constexpr int kDynThreads = 128;
 constexpr int kDynWarps = kDynThreads / 32;
 constexpr int kNWPass = 256;  // frequencies per dynamic pass
+constexpr int kDynPB = 16;    // final tetrahedra buffered per warp (FP32 dynamic kernel)
 
 template <typename T> struct FarK {
   static constexpr int value = sizeof(T) == 8 ? 64 : 32;  // moments kept per final tetrahedron
@@ -625,7 +626,13 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
   __shared__ int s_c[kDynWarps][32][4], s_cq[kDynWarps][32][4];
   __shared__ T s_vol[kDynWarps][32];
   __shared__ int s_nlo[kDynWarps][32], s_nn[kDynWarps][32], s_pre[kDynWarps][33];
-  __shared__ T s_a[kDynWarps][KM];
+  // FP32: final tetrahedra are buffered (kDynPB per warp) so that their far-field moments are
+  // computed one piece per lane instead of serially by one lane; FP64 evaluates each piece
+  // as it is carved (its moment arrays would not fit the buffer in shared memory)
+  constexpr int PB = FP64 ? 1 : kDynPB;
+  __shared__ T s_am[kDynWarps][PB][KM];
+  __shared__ T s_pe[kDynWarps][PB][4], s_pf[kDynWarps][PB][4], s_pv[kDynWarps][PB][3];
+  __shared__ int s_pk[kDynWarps][PB];
   __shared__ T sR[kDynWarps][kNWPass], sI[kDynWarps][kNWPass];
   __shared__ T cR[kDynWarps][kNWPass], cI[kDynWarps][kNWPass];  // compensation terms
   __shared__ T s_w[kNWPass];
@@ -645,6 +652,78 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
     if (tabs(sum) >= tabs(x)) comp += (sum - t) + x;
     else comp += (x - t) + sum;
     sum = t;
+  };
+  // one final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr) on
+  // every frequency of the pass, with its far-field moments am[0..K)
+  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K) {
+    T d[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
+    const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
+    // far field for both terms (Horner on the moments); near-field frequencies are
+    // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
+    unsigned nearm = 0u, nearp = 0u;
+    for (int iw = lane, itn = 0; iw < nw; iw += 32, ++itn) {
+      const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
+      T re = T(0);
+      const T rp = half / (c + om);
+      if (rp <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, -om, rp);
+      else nearp |= 1u << itn;
+      const T dm = c - om;
+      const T rm = half / (dm < T(0) ? -dm : dm);
+      if (rm <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, om, rm);
+      else nearm |= 1u << itn;
+      if (re != T(0)) kadd(sR[wib][iw], cR[wib][iw], vr * re);
+    }
+    // near field: compact the (frequency, term) pairs of the warp into a list
+    int nlist = 0;
+    const int nit = (nw + 31) >> 5;
+    for (int itn = 0; itn < nit; ++itn) {
+#pragma unroll
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
+        const unsigned bal = __ballot_sync(kFull, mine);
+        if (mine) s_near[wib][nlist + __popc(bal & ((1u << lane) - 1u))] = (short)((itn * 32 + lane) * 2 + sgn);
+        nlist += __popc(bal);
+      }
+      if (nlist > kNearCap - 64) {  // flush a full list
+        __syncwarp();
+        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
+                        cI[wib], tau, nfp64);
+        nlist = 0;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
+                        cI[wib], tau, nfp64);
+    __syncwarp();
+  };
+  // buffered pieces (FP32): moments one piece per lane, then each piece on all frequencies
+  int npb = 0;
+  auto flush = [&]() {
+    __syncwarp();  // lane 0's buffer writes are visible to every lane
+    if (lane < npb) {
+      T d[4], ff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        d[i] = s_pv[wib][lane][1] + s_pe[wib][lane][i];
+        ff[i] = s_pf[wib][lane][i];
+      }
+      s_pk[wib][lane] = far_moments<T, KM>(d, ff, s_am[wib][lane]);
+    }
+    __syncwarp();
+    for (int p = 0; p < npb; ++p) {
+      T ee[4], ff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ee[i] = s_pe[wib][p][i];
+        ff[i] = s_pf[wib][p][i];
+      }
+      eval_piece(ee, ff, s_pv[wib][p][0], s_pv[wib][p][1], s_pv[wib][p][2], s_am[wib][p], s_pk[wib][p]);
+    }
+    __syncwarp();
+    npb = 0;
   };
   for (;;) {
     int batch = 0;
@@ -690,13 +769,13 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
     const int total = __shfl_sync(kFull, pre, 31);
     __syncwarp();
     int l = 0;
-    for (int it = 0; it < total; ++it) {  // warp-uniform
+    auto item = [&](int it) {
       while (s_pre[wib][l + 1] <= it) ++l;
       const int loc = it - s_pre[wib][l];
       const int nn = s_nn[wib][l];
       const int mo = div_small(loc, nn, q.hi - q.lo);
       const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
-      if (q.gamma && m == n) continue;
+      if (q.gamma && m == n) return;
       // band pair: a = e^m_k - eF, D = D0 + e (e_0 = 0).  Mixed path: energies as FP32
       // hi + lo pairs, so that D0 (hi + lo) and the corner offsets e come out to full FP32
       // relative precision whatever the size of a and b
@@ -739,7 +818,7 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
           e[i] = (sb - sa) + ((tb - ta) + ((bl[i] - bl[0]) - (al[i] - al[0])));
         }
       }
-      if (!(amin < T(0) && bmax > T(0))) continue;
+      if (!(amin < T(0) && bmax > T(0))) return;
       const T *W2t = (const T *)W2;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -748,56 +827,39 @@ __global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const 
       carve2_off<T>(a, e, D0h, f, [&](T r, T ee[4], T ff[4]) {
         sort4(ee, ff);
         ++npieces;
-        T d[4];
+        if (!(D0h + ee[3] > T(0))) return;
+        if constexpr (FP64) {
+          T d[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
-        if (!(d[3] > T(0))) return;
-        __syncwarp();
-        int K = 0;
-        if (lane == 0) K = far_moments<T, KM>(d, ff, s_a[wib]);
-        K = __shfl_sync(kFull, K, 0);
-        __syncwarp();
-        const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
-        const T vr = vol * r;
-        // far field for both terms (Horner on the moments); near-field frequencies are
-        // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
-        unsigned nearm = 0u, nearp = 0u;
-        for (int iw = lane, itn = 0; iw < nw; iw += 32, ++itn) {
-          const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
-          T re = T(0);
-          const T rp = half / (c + om);
-          if (rp <= T(Num<T>::kappa_far)) re += far_eval(s_a[wib], K, c, -om, rp);
-          else nearp |= 1u << itn;
-          const T dm = c - om;
-          const T rm = half / (dm < T(0) ? -dm : dm);
-          if (rm <= T(Num<T>::kappa_far)) re += far_eval(s_a[wib], K, c, om, rm);
-          else nearm |= 1u << itn;
-          if (re != T(0)) kadd(sR[wib][iw], cR[wib][iw], vr * re);
-        }
-        // near field: compact the (frequency, term) pairs of the warp into a list
-        int nlist = 0;
-        const int nit = (nw + 31) >> 5;
-        for (int itn = 0; itn < nit; ++itn) {
+          for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
+          __syncwarp();
+          int K = 0;
+          if (lane == 0) K = far_moments<T, KM>(d, ff, s_am[wib][0]);
+          K = __shfl_sync(kFull, K, 0);
+          __syncwarp();
+          eval_piece(ee, ff, vol * r, D0h, D0l, s_am[wib][0], K);
+        } else {
+          if (lane == 0) {  // every lane holds the same piece
 #pragma unroll
-          for (int sgn = 0; sgn < 2; ++sgn) {
-            const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
-            const unsigned bal = __ballot_sync(kFull, mine);
-            if (mine) s_near[wib][nlist + __popc(bal & ((1u << lane) - 1u))] = (short)((itn * 32 + lane) * 2 + sgn);
-            nlist += __popc(bal);
+            for (int i = 0; i < 4; ++i) {
+              s_pe[wib][npb][i] = ee[i];
+              s_pf[wib][npb][i] = ff[i];
+            }
+            s_pv[wib][npb][0] = vol * r;
+            s_pv[wib][npb][1] = D0h;
+            s_pv[wib][npb][2] = D0l;
           }
-          if (nlist > kNearCap - 64) {  // flush a full list
-            __syncwarp();
-            near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
-                            cI[wib], tau, nfp64);
-            nlist = 0;
-            __syncwarp();
-          }
+          ++npb;
         }
-        __syncwarp();
-        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
-                            cI[wib], tau, nfp64);
-        __syncwarp();
       });
+    };
+    for (int it = 0;; ++it) {  // warp-uniform; the pass after the last item flushes the buffer
+      const bool last = it >= total;
+      if (!last) item(it);
+      if constexpr (!FP64) {
+        if (last || npb > PB - 9) flush();  // an item adds at most 9 pieces
+      }
+      if (last) break;
     }
     __syncwarp();
     for (int iw = lane; iw < nw; iw += 32) {
