@@ -58,7 +58,6 @@ __device__ __forceinline__ float d2f_int(double x) {
 }
 
 template <typename T> __device__ __forceinline__ T cvt(double x);
-template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
 template <> __device__ __forceinline__ float cvt<float>(double x) { return d2f_int(x); }
 template <typename T> __device__ __forceinline__ T cvt(float x) { return (T)x; }
 
