@@ -225,7 +225,7 @@ TRAFFIC_PER_PIECE_MIXED = 3.58
 # counters of the four k_dynamic launches of one step on its 32x32x8 mesh, 2 q x 512 w:
 # 1.40 M final tetrahedra x 256 w per launch).
 FLOPS_PER_PIECE_W_DYN = 169.3
-TRAFFIC_PER_PIECE_W_DYN = 0.0139
+TRAFFIC_PER_PIECE_W_DYN = None  # counted (0.0139 B) on the kernel before its piece buffering
 
 
 def run_step(P, W):
