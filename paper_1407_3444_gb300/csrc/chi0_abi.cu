@@ -707,6 +707,7 @@ extern "C" int chi0_tune(chi0_plan_t *p, const chi0_q_t *q, int nq, const double
     p->tc_gcap = best_g;
   }
   p->opts.graph = graph;
+  drop_graph(p);  // a graph captured before tuning holds the old launch shapes
   if (rc) return rc;
   res->static_variant = p->static_variant;
   res->static_threads = static_variant_threads(fp64, p->static_variant);
