@@ -30,6 +30,12 @@ MUTANTS = [
      ["test_free_electron_lindhard_static", "test_tet_static_integral_vs_qmc"]),
     ("im_pi", "vs * M_PI * m);", "vs * m);",
      ["test_free_electron_dynamic_im", "test_tet_dynamic_integrals_identities"]),
+    ("bands_transposed", "const double *y = Ckq + 2 * (((int64_t)ckq * in->norb + o) * nb + n);",
+     "const double *y = Ckq + 2 * (((int64_t)ckq * in->norb + o) * nb + m);",
+     ["test_flat_bands_matrix_element_closed_form"]),
+    ("gamma_dos_dropped", "if (nw == 0 || in->omega[k] == 0.0) re_out[k] += sgn * 2.0 * acc_val(&G);",
+     "if (nw == 0 || in->omega[k] == 0.0) re_out[k] += 0.0 * acc_val(&G);",
+     ["test_free_electron_q0_limit"]),
 ]
 
 
