@@ -347,6 +347,9 @@ def run_ours(args):
     k_static_ms = stage_ms(chi0.CHI0_K_STATIC)
     launches = s1.kernels - s0.kernels
     pieces_timed = s1.pieces - s0.pieces
+    # non-empty work: final tetrahedra times the frequencies each is evaluated on, per second
+    w_eval = 1.0 if W.omega is None else len(W.omega) / max(1, -(-len(W.omega) // chi0.DYNAMIC_MAX_NW))
+    nonzero_rate = whole_job_rate(ws, pieces_timed / args.steps * w_eval, ms)
     static_launches = s1.launches[chi0.CHI0_K_STATIC] - s0.launches[chi0.CHI0_K_STATIC]
     stages = {name: stage_ms(k) for name, k in (("overlap", chi0.CHI0_K_OVERLAP), ("weights", chi0.CHI0_K_STATIC),
                                                  ("dynamic", chi0.CHI0_K_DYNAMIC),
@@ -463,6 +466,7 @@ def run_ours(args):
                 "error": {"mixed_vs_fp64_gpu_max_rel": err_mixed, "vs_oracle": err_oracle},
                 "roofline": roof, "roofline_overlap": ovl, "stage_ms_per_q": stages,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "tuned": tuned,
+                "nonzero": {"value": nonzero_rate, "unit": "(final tetrahedron, w) evaluations/s"},
                 "counters": counters, "clocks": ck, "peaks_source": kind}
         print(json.dumps(line), flush=True)
         if args.profile_out:
