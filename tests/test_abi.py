@@ -119,6 +119,16 @@ def test_plan_validation_before_any_launch(lib):
     with pytest.raises(lib.Chi0Error) as ei:
         lib.chi0_plan(_kgrid(lib, E, 3), None, lib.chi0_band_window_t(0, 3), o5)
     assert ei.value.code == lib.CHI0_EINVAL
+    # graph capture and the stall hook exclude each other
+    o6 = lib.chi0_opts_default()
+    o6.cma = 1
+    o6.precision = lib.CHI0_PREC_MIXED
+    o6.overlap = lib.CHI0_OVL_BF16X6
+    o6.test_stall = 1
+    o6.graph = 1
+    with pytest.raises(lib.Chi0Error) as ei:
+        lib.chi0_plan(_kgrid(lib, E, 3), None, lib.chi0_band_window_t(0, 3), o6)
+    assert ei.value.code == lib.CHI0_EINVAL
 
 
 def test_destroy_null_is_safe(lib):
