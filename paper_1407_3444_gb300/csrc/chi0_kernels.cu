@@ -1,15 +1,21 @@
 // chi0_kernels.cu -- sm_103a kernels of the doubly carved tetrahedron method.
 //
-//  k_overlap  (Eq. 1 matrix elements, tight-binding form of the Sec. III footnote):
-//             W2[c][m][n] = |sum_o conj(C_k[o][m]) C_{k+q}[o][n]|^2 at every k corner.
-//  k_static   one warp per tetrahedron: lanes find the occupied bands m (some corner with
-//             e^m_k < eF) and the empty bands n (some corner with e^n_{k+q} > eF), then
-//             walk the (m, n) rectangle; per pair the two carvings of Sec. II and the
-//             closed-form 2/D integral (Eq. 1 at w = 0).  Per-block FP64 partial sums.
-//  k_dynamic  one warp per tetrahedron, pairs walked by the whole warp, the lanes own the
-//             frequencies: PV 1/(D-w) + 1/(D+w) (Eq. 1) and pi delta(w - D) (Eq. 2).
+//  k_overlap_small / k_overlap  (Eq. 1 matrix elements, tight-binding form of the Sec. III
+//             footnote) on the CUDA cores: W2[c][m][n] = |sum_o conj(C_k[o][m]) C_{k+q}[o][n]|^2
+//             at every k corner (the tensor-core form is in chi0_overlap_tc.cu).
+//  k_bands    E - eF in FP32 (hi, and lo for the dynamic kernel) and the occupied / empty band
+//             bounds of every corner.
+//  k_static   persistent warps take batches of 32 tetrahedra; a batch's (m, n) rectangles
+//             (occupied band m at some corner, empty band n at some corner of k+q) form one
+//             item list, sorted into whole-tetrahedron and cut items and evaluated 32 at a
+//             time: the two carvings of Sec. II and the closed-form 2/D integral (Eq. 1 at
+//             w = 0) by its midpoint series; other pieces are queued for k_static_tab.
+//             Per-batch FP64 partial sums.
+//  k_dynamic  persistent warps, band pairs walked by the whole warp, the lanes own the
+//             frequencies: PV 1/(D-w) + 1/(D+w) (Eq. 1) by far-field moments or the
+//             near-field table, and pi delta(w - D) (Eq. 2) by B-splines.
 //  k_dos      Gamma: the intraband q -> 0 limit, tetrahedron DOS at eF (Sec. III).
-//  k_reduce   deterministic fixed-order sum of the block partials.
+//  k_reduce   deterministic fixed-order sum of the batch partials.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
