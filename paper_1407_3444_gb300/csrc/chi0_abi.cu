@@ -353,6 +353,16 @@ int ensure(chi0_plan_t *p, void **buf, size_t *cap, size_t bytes) {
 }
 
 // Resolves one q descriptor into device pointers (staging host explicit data).
+// the checks of one q descriptor (every q of a call is checked before its first launch)
+int validate_q(chi0_plan_t *p, const chi0_q_t &qd) {
+  const int lo = qd.win.lo < 0 ? p->win.lo : qd.win.lo, hi = qd.win.lo < 0 ? p->win.hi : qd.win.hi;
+  if (lo < p->win.lo || hi > p->win.hi || lo >= hi)
+    return fail(p, CHI0_EINVAL, "q window [%d, %d) outside the plan window [%d, %d)", lo, hi, p->win.lo, p->win.hi);
+  if (qd.e_kq && !p->opts.cma && !qd.c_kq) return fail(p, CHI0_EINVAL, "explicit e_kq needs c_kq without CMA");
+  if (!qd.e_kq && !p->g.periodic) return fail(p, CHI0_EINVAL, "on-grid q shift needs a periodic grid");
+  return CHI0_OK;
+}
+
 int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q) {
   const Grid &g = p->g;
   q.lo = qd.win.lo < 0 ? p->win.lo : qd.win.lo;
@@ -511,6 +521,10 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
   const bool dyn = omega != nullptr;
   if (dyn && (nw <= 0 || !re || !im)) return fail(p, CHI0_EINVAL, "dynamic call needs nw > 0, re and im");
   if (!dyn && !re) return fail(p, CHI0_EINVAL, "chi is NULL");
+  for (int iq = 0; iq < nq; ++iq) {  // validation before any launch
+    const int rc = validate_q(p, qs[iq]);
+    if (rc) return rc;
+  }
   const chi0_opts_t &op = p->opts;
   const int fp64 = op.precision == CHI0_PREC_FP64;
   cudaStream_t s = p->stream;
