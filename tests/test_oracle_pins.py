@@ -509,3 +509,21 @@ def test_fig1_worked_example_carved_volume(oracle_mod):
     assert 3.3 < e[12] / e[24] < 4.8 and 3.3 < e[24] / e[48] < 4.8, e
     rich = (4.0 * v[48] - v[24]) / 3.0
     assert abs(rich - exact) < 3e-4 * exact, (rich, exact)
+
+
+def test_chi_periodic_in_q(oracle_mod):
+    """Orbitals at the cell origin (periodic gauge): H(k + G) = H(k), so chi0(q + G) = chi0(q),
+    with the constant matrix element and with the full |M|^2 (CMA periodicity, Sec. III)."""
+    m = wl.random_model(3, wl.SEED_BASE + 32, spread=4.0)
+    n = 4
+    kf = wl.corner_frac((n, n, n), True)
+    E, C = m.eig(kf)
+    ef = wl.fermi_level(E, 1.5)
+    q = np.array([0.13, -0.21, 0.07])
+    q0 = wl.explicit_q(m, (n, n, n), q)
+    qG = wl.explicit_q(m, (n, n, n), q + np.array([1.0, -1.0, 2.0]))
+    for cma in (True, False):
+        W = wl.Workload("t", (n, n, n), True, 3, 3, E, C, ef, (0, 3), cma, [q0, qG])
+        a = oracle_mod.chi0_q(W, q0)
+        b = oracle_mod.chi0_q(W, qG)
+        assert abs(a - b) < 1e-10 * abs(a), (cma, a, b)
