@@ -192,6 +192,9 @@ typedef struct {
   long long pieces;     /* final tetrahedra evaluated (profile mode)                     */
   long long fp64_evals; /* weight evaluations taken by the FP64 branch (mixed, profile)  */
   long long kernels;    /* kernel launches made by the plan's calls (always counted)     */
+  long long queue_overflow; /* static weights (profile): final tetrahedra that found their
+                               batch's queue of long-series pieces full and were evaluated
+                               in place by the carving warp instead                      */
 } chi0_stats_t;
 
 /* ---------------------------------------------------------------- entry points */
@@ -285,7 +288,7 @@ void chi0_destroy(chi0_plan_t *plan);
  * chi0_plan call when plan == NULL). */
 const char *chi0_last_error(const chi0_plan_t *plan);
 
-/* Library ABI version (major*10000 + minor*100 + patch). */
+/* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow. */
 int chi0_version(void);
 
 #ifdef __cplusplus

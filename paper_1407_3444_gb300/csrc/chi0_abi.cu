@@ -103,7 +103,7 @@ extern "C" void chi0_opts_default(chi0_opts_t *o) {
   o->wait_budget = 0;
 }
 
-extern "C" int chi0_version(void) { return 100; }
+extern "C" int chi0_version(void) { return 101; }
 
 extern "C" const char *chi0_last_error(const chi0_plan_t *p) { return p ? p->err : g_plan_err; }
 
@@ -618,10 +618,11 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
   if (op.profile || !op.outputs_on_device) CK(p, cudaStreamSynchronize(s));
   CK(p, cudaGetLastError());
   if (op.profile) {
-    unsigned long long cnt[2] = {0, 0};
+    unsigned long long cnt[3] = {0, 0, 0};
     CK(p, cudaMemcpy(cnt, p->counters_d, sizeof(cnt), cudaMemcpyDeviceToHost));
     p->stats.pieces += (long long)cnt[0];
     p->stats.fp64_evals += (long long)cnt[1];
+    p->stats.queue_overflow += (long long)cnt[2];
   }
   tm.collect();
   p->stats.calls += 1;

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(NT, MINB)
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = q.hi - q.lo;
   const long long nbatch = (g.ntet + 31) / 32;
-  int nfp64 = 0, npieces = 0;
+  int nfp64 = 0, npieces = 0, nover = 0;
   for (;;) {
     int batch = 0;
     if (lane == 0) batch = atomicAdd(sb.next, 1);
@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(NT, MINB)
         nfp64 += fp;
         tq[(long long)batch * sb.tcap + slot] = pc;
       } else {
+        ++nover;
         acc_q += piece_eval<FP64>(pc, tau, nfp64);
       }
     };
@@ -457,15 +458,18 @@ __global__ void __launch_bounds__(NT, MINB)
     __syncwarp();
   }
   if (counters) {
-    unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64;
+    unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64,
+                       o2 = (unsigned long long)nover;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(kFull, a, o);
       b += __shfl_xor_sync(kFull, b, o);
+      o2 += __shfl_xor_sync(kFull, o2, o);
     }
     if (lane == 0) {
       atomicAdd(&counters[0], a);
       atomicAdd(&counters[1], b);
+      if (o2) atomicAdd(&counters[2], o2);
     }
   }
 }

@@ -65,7 +65,11 @@ int scratch_base(unsigned char **out) {
   return CHI0_OK;
 }
 
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kSat = ~(size_t)0;  // saturated size: larger than any scratch array
+
+// a * b and a + b rounded up to 256, saturating at kSat instead of wrapping around
+size_t mul_sat(size_t a, size_t b) { return (b != 0 && a > kSat / b) ? kSat : a * b; }
+size_t align256(size_t x) { return x > kSat - 255 ? kSat : (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t occ, emp, occq, empq, E32, Eq32, C32, W2, next, counters, tq, tq_n, part, dos, total;
@@ -73,27 +77,30 @@ struct Layout {
 
 Layout layout(const Grid &g, int w, int fp64, int cma, int dtype) {
   Layout L{};
+  // every size saturates instead of wrapping, so a mesh too large for the array can never
+  // come out small here (total == kSat then fails the size check)
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
-    o = align256(o + bytes);
+    o = align256(bytes > kSat - o ? kSat : o + bytes);
     return at;
   };
-  const long long nbatch = static_batches(g.ntet);
-  L.occ = take(sizeof(short) * g.nc);
-  L.emp = take(sizeof(short) * g.nc);
-  L.occq = take(sizeof(short) * g.nc);
-  L.empq = take(sizeof(short) * g.nc);
-  L.E32 = take(fp64 ? 0 : sizeof(float) * g.nc * g.nb);
-  L.Eq32 = take(fp64 ? 0 : sizeof(float) * g.nc * g.nb);
-  L.C32 = take((!fp64 && !cma && dtype == CHI0_C128) ? 8 * (size_t)g.nc * g.norb * g.nb : 0);
-  L.W2 = take(cma ? 0 : (fp64 ? 8 : 4) * (size_t)g.nc * w * w);
+  const size_t nc = (size_t)g.nc, nb = (size_t)g.nb, no = (size_t)g.norb, ww = (size_t)w;
+  const size_t nbatch = (size_t)static_batches(g.ntet);
+  L.occ = take(mul_sat(sizeof(short), nc));
+  L.emp = take(mul_sat(sizeof(short), nc));
+  L.occq = take(mul_sat(sizeof(short), nc));
+  L.empq = take(mul_sat(sizeof(short), nc));
+  L.E32 = take(fp64 ? 0 : mul_sat(mul_sat(sizeof(float), nc), nb));
+  L.Eq32 = take(fp64 ? 0 : mul_sat(mul_sat(sizeof(float), nc), nb));
+  L.C32 = take((!fp64 && !cma && dtype == CHI0_C128) ? mul_sat(mul_sat(mul_sat(8, nc), no), nb) : 0);
+  L.W2 = take(cma ? 0 : mul_sat(mul_sat(mul_sat(fp64 ? 8 : 4, nc), ww), ww));
   L.next = take(sizeof(int));
   L.counters = take(4 * sizeof(unsigned long long));
-  L.tq = take(static_piece_bytes(fp64) * (size_t)nbatch * kNoallocTabCap);
-  L.tq_n = take(sizeof(int) * (size_t)nbatch);
-  L.part = take(sizeof(double) * (size_t)(2 * nbatch));
-  L.dos = take(sizeof(double) * (size_t)static_blocks());
+  L.tq = take(mul_sat(mul_sat(static_piece_bytes(fp64), nbatch), kNoallocTabCap));
+  L.tq_n = take(mul_sat(sizeof(int), nbatch));
+  L.part = take(mul_sat(sizeof(double), mul_sat(2, nbatch)));
+  L.dos = take(mul_sat(sizeof(double), (size_t)static_blocks()));
   L.total = o;
   return L;
 }
@@ -113,6 +120,7 @@ extern "C" int chi0_static_noalloc(const chi0_kgrid_t *kg, chi0_band_window_t wi
   if (!kg->energies) return err(CHI0_EINVAL, "energies is NULL");
   if (!op.cma && (!kg->evecs || kg->norb < 1 || (kg->evec_dtype != CHI0_C64 && kg->evec_dtype != CHI0_C128)))
     return err(CHI0_EINVAL, "eigenvectors (norb, dtype) required without CMA");
+  if (!op.cma && kg->norb > 65536) return err(CHI0_EINVAL, "norb = %d out of range", kg->norb);
   if (win.lo < 0 || win.hi > kg->nbands || win.lo >= win.hi)
     return err(CHI0_EINVAL, "band window [%d, %d) outside [0, %d)", win.lo, win.hi, kg->nbands);
   const int fp64 = op.precision == CHI0_PREC_FP64;

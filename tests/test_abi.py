@@ -42,13 +42,14 @@ def test_struct_layouts_match_header(lib):
     assert ct.sizeof(lib.chi0_kgrid_t) == 4 * 3 + 4 * 3 + 8 + 8 + 4 + 4 + 8
     assert ct.sizeof(lib.chi0_q_t) == 12 + 4 + 8 + 8 + 8 + 4 + 4
     assert ct.sizeof(lib.chi0_opts_t) == 4 * 4 + 8 + 4 * 2 + 8 + 4 + 4 + 8 + 32
+    assert ct.sizeof(lib.chi0_stats_t) == 8 * 8 + 8 * 8 + 5 * 8
 
 
 def test_opts_default(lib):
     o = lib.chi0_opts_default()
     assert o.precision == lib.CHI0_PREC_FP64 and o.sign == lib.CHI0_SIGN_POSITIVE
     assert o.cma == 0 and abs(o.tau - 2.0 ** -20) < 1e-18 and o.inputs_on_device == 0
-    assert lib.chi0_version() >= 100
+    assert lib.chi0_version() >= 101
 
 
 def _kgrid(lib, E, nb, n=(2, 2, 2)):
@@ -141,3 +142,24 @@ def test_null_plan_calls_fail_cleanly(lib):
     with pytest.raises(lib.Chi0Error) as ei:
         lib.chi0_static(None, q, 1, out.ctypes.data)
     assert ei.value.code == lib.CHI0_EINVAL
+
+
+def test_noalloc_rejects_orbital_counts_beyond_the_plan_limit(lib):
+    """chi0_static_noalloc caps norb like chi0_plan (65536), so that no buffer size of its
+    work-array layout can wrap around; the check comes before any CUDA call."""
+    kg = lib.chi0_kgrid_t()
+    kg.n[:] = [4, 4, 4]
+    kg.periodic = 1
+    kg.nbands = 4096
+    kg.norb = 1 << 20
+    kg.energies = 16  # never dereferenced: validation fails first
+    kg.evecs = 16
+    kg.evec_dtype = lib.CHI0_C128
+    o = lib.chi0_opts_default()
+    o.precision = lib.CHI0_PREC_MIXED
+    q = (lib.chi0_q_t * 1)()
+    q[0].win = lib.chi0_band_window_t(-1, -1)
+    with pytest.raises(lib.Chi0Error) as ei:
+        lib.chi0_static_noalloc(kg, lib.chi0_band_window_t(0, 4096), o, q, 1, 16)
+    assert ei.value.code == lib.CHI0_EINVAL
+    assert "norb" in str(ei.value)

@@ -75,6 +75,31 @@ def test_noalloc_matches_chi0_static_on_two_calls(C, prec):
         assert np.max(np.abs(got - ref) / np.abs(ref)) < TOL[prec], (call, got, ref)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_noalloc_queue_overflow_path(C, prec):
+    """A dense Fermi surface (40 bands, coarse mesh): batches queue more long-series final
+    tetrahedra than the queue holds, and the overflow is evaluated in place by the carving
+    warp.  The plan path's profile counter shows overflow with its 64-entry queue, so the
+    16-entry queue of chi0_static_noalloc overflows too; both agree within the tolerance."""
+    import torch
+    W = wl.band_sweep(n=4, nb=40, nq=2, nw=4)
+    W.omega = None
+    W.qs = [wl.QPoint(shift=q.shift) for q in W.qs]  # full 40-band window
+    staged = C.DeviceInputs(W)
+    P = C.Plan(W, precision=prec, device=True, staged=staged, profile=True)
+    ref = P.static().cpu().numpy()
+    assert P.counters()["queue_overflow"] > 0
+    P.close()
+    kg, win, opts, qarr = noalloc_args(C, W, staged, prec)
+    out = torch.empty(len(W.qs), dtype=torch.float64, device="cuda")
+    for call in range(2):
+        out.fill_(float("nan"))
+        C.chi0_static_noalloc(kg, win, opts, qarr, len(W.qs), out.data_ptr())
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < TOL[prec], (call, got, ref)
+
+
 def test_noalloc_rejects_meshes_beyond_its_work_array(C):
     import torch
     E = torch.zeros(16, dtype=torch.float64, device="cuda")  # never read: the size check comes first
