@@ -3,10 +3,11 @@
 // operands and an FP32 accumulator in tensor memory.
 //
 // Per k corner c the overlap O = A^H B, A = C[c][:, lo:hi] (norb x w, complex), B the same
-// block at k+q, is one real GEMM with K = 2 norb:
-//   row m of the A operand:        [Re A[:, m], Im A[:, m]]
-//   row n of the B operand (Re):   [Re B[:, n], Im B[:, n]]       -> Re O[m][n]
-//   row NW + n (Im):               [Im B[:, n], -Re B[:, n]]      -> Im O[m][n]
+// block at k+q, is one real GEMM with K = 2 norb, real and imaginary parts interleaved along K
+// (K index 2o: real part of orbital o, 2o + 1: imaginary part):
+//   row m of the A operand:        (Re A[o][m], Im A[o][m])  for o = 0 .. norb-1
+//   row n of the B operand (Re):   (Re B[o][n], Im B[o][n])          -> Re O[m][n]
+//   row NW + n (Im):               (Im B[o][n], -Re B[o][n])         -> Im O[m][n]
 // so that one accumulator row (one tensor-memory lane) holds both Re O[m][:] and Im O[m][:]
 // and the epilogue forms |O|^2 without exchanging data between lanes.  Several corners share
 // one MMA round: corner g's A rows sit at g*w .. g*w + w - 1 of the M = 128 tile and its B
@@ -17,15 +18,23 @@
 // truncation, so every MMA accumulated into one place moves the result toward zero by a
 // fraction of an ulp: measured on chi0, 6e-8 relative per MMA (3.2e-7 with 6 MMAs per
 // element, 1.8e-6 with 30), a bias that the sum over k does not average away.  The K steps
-// are therefore spread round-robin over NACC accumulators (tensor-memory column blocks of
-// N), each accumulator takes its smallest products first and the leading piece product last,
-// and the epilogue adds the NACC partial results on the CUDA cores (round to nearest).  With
-// NACC equal to the number of K steps each accumulator sees one leading-order MMA.
+// are therefore spread over NACC accumulators (tensor-memory column blocks of N: round-robin
+// when all of K is staged at once, one contiguous chunk each otherwise), each accumulator
+// takes its smallest products first and the leading piece product last, and the epilogue
+// adds the NACC partial results on the CUDA cores (round to nearest).  With NACC equal to
+// the number of K steps each accumulator sees one leading-order MMA.
 //
 // Precision forms (FP32 accumulation in all):
 //   TF32    one product of round-to-nearest TF32 operands
 //   BF16X3  x = p0 + p1 with p0 = bf16(x), p1 = bf16(x - p0); products p0 p0 + p0 p1 + p1 p0
 //   BF16X6  x = p0 + p1 + p2 (p2 = bf16(x - p0 - p1)); the six products pa pb with a + b <= 2
+//
+// K chunks.  When the whole K extent of every piece does not fit in shared memory (the
+// three-piece split at 80 orbitals: 3 (128 + 160) 320 bytes = 276 KB), K is cut into chunks of
+// kc K steps, staged into two buffers in turn: the threads convert chunk j + 1 while the
+// tensor core multiplies chunk j.  Each chunk goes to its own accumulator (chunks are
+// contiguous runs of K steps), smallest products first, so that the truncation bias stays
+// that of kc leading-order MMAs per accumulator.
 //
 // Operands are staged by the CTA's threads (conversion to TF32/BF16 and the real form above)
 // into the K-major, non-swizzled tcgen05 layout: core matrices of 8 rows x 16 bytes stored as
@@ -52,6 +61,7 @@ constexpr int kTcOneSmem = 116 * 1024; // one CTA per SM when it takes all 512 c
 
 struct TcShape {
   int w, NW, G, N, Kpad, Kbytes, ES, P, nks, NACC, ncols;
+  int kc, nch, chunked;  // K steps per staged chunk, chunks per round, double-buffered chunks
   size_t smem;
 };
 
@@ -79,10 +89,23 @@ __host__ __device__ inline TcShape tc_shape(int w, int norb, int mode, int gcap)
   s.NACC = mode == TC_TF32 ? 1 : (s.N > 0 ? kTcCols / s.N : 1);
   if (s.NACC > s.nks) s.NACC = s.nks;
   if (s.NACC < 1) s.NACC = 1;
+  s.kc = s.nks;
+  s.nch = 1;
+  s.chunked = 0;
+  s.smem = (size_t)s.P * (kTcM + s.N) * s.Kbytes + 64;
+  if (s.G >= 1 && s.smem > kTcSmemMax) {
+    // two chunk buffers; one accumulator per chunk where the tensor memory allows
+    s.chunked = 1;
+    s.kc = (s.nks + s.NACC - 1) / s.NACC;
+    while (s.kc > 1 && 2 * (size_t)s.P * (kTcM + s.N) * s.kc * 32 + 64 > kTcSmemMax) --s.kc;
+    s.nch = (s.nks + s.kc - 1) / s.kc;
+    if (s.NACC > s.nch) s.NACC = s.nch;
+    s.smem = 2 * (size_t)s.P * (kTcM + s.N) * s.kc * 32 + 64;
+    if (s.smem > kTcSmemMax) s.G = 0;  // even one K step per chunk does not fit
+  }
   int nc = 32;
   while (nc < s.NACC * s.N) nc <<= 1;
   s.ncols = nc;
-  s.smem = (size_t)s.P * (kTcM + s.N) * s.Kbytes + 64;
   return s;
 }
 
@@ -172,23 +195,91 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
   }
 }
 
+// Stages orbitals [o0, o1) of the round's corners c0 .. c0 + G - 1 into one operand buffer
+// (P pieces of A, then P pieces of B; KB 16-byte columns per row): element (g, o, band) goes
+// to A row g*w + m and B rows g*2NW + n, g*2NW + NW + n at K columns 2(o - o0) and 2(o - o0) + 1.
+// kUnroll elements per thread and pass: all their loads are issued before the first store.
+template <int MODE, typename CTq>
+__device__ __forceinline__ void stage_orbitals(const Grid &g, const float2 *__restrict__ C,
+                                               const CTq *__restrict__ Cb, int explicit_q, const Q &q,
+                                               const TcShape &sh, long long c0, int o0, int o1,
+                                               unsigned char *sA, unsigned char *sB, size_t a_piece,
+                                               size_t b_piece, int KB) {
+  const int w = sh.w, NW = sh.NW, no = g.norb, nob = o1 - o0;
+  const int per = nob * w, tot = sh.G * per;
+  constexpr int kUnroll = 4;
+  for (int i0 = threadIdx.x; i0 < tot; i0 += kUnroll * kTcThreads) {
+    float2 xv[kUnroll];
+    CTq yv[kUnroll];
+    int ra[kUnroll], rb[kUnroll], kk[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kTcThreads;
+      const int gg = i / per, rem = i - gg * per;
+      const long long c = c0 + gg;
+      ra[u] = -1;
+      if (i >= tot || c >= g.nc) continue;
+      const int ol = rem / w, mm = rem - ol * w;
+      const int o = o0 + ol;
+      const long long ck = explicit_q ? c : shift_corner(g, c, q.shift);
+      xv[u] = C[(c * no + o) * g.nb + q.lo + mm];
+      yv[u] = Cb[(ck * no + o) * g.nb + q.lo + mm];
+      ra[u] = gg * w + mm;
+      rb[u] = gg * 2 * NW + mm;
+      kk[u] = 2 * ol;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (ra[u] < 0) continue;
+      const float yr = (float)yv[u].x, yi = (float)yv[u].y;
+      const int k = kk[u];
+      put<MODE>(sA, a_piece, ra[u], k, KB, xv[u].x);
+      put<MODE>(sA, a_piece, ra[u], k + 1, KB, xv[u].y);
+      put<MODE>(sB, b_piece, rb[u], k, KB, yr);
+      put<MODE>(sB, b_piece, rb[u], k + 1, KB, yi);
+      put<MODE>(sB, b_piece, rb[u] + NW, k, KB, yi);
+      put<MODE>(sB, b_piece, rb[u] + NW, k + 1, KB, -yr);
+    }
+  }
+}
+
+// Zeroes K columns [k0, k1) of the rows a round uses (a chunk buffer that held a longer chunk
+// before: its K padding must read as zero).
+template <int MODE>
+__device__ __forceinline__ void zero_columns(const TcShape &sh, int k0, int k1, unsigned char *sA,
+                                             unsigned char *sB, size_t a_piece, size_t b_piece, int KB) {
+  const int na = sh.G * sh.w, nbr = sh.N, nk = k1 - k0;
+  const int tot = (na + nbr) * nk;
+  for (int i = threadIdx.x; i < tot; i += kTcThreads) {
+    const int r = i / nk, k = k0 + (i - r * nk);
+    if (r < na) put<MODE>(sA, a_piece, r, k, KB, 0.0f);
+    else put<MODE>(sB, b_piece, r - na, k, KB, 0.0f);
+  }
+}
+
 template <int MODE, typename CTq>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_overlap_tc(Grid g, const float2 *__restrict__ C, const CTq *__restrict__ Cb, int explicit_q, Q q,
                  float *__restrict__ W2, long long budget, int test_stall, int gcap, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const TcShape sh = tc_shape(q.hi - q.lo, g.norb, MODE, gcap);
-  const int w = sh.w, NW = sh.NW, G = sh.G, KB = sh.Kbytes / 16, no = g.norb;
-  const size_t a_piece = (size_t)kTcM * sh.Kbytes, b_piece = (size_t)sh.N * sh.Kbytes;
-  unsigned char *sA = smem;
-  unsigned char *sB = smem + sh.P * a_piece;
-  unsigned char *tail = sB + sh.P * b_piece;
+  const int w = sh.w, NW = sh.NW, G = sh.G;
+  // operand buffers: one holding all of K, or two holding one chunk of kc K steps each
+  const int cbytes = sh.chunked ? sh.kc * 32 : sh.Kbytes;  // K bytes per row of a buffer
+  const int KB = cbytes / 16;
+  const size_t a_piece = (size_t)kTcM * cbytes, b_piece = (size_t)sh.N * cbytes;
+  const size_t buf_bytes = sh.P * (a_piece + b_piece);
+  const int nbuf = sh.chunked ? 2 : 1;
+  unsigned char *tail = smem + nbuf * buf_bytes;
   uint64_t *bar = (uint64_t *)tail;
   uint32_t *tslot = (uint32_t *)(tail + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kOrbStep = MODE == TC_TF32 ? 4 : 8;  // orbitals per K step (32 bytes of K)
+  const int ostep = kOrbStep * sh.kc;                 // orbitals per chunk
 
   // operand memory starts at zero: padding rows and K columns are never written again
-  const size_t nz = (sh.P * (a_piece + b_piece)) / 16;
+  // (except a chunk buffer's K padding, cleared where a longer chunk used the buffer before)
+  const size_t nz = (nbuf * buf_bytes) / 16;
   for (size_t i = tid; i < nz; i += blockDim.x) ((uint4 *)smem)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
@@ -208,74 +299,68 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long nround = (g.nc + G - 1) / G;
   uint32_t parity = 0;
   bool ok = true;
-  for (long long rd = blockIdx.x; rd < nround && ok; rd += gridDim.x) {
-    const long long c0 = rd * G;
-    // stage the round's corners: element (g, o, band) -> A row g*w + m, B rows g*2NW + n, + NW.
-    // kUnroll elements per thread and pass: all their loads are issued before the first store
-    const int per = no * w, tot = G * per;
-    constexpr int kUnroll = 4;
-    for (int i0 = tid; i0 < tot; i0 += kUnroll * kTcThreads) {
-      float2 xv[kUnroll];
-      CTq yv[kUnroll];
-      int ra[kUnroll], rb[kUnroll], oo[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * kTcThreads;
-        const int gg = i / per, rem = i - gg * per;
-        const long long c = c0 + gg;
-        ra[u] = -1;
-        if (i >= tot || c >= g.nc) continue;
-        const int o = rem / w, mm = rem - o * w;
-        const long long ck = explicit_q ? c : shift_corner(g, c, q.shift);
-        xv[u] = C[(c * no + o) * g.nb + q.lo + mm];
-        yv[u] = Cb[(ck * no + o) * g.nb + q.lo + mm];
-        ra[u] = gg * w + mm;
-        rb[u] = gg * 2 * NW + mm;
-        oo[u] = o;
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        if (ra[u] < 0) continue;
-        const float yr = (float)yv[u].x, yi = (float)yv[u].y;
-        const int o = oo[u];
-        put<MODE>(sA, a_piece, ra[u], o, KB, xv[u].x);
-        put<MODE>(sA, a_piece, ra[u], no + o, KB, xv[u].y);
-        put<MODE>(sB, b_piece, rb[u], o, KB, yr);
-        put<MODE>(sB, b_piece, rb[u], no + o, KB, yi);
-        put<MODE>(sB, b_piece, rb[u] + NW, o, KB, yi);
-        put<MODE>(sB, b_piece, rb[u] + NW, no + o, KB, -yr);
-      }
+  // stages chunk j of the round starting at corner c0 into buffer j % nbuf
+  auto stage = [&](long long c0, int j) {
+    unsigned char *sA = smem + (j % nbuf) * buf_bytes;
+    unsigned char *sB = sA + sh.P * a_piece;
+    const int o0 = j * ostep, o1 = min(g.norb, o0 + ostep);
+    stage_orbitals<MODE, CTq>(g, C, Cb, explicit_q, q, sh, c0, o0, o1, sA, sB, a_piece, b_piece, KB);
+    // the last chunk of three or more may sit in a buffer whose K padding (inside its last K
+    // step) an earlier, longer chunk filled
+    if (sh.chunked && sh.nch >= 3 && j == sh.nch - 1) {
+      const int kstep = 32 / sh.ES, kused = 2 * (o1 - o0);
+      const int kpad = (kused + kstep - 1) / kstep * kstep;
+      if (kused < kpad) zero_columns<MODE>(sh, kused, kpad, sA, sB, a_piece, b_piece, KB);
     }
     // generic-proxy stores must be visible to the tensor core's (async-proxy) reads
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  };
+  // one thread issues chunk j's MMAs and commits them to the mbarrier
+  auto issue = [&](int j) {
+    if (tid != 0 || test_stall) return;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned char *sA = smem + (j % nbuf) * buf_bytes;
+    const unsigned char *sB = sA + sh.P * a_piece;
+    const int s0 = j * sh.kc, s1 = min(sh.nks, s0 + sh.kc);  // global K steps of the chunk
+    for (int ia = 0; ia < sh.NACC; ++ia) {
+      // unchunked: K step s goes to accumulator s % NACC; chunked: chunk j to j * NACC / nch
+      if (sh.chunked && ia != j * sh.NACC / sh.nch) continue;
+      // the first MMA into an accumulator in this round overwrites it
+      uint32_t acc = (sh.chunked && j > 0 && (j - 1) * sh.NACC / sh.nch == ia) ? 1u : 0u;
+      // products of pieces a, b with a + b = lvl < P, smallest level first
+      for (int lvl = sh.P - 1; lvl >= 0; --lvl)
+        for (int pa = 0; pa <= lvl; ++pa)
+          for (int s = s0; s < s1; ++s) {
+            if (!sh.chunked && s % sh.NACC != ia) continue;
+            const uint32_t kb = (uint32_t)(s - s0) * 256u;  // 32 bytes of K = 2 core-matrix columns
+            const uint64_t da = sdesc(smem_u32(sA + pa * a_piece) + kb, 128, KB * 128);
+            const uint64_t db = sdesc(smem_u32(sB + (lvl - pa) * b_piece) + kb, 128, KB * 128);
+            mma(tmem + (uint32_t)(ia * sh.N), da, db, id, acc, MODE);
+            acc = 1;
+          }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+  };
+  for (long long rd = blockIdx.x; rd < nround && ok; rd += gridDim.x) {
+    const long long c0 = rd * G;
+    stage(c0, 0);
     __syncthreads();
-    if (tid == 0 && !test_stall) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int ia = 0; ia < sh.NACC; ++ia) {
-        uint32_t acc = 0;
-        // products of pieces a, b with a + b = lvl < P, smallest level first
-        for (int lvl = sh.P - 1; lvl >= 0; --lvl)
-          for (int pa = 0; pa <= lvl; ++pa)
-            for (int s = ia; s < sh.nks; s += sh.NACC) {
-              const uint64_t da = sdesc(smem_u32(sA + pa * a_piece) + s * 256, 128, KB * 128);
-              const uint64_t db = sdesc(smem_u32(sB + (lvl - pa) * b_piece) + s * 256, 128, KB * 128);
-              mma(tmem + (uint32_t)(ia * sh.N), da, db, id, acc, MODE);
-              acc = 1;
-            }
+    for (int j = 0; j < sh.nch; ++j) {
+      issue(j);
+      if (j + 1 < sh.nch) stage(c0, j + 1);  // the other buffer: chunk j - 1's MMAs are done
+      // test_stall: nothing arrives, so the bounded wait below runs out (error path test).  The
+      // CTA agrees on the outcome before any warp-wide tensor-memory load or buffer reuse.
+      const int got = mbar_wait(smem_u32(bar), parity, budget) ? 1 : 0;
+      if (!__syncthreads_and(got)) {
+        ok = false;
+        if (tid == 0) atomicExch(err, 1);
+        break;
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(bar))
-                   : "memory");
+      parity ^= 1u;
     }
-    // test_stall: nothing arrives, so the bounded wait below runs out (error path test).  The
-    // CTA agrees on the outcome before any warp-wide tensor-memory load.
-    const int got = mbar_wait(smem_u32(bar), parity, budget) ? 1 : 0;
-    if (!__syncthreads_and(got)) {
-      ok = false;
-      if (tid == 0) atomicExch(err, 1);
-      break;
-    }
-    parity ^= 1u;
+    if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // epilogue: lane r = gg*w + m of the tile holds Re O (columns gg*2NW + n) and Im O (+ NW);
     // warps i and i + 4 share lane quarter i%4 and split the 8-column chunks between them
@@ -311,7 +396,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   if (!ok) {
     // the MMAs this CTA issued (if any) may still be running: wait for them once more,
-    // bounded, before the tensor memory is released
+    // bounded, before the tensor memory is released.  (The error-path test issues no MMA, so
+    // there the second wait runs out as well and nothing is in flight.)
     mbar_wait(smem_u32(bar), parity, budget);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
