@@ -195,6 +195,9 @@ typedef struct {
   long long queue_overflow; /* static weights (profile): final tetrahedra that found their
                                batch's queue of long-series pieces full and were evaluated
                                in place by the carving warp instead                      */
+  long long box_pieces;     /* dynamic weights (profile): final tetrahedra whose principal-
+                               value terms were gathered into a box of D (far frequencies
+                               by the box's moments) instead of evaluated per frequency    */
 } chi0_stats_t;
 
 /* ---------------------------------------------------------------- entry points */
@@ -288,7 +291,8 @@ void chi0_destroy(chi0_plan_t *plan);
  * chi0_plan call when plan == NULL). */
 const char *chi0_last_error(const chi0_plan_t *plan);
 
-/* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow. */
+/* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow
+ * and chi0_stats_t.box_pieces. */
 int chi0_version(void);
 
 #ifdef __cplusplus

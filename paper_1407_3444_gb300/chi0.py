@@ -72,7 +72,7 @@ class chi0_opts_t(ct.Structure):
 class chi0_stats_t(ct.Structure):
     _fields_ = [("time_ms", ct.c_double * CHI0_K_COUNT), ("launches", ct.c_longlong * CHI0_K_COUNT),
                 ("calls", ct.c_longlong), ("pieces", ct.c_longlong), ("fp64_evals", ct.c_longlong),
-                ("kernels", ct.c_longlong), ("queue_overflow", ct.c_longlong)]
+                ("kernels", ct.c_longlong), ("queue_overflow", ct.c_longlong), ("box_pieces", ct.c_longlong)]
 
 
 class chi0_tune_t(ct.Structure):
@@ -409,7 +409,7 @@ class Plan:
     def counters(self):
         s = self.stats()
         return {"pieces": int(s.pieces), "fp64_evals": int(s.fp64_evals), "kernels": int(s.kernels),
-                "queue_overflow": int(s.queue_overflow),
+                "queue_overflow": int(s.queue_overflow), "box_pieces": int(s.box_pieces),
                 "static_launches": int(s.launches[CHI0_K_STATIC]),
                 "dynamic_launches": int(s.launches[CHI0_K_DYNAMIC])}
 

@@ -47,6 +47,10 @@ struct chi0_plan {
   cudaGraphExec_t gexec = nullptr;
   std::vector<unsigned char> gkey;
   long long gkernels = 0;
+  void *box_tab_d = nullptr;                  // dynamic weights: box table of the pass,
+  double *box_part_d = nullptr;               // per-warp box moments, their totals and the
+  double *box_tot_d = nullptr;                // boxes' share of Re per frequency
+  double *far_d = nullptr;
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
   int static_grid = 0, dynamic_grid = 0;  // persistent CTAs of the weight kernels
@@ -140,6 +144,10 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->err_d);
   cudaFree(p->tq_d);
   cudaFree(p->tq_n_d);
+  cudaFree(p->box_tab_d);
+  cudaFree(p->box_part_d);
+  cudaFree(p->box_tot_d);
+  cudaFree(p->far_d);
 }
 
 extern "C" void chi0_destroy(chi0_plan_t *p) {
@@ -282,7 +290,17 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
   g.fN2 = make_fastdiv((unsigned)g.N[2]);
   if (g.ntet >= (1LL << 31)) return fail(p, CHI0_EINVAL, "more than 2^31 tetrahedra");
   p->static_grid = static_persistent_blocks(op.precision == CHI0_PREC_FP64);
+  CK(p, dynamic_prepare());
   p->dynamic_grid = dynamic_persistent_blocks(op.precision == CHI0_PREC_FP64);
+  {
+    // dynamic weights: box moments of every warp of the largest grid the autotuner may pick
+    const int fp64 = op.precision == CHI0_PREC_FP64;
+    const size_t warps = (size_t)dynamic_max_ctas_per_sm(fp64) * device_sms() * dynamic_warps_per_cta(fp64);
+    CK(p, cudaMalloc(&p->box_tab_d, dynamic_box_tab_bytes()));
+    CK(p, cudaMalloc(&p->box_part_d, sizeof(double) * warps * dynamic_box_slots(fp64)));
+    CK(p, cudaMalloc(&p->box_tot_d, sizeof(double) * dynamic_box_slots(fp64)));
+    CK(p, cudaMalloc(&p->far_d, sizeof(double) * dynamic_max_nw()));
+  }
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, p->stream));
   CK(p, cudaStreamSynchronize(p->stream));
   memset(&p->stats, 0, sizeof(p->stats));
@@ -468,15 +486,15 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
       const int maxw = dynamic_max_nw();
       for (int w0 = 0; w0 < nw; w0 += maxw) {
         const int nwc = nw - w0 < maxw ? nw - w0 : maxw;
-        DynBufs db{p->partR, p->partI, p->next_d};
+        DynBufs db{p->partR, p->partI, p->box_tab_d, p->box_part_d, p->box_tot_d, p->far_d};
         tm.start(CHI0_K_DYNAMIC);
         CK(p, launch_dynamic(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
                              om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s, Eklo, Ekqlo));
-        p->stats.kernels += 1;
+        p->stats.kernels += 4;  // box table, weights, box sums, box evaluation
         tm.stop();
         tm.start(CHI0_K_REDUCE);
         CK(p, launch_reduce(p->partR, nb, nwc, scale, q.gamma ? p->dos_d : nullptr, ndos, om_d + w0,
-                            outR + (size_t)iq * nw + w0, s));
+                            outR + (size_t)iq * nw + w0, s, p->far_d));
         CK(p, launch_reduce(p->partI, nb, nwc, scale, nullptr, 0, nullptr, outI + (size_t)iq * nw + w0, s));
         p->stats.kernels += 2;
         tm.stop();
@@ -618,11 +636,12 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
   if (op.profile || !op.outputs_on_device) CK(p, cudaStreamSynchronize(s));
   CK(p, cudaGetLastError());
   if (op.profile) {
-    unsigned long long cnt[3] = {0, 0, 0};
+    unsigned long long cnt[4] = {0, 0, 0, 0};
     CK(p, cudaMemcpy(cnt, p->counters_d, sizeof(cnt), cudaMemcpyDeviceToHost));
     p->stats.pieces += (long long)cnt[0];
     p->stats.fp64_evals += (long long)cnt[1];
     p->stats.queue_overflow += (long long)cnt[2];
+    p->stats.box_pieces += (long long)cnt[3];
   }
   tm.collect();
   p->stats.calls += 1;

@@ -1,0 +1,676 @@
+// chi0_dynamic.cu -- frequency-resolved weights of the doubly carved tetrahedron method:
+// Re chi0 as the principal value of Eq. 1, Im chi0 from the delta function of Eq. 2, odd in w
+// (Eq. 3), on every final tetrahedron of the two carvings of Sec. II, for one pass of up to
+// 256 frequencies.
+//
+// Per final tetrahedron S (knots d_j of D, values f_j of |M|^2, weight v = volume fraction):
+//   Re(u) += v sum_j f_j (1/V) int_S lambda_j [1/(D - u) + 1/(D + u)],   u = |w|
+//   Im(w) += sign(w) pi v sum_j f_j (1/V) int_S lambda_j delta(u - D)
+// The delta term is nonzero only for u inside (d_0, d_3) and is always evaluated piece by
+// piece.  The principal-value terms are smooth in u away from the knots, so for frequencies
+// far from a piece they are gathered per box of D instead of per (piece, frequency):
+//
+//   box b: centre C_b, radius R_b; every piece assigned to it has |d_j - C_b| <= R_b, and adds
+//     its moments  M_k += v sum_j f_j (1/V) int_S lambda_j eps^k,  eps = (D - C_b)/R_b,
+//     = v 6 k!/(k+4)! sum_j f_j h_k(e_1..e_4, e_j)  (e = (d - C_b)/R_b; Dirichlet moments of
+//     the simplex, h_k the complete homogeneous symmetric polynomials);
+//   1/(D -+ u) = 1/(C_b -+ u) sum_k (-z)^k eps^k,  z = R_b/(C_b -+ u),  |z| <= 1/2 where the
+//     box stands in for its pieces, so the box's share of Re(u) is sum_k M_k (-z)^k/(C_b -+ u),
+//     evaluated once per (box, frequency) in FP64 after the moments of all warps are summed.
+//
+// Boxes (rebuilt each pass from u_max = max |w| of the pass):
+//   fine boxes, levels l = 0..3 of width w_l = (u_max/32) 2^l: centres (j + 1/2) w_l, radius
+//     w_l; a piece of half-width s <= w_l/2 whose centre lies in [j w_l, (j+1) w_l) fits.  For a
+//     frequency with |C_b - u| < 2 R_b (the - term) or C_b + u < 2 R_b (the + term) the box does
+//     not stand in: its pieces evaluate that term themselves (own far-field series about their
+//     midpoint, or the divided-difference table near their knots);
+//   geometric boxes past u_max: x = c - u_max in [x_b, 1.25 x_b), x_0 = 5 u_max/32, centre
+//     u_max + 1.125 x_b, radius x_b/4, pieces with s <= x_b/8; every frequency of the pass is
+//     far (|z| <= 2/9), so their pieces evaluate nothing per frequency;
+//   pieces wider than any box, or past the last one, are evaluated at every frequency.
+// Every (piece, frequency, term) is taken exactly once, either by the piece or by its box;
+// the predicate that decides is computed in the kernels' precision from the same table.
+//
+// The moments of a warp's pieces go to per-warp sums in shared memory (one lane per moment
+// index, no atomics), added after every batch into per-warp FP64 partials in global memory.
+// Batches are assigned to warps statically (batch = warp + k * warps), and every sum runs in
+// a fixed order, so results are bitwise reproducible for a given launch shape.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "chi0_grid.cuh"
+#include "chi0_internal.h"
+#include "chi0_math.cuh"
+
+using namespace chi0dev;
+
+namespace chi0int {
+namespace {
+
+using grid::div_small;
+using grid::kFull;
+using grid::tet_corners;
+
+constexpr int kNWPass = 256;   // frequencies per dynamic pass
+constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed per warp
+
+template <bool FP64> struct DynShape {
+  static constexpr int threads = FP64 ? 64 : 128;
+  static constexpr int warps = threads / 32;
+  static constexpr int PB = FP64 ? 8 : 16;   // final tetrahedra buffered per warp
+  static constexpr int KM = FP64 ? 64 : 32;  // own far-field moments kept per buffered piece
+  static constexpr int KF = FP64 ? 40 : 24;  // moments of a fine box   (truncation 2^-KF)
+  static constexpr int KG = FP64 ? 22 : 12;  // moments of a geometric box ((2/9)^KG)
+};
+
+// box geometry
+constexpr int kBoxL = 4;      // fine levels
+constexpr int kBoxJ0 = 32;    // finest boxes across [0, u_max]
+constexpr int kBoxExtra = 6;  // fine boxes per level past u_max
+constexpr int kBoxG = 40;     // geometric boxes (x_0 1.25^40 = 7500 x_0)
+constexpr int kMinBoxNw = 8;  // fewer frequencies: every piece evaluates all of them
+__host__ __device__ constexpr int box_J(int l) { return (kBoxJ0 >> l) + kBoxExtra; }
+constexpr int kBoxFine = box_J(0) + box_J(1) + box_J(2) + box_J(3);
+constexpr int kBoxes = kBoxFine + kBoxG;
+template <bool FP64> __host__ __device__ constexpr int box_slots() {
+  return kBoxFine * DynShape<FP64>::KF + kBoxG * DynShape<FP64>::KG;
+}
+template <bool FP64> __host__ __device__ constexpr int slot_base(int b) {
+  return b < kBoxFine ? b * DynShape<FP64>::KF
+                      : kBoxFine * DynShape<FP64>::KF + (b - kBoxFine) * DynShape<FP64>::KG;
+}
+
+// the pass's boxes in the kernels' precision (written by k_box_setup, read by both kernels)
+template <typename T> struct BoxTab {
+  T C[kBoxes], R[kBoxes];  // centre and radius
+  T lowG[kBoxG + 1];       // lower edges x_b of the geometric boxes (x = c - u_max)
+  T W0, x0, umax;
+  int on;
+};
+
+template <typename T> __device__ __forceinline__ void kadd_t(T &sum, T &comp, T x) {
+  const T t = sum + x;
+  if (tabs(sum) >= tabs(x)) comp += (sum - t) + x;
+  else comp += (x - t) + sum;
+  sum = t;
+}
+
+// one block: u_max of the pass and the box table
+template <typename T>
+__global__ void __launch_bounds__(256) k_box_setup(const double *__restrict__ omega, int nw, BoxTab<T> *tab) {
+  __shared__ double red[8];
+  double u = 0.0;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) u = fmax(u, fabs(omega[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(kFull, u, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = u;
+  __syncthreads();
+  double umax = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) umax = fmax(umax, red[i]);
+  const T W0 = (T)(umax / kBoxJ0), um = (T)umax, x0 = W0 * T(5);
+  const int on = (nw >= kMinBoxNw && umax > 1e-30 && umax < 1e30 && W0 > T(0)) ? 1 : 0;
+  if (threadIdx.x == 0) {
+    tab->W0 = W0;
+    tab->x0 = x0;
+    tab->umax = um;
+    tab->on = on;
+    double lo = (double)x0;
+    for (int b = 0; b <= kBoxG; ++b) {
+      tab->lowG[b] = (T)lo;
+      lo *= 1.25;
+    }
+  }
+  __syncthreads();
+  const int b = threadIdx.x;
+  if (b < kBoxFine) {
+    int l = 0, j = b;
+    while (j >= box_J(l)) {
+      j -= box_J(l);
+      ++l;
+    }
+    const T w = W0 * (T)(1 << l);
+    tab->C[b] = ((T)j + T(0.5)) * w;
+    tab->R[b] = w;
+  } else if (b < kBoxes) {
+    const T xb = tab->lowG[b - kBoxFine];
+    tab->C[b] = um + xb * T(1.125);
+    tab->R[b] = xb * T(0.25);
+  }
+}
+
+// box of a final tetrahedron with midpoint c and half-width s (-1: none, evaluate directly)
+template <typename T> __device__ __forceinline__ int box_of(T c, T s, const BoxTab<T> &tb) {
+  if (!tb.on) return -1;
+  const T x = c - tb.umax;
+  if (x >= tb.x0) {
+    int b = (int)(__log2f((float)(x / tb.x0)) * 3.1062837f);  // log base 1.25
+    b = b < 0 ? 0 : (b > kBoxG - 1 ? kBoxG - 1 : b);
+    while (b > 0 && x < tb.lowG[b]) --b;
+    while (b < kBoxG - 1 && x >= tb.lowG[b + 1]) ++b;
+    if (x >= tb.lowG[b] && x < tb.lowG[b + 1] && s <= T(0.125) * tb.lowG[b]) return kBoxFine + b;
+  }
+  T w = tb.W0;
+  int off = 0;
+#pragma unroll 1
+  for (int l = 0; l < kBoxL; ++l) {
+    if (s <= T(0.5) * w) {
+      const T jf = floor(c / w);
+      return jf < (T)box_J(l) ? off + (int)jf : -1;
+    }
+    off += box_J(l);
+    w *= T(2);
+  }
+  return -1;
+}
+
+// moments m_k = v 6 k!/(k+4)! sum_j f_j h_k(e, e_j), k < K, of a piece about a box (e = (d - C)/R)
+template <typename T> __device__ __forceinline__ void box_moments(const T e[4], const T f[4], T v, T *m, int K) {
+  T H[4] = {T(1), T(1), T(1), T(1)};
+  T P[4] = {T(1), T(1), T(1), T(1)};
+  m[0] = v * T(0.25) * (f[0] + f[1] + f[2] + f[3]);
+  for (int k = 1; k < K; ++k) {
+    H[0] = e[0] * H[0];
+#pragma unroll
+    for (int l = 1; l < 4; ++l) H[l] = H[l - 1] + e[l] * H[l];
+    T sj = T(0);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      P[jj] = H[3] + e[jj] * P[jj];
+      sj += f[jj] * P[jj];
+    }
+    m[k] = v * tabs(series_coef<T>(k)) * sj;
+  }
+}
+
+// does box b stand in for term (0: 1/(D - u), 1: 1/(D + u)) at frequency u = om?  Fine boxes
+// only near themselves; geometric boxes always.  Same expression in both kernels.
+template <typename T> __device__ __forceinline__ bool box_far(T C, T R, int b, T om, int term) {
+  if (b >= kBoxFine) return true;
+  const T r2 = R + R;
+  if (term) return !(C + om < r2);
+  return !(tabs(C - om) < r2);
+}
+
+// sum_j f_j (1/V) int lambda_j / X for knots x of X near 0: divided-difference table (principal
+// value across X = 0); one out-of-line copy shared by every call site
+template <bool FP64>
+__device__ __noinline__ typename std::conditional<FP64, double, float>::type near_term(
+    const typename std::conditional<FP64, double, float>::type *x,
+    const typename std::conditional<FP64, double, float>::type *f, float tau, int &nfp64) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  T xx[4] = {x[0], x[1], x[2], x[3]};
+  if constexpr (FP64) {
+    return inv_sum(xx, f);
+  } else {
+    return inv_sum_mixed(xx, f, tau, &nfp64);
+  }
+}
+
+// D0 - w for a frequency near the knots: with D0 = D0h + D0l and w = wh + wl split into
+// FP32 parts the difference keeps full relative precision however close D0 is to w
+__device__ __forceinline__ float near_shift(float D0h, float D0l, float wh, float wl) {
+  float sv, tv;
+  two_diff(D0h, wh, sv, tv);
+  return sv + (tv + (D0l - wl));
+}
+__device__ __forceinline__ double near_shift(double D0h, double, double wh, double) { return D0h - wh; }
+
+// evaluates a warp's near-field list: entry = 2 * frequency index + term; every entry of one
+// round has a different frequency index or term, and the two terms of one frequency go to
+// different rounds only through the list order, so each round adds to distinct slots.
+// Knots of the piece: d = D0 + e (sorted), D0 = D0h + D0l; term 0 is 1/(D - |w|) with knots
+// (D0 - |w|) + e, term 1 is 1/(D + |w|) with knots d + |w|.
+template <bool FP64, typename T>
+__device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D0l, const T f[4], T vr,
+                                          const T *s_w, const T *s_wl, const short *list, int n, T *sR, T *cR,
+                                          T *sI, T *cI, float tau, int &nfp64) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    const int k = base + lane;
+    if (k < n) {
+      const int ent = list[k];
+      const int iw = ent >> 1, sgn = ent & 1;
+      const T w = s_w[iw];
+      const bool neg = w < T(0);
+      const T om = neg ? -w : w;
+      T x[4];
+      if (sgn) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = d[i] + om;
+      } else {
+        const T sh = near_shift(D0h, D0l, om, FP64 ? T(0) : (neg ? -s_wl[iw] : s_wl[iw]));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = sh + e[i];
+      }
+      // a frequency and its two terms may both be in this round: add them one term at a time
+      const T re = near_term<FP64>(x, f, tau, nfp64);
+      for (int t2 = 0; t2 < 2; ++t2) {
+        if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
+        __syncwarp(__activemask());
+      }
+      if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {  // |w| inside the knot range: the delta term too
+        const T im = delta_sum(x, f, T(0)) * T(3.141592653589793);
+        kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
+    k_dynamic(Grid g, Tet tet, const void *__restrict__ Ek, const void *__restrict__ Ekq, Q q,
+              const void *__restrict__ W2, int cma, float tau, const short *__restrict__ occ,
+              const short *__restrict__ empq, const double *__restrict__ omega, int nw, DynBufs db,
+              const float *__restrict__ Eklo, const float *__restrict__ Ekqlo,
+              unsigned long long *__restrict__ counters) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  using S = DynShape<FP64>;
+  constexpr int W = S::warps, PB = S::PB, KM = S::KM, KF = S::KF, KG = S::KG;
+  constexpr int NS = box_slots<FP64>();
+  __shared__ int s_c[W][32][4], s_cq[W][32][4];
+  __shared__ T s_vol[W][32];
+  __shared__ int s_nlo[W][32], s_nn[W][32], s_pre[W][33];
+  // buffered final tetrahedra: offsets e from D0 (sorted), values f, (weight, D0h, D0l), their
+  // own far-field moments (K of them) and box moments (box id; -1 none)
+  __shared__ T s_pe[W][PB][4], s_pf[W][PB][4], s_pv[W][PB][3];
+  __shared__ T s_am[W][PB][KM], s_bm[W][PB][KF];
+  __shared__ int s_pk[W][PB], s_bx[W][PB];
+  __shared__ T sR[W][kNWPass], sI[W][kNWPass];
+  __shared__ T cR[W][kNWPass], cI[W][kNWPass];  // compensation terms
+  __shared__ T s_w[kNWPass];
+  __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
+  __shared__ short s_near[W][kNearCap];
+  __shared__ BoxTab<T> s_tab;
+  extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  T *acc = (T *)s_dyn + (size_t)wib * NS;
+  const int w = q.hi - q.lo;
+  const long long nbatch = (g.ntet + 31) / 32;
+  const long long gwarp = (long long)blockIdx.x * W + wib, nwarps = (long long)gridDim.x * W;
+  double *gpart = db.box_part + gwarp * NS;
+  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
+    s_w[iw] = (T)omega[iw];
+    if constexpr (!FP64) s_wl[iw] = (float)(omega[iw] - (double)s_w[iw]);
+  }
+  {
+    const BoxTab<T> *src = (const BoxTab<T> *)db.box_tab;
+    const int nwords = (int)(sizeof(BoxTab<T>) / 4);
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) ((int *)&s_tab)[i] = ((const int *)src)[i];
+  }
+  for (int i = lane; i < NS; i += 32) acc[i] = T(0);
+  __syncthreads();
+  const bool boxes = s_tab.on != 0;
+  int nfp64 = 0, npieces = 0, nboxed = 0;
+  // one final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr, own
+  // far-field moments am[0..K)) on the frequencies its box (b >= 0) does not stand in for
+  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b) {
+    T d[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
+    const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
+    const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
+    // far field for both terms (Horner on the moments); near-field frequencies are
+    // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
+    unsigned nearm = 0u, nearp = 0u;
+    for (int iw = lane, itn = 0; iw < nw; iw += 32, ++itn) {
+      const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
+      T re = T(0);
+      if (b < 0 || !box_far(Cb, Rb, b, om, 1)) {
+        const T rp = half / (c + om);
+        if (rp <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, -om, rp);
+        else nearp |= 1u << itn;
+      }
+      if (b < 0 || !box_far(Cb, Rb, b, om, 0)) {
+        const T dm = c - om;
+        const T rm = half / (dm < T(0) ? -dm : dm);
+        if (rm <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, om, rm);
+        else nearm |= 1u << itn;
+      }
+      if (re != T(0)) kadd_t(sR[wib][iw], cR[wib][iw], vr * re);
+    }
+    // near field: compact the (frequency, term) pairs of the warp into a list
+    int nlist = 0;
+    const int nit = (nw + 31) >> 5;
+    for (int itn = 0; itn < nit; ++itn) {
+#pragma unroll
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
+        const unsigned bal = __ballot_sync(kFull, mine);
+        if (mine) s_near[wib][nlist + __popc(bal & ((1u << lane) - 1u))] = (short)((itn * 32 + lane) * 2 + sgn);
+        nlist += __popc(bal);
+      }
+      if (nlist > kNearCap - 64) {  // flush a full list
+        __syncwarp();
+        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
+                        cI[wib], tau, nfp64);
+        nlist = 0;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib], cI[wib],
+                    tau, nfp64);
+    __syncwarp();
+  };
+  // buffered pieces: box and moments one piece per lane, box sums one moment per lane, then
+  // each piece on the frequencies its box leaves to it
+  int npb = 0;
+  auto flush = [&]() {
+    __syncwarp();  // lane 0's buffer writes are visible to every lane
+    if (lane < npb) {
+      T ee[4], ff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ee[i] = s_pe[wib][lane][i];
+        ff[i] = s_pf[wib][lane][i];
+      }
+      const T vr = s_pv[wib][lane][0], D0h = s_pv[wib][lane][1], D0l = s_pv[wib][lane][2];
+      const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
+      const int b = boxes ? box_of(c, half, s_tab) : -1;
+      s_bx[wib][lane] = b;
+      nboxed += b >= 0;
+      if (b >= 0) {
+        const T ri = T(1) / s_tab.R[b], base = (D0h - s_tab.C[b]) + D0l;
+        T e[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) e[i] = (base + ee[i]) * ri;
+        box_moments(e, ff, vr, s_bm[wib][lane], b < kBoxFine ? KF : KG);
+      }
+      if (b < kBoxFine) {  // the piece evaluates some frequencies itself
+        T d[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
+        s_pk[wib][lane] = far_moments<T, KM>(d, ff, s_am[wib][lane]);
+      }
+    }
+    __syncwarp();
+    for (int p = 0; p < npb; ++p) {  // lane k adds moment k: no two lanes share a slot
+      const int b = s_bx[wib][p];
+      if (b < 0) continue;
+      const int K = b < kBoxFine ? KF : KG, base = slot_base<FP64>(b);
+      for (int k = lane; k < K; k += 32) acc[base + k] += s_bm[wib][p][k];
+    }
+    for (int p = 0; p < npb; ++p) {
+      const int b = s_bx[wib][p];
+      if (b >= kBoxFine) continue;
+      T ee[4], ff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ee[i] = s_pe[wib][p][i];
+        ff[i] = s_pf[wib][p][i];
+      }
+      eval_piece(ee, ff, s_pv[wib][p][0], s_pv[wib][p][1], s_pv[wib][p][2], s_am[wib][p], s_pk[wib][p], b);
+    }
+    __syncwarp();
+    npb = 0;
+  };
+  bool first = true;  // this warp's first batch writes its box partials, later ones add to them
+  for (long long batch = gwarp; batch < nbatch; batch += nwarps) {
+    for (int iw = lane; iw < nw; iw += 32) {
+      sR[wib][iw] = T(0);
+      sI[wib][iw] = T(0);
+      cR[wib][iw] = T(0);
+      cI[wib][iw] = T(0);
+    }
+    const long long t = batch * 32 + lane;
+    int cnt = 0;
+    if (t < g.ntet) {
+      long long c[4], cq[4];
+      double vol;
+      tet_corners(g, tet, q, t, c, cq, vol);
+      int mhi = 0, nlo = g.nb;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        s_c[wib][lane][i] = (int)c[i];
+        s_cq[wib][lane][i] = (int)cq[i];
+        mhi = max(mhi, (int)occ[c[i]]);
+        nlo = min(nlo, (int)empq[cq[i]]);
+      }
+      mhi = min(mhi, q.hi);
+      nlo = max(nlo, q.lo);
+      const int nm = mhi - q.lo, nn = q.hi - nlo;
+      cnt = (nm > 0 && nn > 0) ? nm * nn : 0;
+      s_vol[wib][lane] = (T)vol;
+      s_nlo[wib][lane] = nlo;
+      s_nn[wib][lane] = nn;
+    }
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, pre, o);
+      if (lane >= o) pre += v;
+    }
+    s_pre[wib][lane + 1] = pre;
+    if (lane == 0) s_pre[wib][0] = 0;
+    const int total = __shfl_sync(kFull, pre, 31);
+    __syncwarp();
+    int l = 0;
+    auto item = [&](int it) {
+      while (s_pre[wib][l + 1] <= it) ++l;
+      const int loc = it - s_pre[wib][l];
+      const int nn = s_nn[wib][l];
+      const int mo = div_small(loc, nn, q.hi - q.lo);
+      const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
+      if (q.gamma && m == n) return;
+      // band pair: a = e^m_k - eF, D = D0 + e (e_0 = 0).  Mixed path: energies as FP32
+      // hi + lo pairs, so that D0 (hi + lo) and the corner offsets e come out to full FP32
+      // relative precision whatever the size of a and b
+      T a[4], e[4], f[4];
+      T D0h = T(0), D0l = T(0);
+      T amin = T(1e30), bmax = T(-1e30);
+      if constexpr (FP64) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
+          a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
+          const double b = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
+          e[i] = b - a[i];
+          amin = a[i] < amin ? a[i] : amin;
+          bmax = b > bmax ? b : bmax;
+        }
+      } else {
+        float al[4], bh[4], bl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const long long ik = (long long)s_c[wib][l][i] * g.nb + m, iq = (long long)s_cq[wib][l][i] * g.nb + n;
+          a[i] = ((const float *)Ek)[ik];
+          al[i] = Eklo[ik];
+          bh[i] = ((const float *)Ekq)[iq];
+          bl[i] = Ekqlo[iq];
+          amin = a[i] < amin ? a[i] : amin;
+          bmax = bh[i] > bmax ? bh[i] : bmax;
+        }
+        float sv, tv;
+        two_diff(bh[0], a[0], sv, tv);
+        const float corr = tv + (bl[0] - al[0]);
+        D0h = sv + corr;
+        D0l = corr - (D0h - sv);
+        e[0] = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 4; ++i) {
+          float sa, ta, sb, tb;
+          two_diff(a[i], a[0], sa, ta);
+          two_diff(bh[i], bh[0], sb, tb);
+          e[i] = (sb - sa) + ((tb - ta) + ((bl[i] - bl[0]) - (al[i] - al[0])));
+        }
+      }
+      if (!(amin < T(0) && bmax > T(0))) return;
+      const T *W2t = (const T *)W2;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
+      const T vol = s_vol[wib][l];
+      carve2_off<T>(a, e, D0h, f, [&](T r, T ee[4], T ff[4]) {
+        sort4(ee, ff);
+        ++npieces;
+        if (!(D0h + ee[3] > T(0))) return;
+        if (lane == 0) {  // every lane holds the same piece
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            s_pe[wib][npb][i] = ee[i];
+            s_pf[wib][npb][i] = ff[i];
+          }
+          s_pv[wib][npb][0] = vol * r;
+          s_pv[wib][npb][1] = D0h;
+          s_pv[wib][npb][2] = D0l;
+        }
+        ++npb;
+      });
+    };
+    for (int it = 0;; ++it) {  // warp-uniform; the pass after the last item flushes the buffer
+      const bool last = it >= total;
+      if (!last) item(it);
+      if (last || npb > PB - 9) flush();  // an item adds at most 9 pieces
+      if (last) break;
+    }
+    __syncwarp();
+    for (int iw = lane; iw < nw; iw += 32) {
+      db.partR[batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
+      db.partI[batch * nw + iw] = (double)sI[wib][iw] + (double)cI[wib][iw];
+    }
+    // this batch's box sums into the warp's FP64 partials (a fixed order: bitwise reproducible)
+    if (boxes) {
+      for (int i = lane; i < NS; i += 32) {
+        const double v = (double)acc[i];
+        gpart[i] = first ? v : gpart[i] + v;
+        acc[i] = T(0);
+      }
+    }
+    first = false;
+    __syncwarp();
+  }
+  if (boxes && first)  // a warp without batches
+    for (int i = lane; i < NS; i += 32) gpart[i] = 0.0;
+  if (counters) {
+    unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64,
+                       x = (unsigned long long)nboxed;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+      x += __shfl_xor_sync(kFull, x, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&counters[0], a / 32);  // every lane counted each piece
+      atomicAdd(&counters[1], b);
+      atomicAdd(&counters[3], x);       // each lane counted its own buffered pieces
+    }
+  }
+}
+
+// box totals: slot i summed over the warps of the weight launch, in warp order
+template <bool FP64>
+__global__ void __launch_bounds__(256) k_box_sum(const double *__restrict__ part, int nwarps, double *__restrict__ tot) {
+  constexpr int NS = box_slots<FP64>();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NS) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int wv = 0;
+  for (; wv + 3 < nwarps; wv += 4) {
+    s0 += part[(size_t)wv * NS + i];
+    s1 += part[(size_t)(wv + 1) * NS + i];
+    s2 += part[(size_t)(wv + 2) * NS + i];
+    s3 += part[(size_t)(wv + 3) * NS + i];
+  }
+  for (; wv < nwarps; ++wv) s0 += part[(size_t)wv * NS + i];
+  tot[i] = (s0 + s1) + (s2 + s3);
+}
+
+// far[iw]: the boxes' share of Re at frequency iw (FP64 evaluation of the multipoles); one
+// block per frequency, fixed-order reduction
+template <bool FP64>
+__global__ void __launch_bounds__(128) k_box_eval(const double *__restrict__ omega, const void *__restrict__ tabp,
+                                                  const double *__restrict__ tot, double *__restrict__ far) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  using S = DynShape<FP64>;
+  const BoxTab<T> &tb = *(const BoxTab<T> *)tabp;
+  const int iw = blockIdx.x;
+  const double u = fabs(omega[iw]);
+  const T wT = (T)omega[iw];
+  const T om = wT < T(0) ? -wT : wT;
+  double v = 0.0;
+  if (tb.on) {
+    for (int b = threadIdx.x; b < kBoxes; b += blockDim.x) {
+      const int K = b < kBoxFine ? S::KF : S::KG;
+      const double *M = tot + slot_base<FP64>(b);
+      const double C = (double)tb.C[b], R = (double)tb.R[b];
+      for (int term = 0; term < 2; ++term) {
+        if (!box_far(tb.C[b], tb.R[b], b, om, term)) continue;
+        const double den = term ? C + u : C - u;
+        const double mz = -R / den;
+        double s = M[K - 1];
+        for (int k = K - 2; k >= 0; --k) s = s * mz + M[k];
+        v += s / den;
+      }
+    }
+  }
+  __shared__ double red[4];
+  v = grid::warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) far[iw] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+template <bool FP64> size_t dyn_smem() {
+  return (size_t)DynShape<FP64>::warps * box_slots<FP64>() * (FP64 ? sizeof(double) : sizeof(float));
+}
+
+}  // namespace
+
+int dynamic_max_nw() { return kNWPass; }
+int dynamic_warps_per_cta(int fp64) { return fp64 ? DynShape<true>::warps : DynShape<false>::warps; }
+size_t dynamic_box_slots(int fp64) { return fp64 ? box_slots<true>() : box_slots<false>(); }
+size_t dynamic_box_tab_bytes() {
+  return sizeof(BoxTab<double>) > sizeof(BoxTab<float>) ? sizeof(BoxTab<double>) : sizeof(BoxTab<float>);
+}
+
+cudaError_t dynamic_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_dynamic<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dyn_smem<true>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_dynamic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)dyn_smem<false>());
+}
+
+cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
+                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
+                           const double *omega, int nw, const DynBufs &db, int nblocks,
+                           unsigned long long *counters, cudaStream_t s, const float *Eklo,
+                           const float *Ekqlo) {
+  if (nw > kNWPass || nw <= 0 || nblocks <= 0) return cudaErrorInvalidValue;
+  if (!fp64 && (!Eklo || !Ekqlo)) return cudaErrorInvalidValue;
+  if (!db.box_tab || !db.box_part || !db.box_tot || !db.far) return cudaErrorInvalidValue;
+  if (fp64) {
+    const int nwarps = nblocks * DynShape<true>::warps;
+    k_box_setup<double><<<1, 256, 0, s>>>(omega, nw, (BoxTab<double> *)db.box_tab);
+    k_dynamic<true><<<nblocks, DynShape<true>::threads, dyn_smem<true>(), s>>>(
+        g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db, Eklo, Ekqlo, counters);
+    k_box_sum<true><<<(box_slots<true>() + 255) / 256, 256, 0, s>>>(db.box_part, nwarps, db.box_tot);
+    k_box_eval<true><<<nw, 128, 0, s>>>(omega, db.box_tab, db.box_tot, db.far);
+  } else {
+    const int nwarps = nblocks * DynShape<false>::warps;
+    k_box_setup<float><<<1, 256, 0, s>>>(omega, nw, (BoxTab<float> *)db.box_tab);
+    k_dynamic<false><<<nblocks, DynShape<false>::threads, dyn_smem<false>(), s>>>(
+        g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db, Eklo, Ekqlo, counters);
+    k_box_sum<false><<<(box_slots<false>() + 255) / 256, 256, 0, s>>>(db.box_part, nwarps, db.box_tot);
+    k_box_eval<false><<<nw, 128, 0, s>>>(omega, db.box_tab, db.box_tot, db.far);
+  }
+  return cudaGetLastError();
+}
+
+int dynamic_max_ctas_per_sm(int fp64) {
+  int nb = 0;
+  cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<true>, DynShape<true>::threads,
+                                                                      dyn_smem<true>())
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<false>,
+                                                                      DynShape<false>::threads, dyn_smem<false>());
+  return (e != cudaSuccess || nb < 1) ? 1 : nb;
+}
+
+int dynamic_persistent_blocks(int fp64) { return dynamic_max_ctas_per_sm(fp64) * device_sms(); }
+
+}  // namespace chi0int

@@ -92,27 +92,37 @@ int static_tab_cap();
 void set_global_error(const char *msg);
 size_t static_piece_bytes(int fp64);
 
-// Work buffers of the dynamic kernel: one partial per (batch of 32 tetrahedra, frequency)
+// Work buffers of the dynamic weights: one partial per (batch of 32 tetrahedra, frequency) for
+// the pieces evaluated directly, and the far-field box moments (per warp, then summed)
 struct DynBufs {
   double *partR, *partI;  // [nbatch][nw]
-  int *next;              // batch counter
+  void *box_tab;          // box centres and radii of the pass (dynamic_box_tab_bytes())
+  double *box_part;       // [warps of the launch][dynamic_box_slots(fp64)]
+  double *box_tot;        // [dynamic_box_slots(fp64)]
+  double *far;            // [nw]: Re contribution of the box multipoles per frequency
 };
 
-// dynamic weights for one q and nw <= dynamic_max_nw() frequencies
+// dynamic weights for one q and nw <= dynamic_max_nw() frequencies: partR/partI per batch and
+// far[nw] (add far to the sum of partR)
 cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                            const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
                            const double *omega, int nw, const DynBufs &db, int nblocks,
                            unsigned long long *counters, cudaStream_t s, const float *Eklo,
                            const float *Ekqlo);
 int dynamic_persistent_blocks(int fp64);
+int dynamic_warps_per_cta(int fp64);
+size_t dynamic_box_slots(int fp64);
+size_t dynamic_box_tab_bytes();
+cudaError_t dynamic_prepare();  // kernel attributes (shared memory); call outside stream capture
 
 // Gamma: intraband q -> 0 limit, tetrahedron DOS at eF: partial[nblocks]
 cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,
                        int nblocks, cudaStream_t s);
 
-// out[idx*stride_out + k] = scale * sum_b partial[b*nw + k] (+ scale * sum dos where omega == 0)
+// out[k] = scale * (sum_b partial[b*nw + k] (+ sum dos where omega == 0) (+ extra[k]))
 cudaError_t launch_reduce(const double *partial, int nblocks, int nw, double scale, const double *dos,
-                          int ndos, const double *omega, double *out, cudaStream_t s);
+                          int ndos, const double *omega, double *out, cudaStream_t s,
+                          const double *extra = nullptr);
 
 int static_blocks();
 int dynamic_max_nw();

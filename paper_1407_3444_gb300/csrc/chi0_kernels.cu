@@ -11,9 +11,7 @@
 //             time: the two carvings of Sec. II and the closed-form 2/D integral (Eq. 1 at
 //             w = 0) by its midpoint series; other pieces are queued for k_static_tab.
 //             Per-batch FP64 partial sums.
-//  k_dynamic  persistent warps, band pairs walked by the whole warp, the lanes own the
-//             frequencies: PV 1/(D-w) + 1/(D+w) (Eq. 1) by far-field moments or the
-//             near-field table, and pi delta(w - D) (Eq. 2) by B-splines.
+//  (the dynamic weights, Eqs. 1-3, are in chi0_dynamic.cu)
 //  k_dos      Gamma: the intraband q -> 0 limit, tetrahedron DOS at eF (Sec. III).
 //  k_reduce   deterministic fixed-order sum of the batch partials.
 #include <cuda_runtime.h>
@@ -21,6 +19,7 @@
 
 #include <type_traits>
 
+#include "chi0_grid.cuh"
 #include "chi0_internal.h"
 #include "chi0_math.cuh"
 
@@ -34,18 +33,10 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kSMs = 152;
 constexpr int kStaticBlocks = kSMs * 8;
-constexpr unsigned kFull = 0xffffffffu;
-
-// x / d for 0 <= x < qmax * d (small quotients): binary search, no division sequence
-__device__ __forceinline__ int div_small(int x, int d, int qmax) {
-  int lo = 0, hi = qmax;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (mid * d <= x) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
+using grid::kFull;
+using grid::div_small;
+using grid::tet_corners;
+using grid::warp_sum;
 
 // double -> float rounded to nearest even by integer operations (keeps the conversion of
 // complex128 inputs off the FP64 pipe); magnitudes below 2^-126 flush to zero
@@ -66,55 +57,6 @@ __device__ __forceinline__ float d2f_int(double x) {
 template <typename T> __device__ __forceinline__ T cvt(double x);
 template <> __device__ __forceinline__ float cvt<float>(double x) { return d2f_int(x); }
 template <typename T> __device__ __forceinline__ T cvt(float x) { return (T)x; }
-
-// Corners of tetrahedron t at k and at k+q, and its fractional volume.  Builtin mesh:
-// tetrahedron 6*cube + p = {000, e_a, e_a + e_b, 111} for the p-th axis order (a, b, .)
-// of the lexicographically ordered permutations of (0, 1, 2).
-__device__ __forceinline__ void tet_corners(const Grid &g, const Tet &tet, const Q &q, long long t,
-                                            long long c[4], long long cq[4], double &vol) {
-  if (tet.corners) {
-    const int4 v = tet.corners[t];
-    c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
-    vol = tet.vol[t];
-    for (int i = 0; i < 4; ++i) cq[i] = q.Eq ? c[i] : shift_corner(g, c[i], q.shift);
-    return;
-  }
-  const unsigned tu = (unsigned)t;
-  const unsigned cube = tu / 6u;
-  const int p = (int)(tu - cube * 6u);
-  const unsigned r = fdiv(cube, g.fn2);
-  const int i2 = (int)(cube - r * (unsigned)g.n[2]);
-  const unsigned i0u = fdiv(r, g.fn1);
-  const int i1 = (int)(r - i0u * (unsigned)g.n[1]);
-  const int i0 = (int)i0u;
-  const int ax = p >> 1;                                // first axis: 0,0,1,1,2,2
-  const int bx = (p == 0) ? 1 : (p == 1) ? 2 : (p == 2) ? 0 : (p == 3) ? 2 : (p == 4) ? 0 : 1;
-  int o1[3] = {0, 0, 0}, o2[3] = {0, 0, 0};
-  o1[ax] = 1;
-  o2[ax] = 1;
-  o2[bx] = 1;
-  const int *s = q.shift;
-  const bool ex = q.Eq != nullptr;
-  c[0] = cid(g, i0, i1, i2);
-  c[1] = cid(g, i0 + o1[0], i1 + o1[1], i2 + o1[2]);
-  c[2] = cid(g, i0 + o2[0], i1 + o2[1], i2 + o2[2]);
-  c[3] = cid(g, i0 + 1, i1 + 1, i2 + 1);
-  if (ex) {
-    for (int i = 0; i < 4; ++i) cq[i] = c[i];
-  } else {
-    cq[0] = cid(g, i0 + s[0], i1 + s[1], i2 + s[2]);
-    cq[1] = cid(g, i0 + o1[0] + s[0], i1 + o1[1] + s[1], i2 + o1[2] + s[2]);
-    cq[2] = cid(g, i0 + o2[0] + s[0], i1 + o2[1] + s[1], i2 + o2[2] + s[2]);
-    cq[3] = cid(g, i0 + 1 + s[0], i1 + 1 + s[1], i2 + 1 + s[2]);
-  }
-  vol = tet.vol_builtin;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
 
 __device__ __forceinline__ void block_sum_store(double v, double *out) {
   __shared__ double red[kWarps];
@@ -517,380 +459,6 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
   }
 }
 
-// ---------------------------------------------------------------- dynamic weights
-// Persistent warps take batches of 32 tetrahedra (as k_static); the warp walks the batch's
-// (m, n) items together and the lanes own the frequencies.  Per final tetrahedron the warp
-// forms the far-field moments once; each lane then evaluates 1/(D - w) + 1/(D + w) for its
-// frequencies from them (Horner in z = c/(c -+ w)) wherever rho = max|D - c|/|c -+ w| is at
-// most kappa_far, and from the divided-difference table (principal value) nearer; Im uses
-// the B-spline density inside the knot range.  Per (warp, w) compensated accumulators in
-// shared memory; one partial per (batch, w), summed in a fixed order.
-constexpr int kDynThreads = 128;
-constexpr int kDynWarps = kDynThreads / 32;
-constexpr int kNWPass = 256;  // frequencies per dynamic pass
-constexpr int kDynPB = 16;    // final tetrahedra buffered per warp (FP32 dynamic kernel)
-
-template <typename T> struct FarK {
-  static constexpr int value = sizeof(T) == 8 ? 64 : 32;  // moments kept per final tetrahedron
-};
-constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed per warp
-
-template <typename T> __device__ __forceinline__ void kadd_t(T &sum, T &comp, T x) {
-  const T t = sum + x;
-  if (tabs(sum) >= tabs(x)) comp += (sum - t) + x;
-  else comp += (x - t) + sum;
-  sum = t;
-}
-
-// sum_j f_j (1/V) int lambda_j / X for knots x of X near 0: divided-difference table (principal
-// value across X = 0); one out-of-line copy shared by every call site
-template <bool FP64>
-__device__ __noinline__ typename std::conditional<FP64, double, float>::type near_term(
-    const typename std::conditional<FP64, double, float>::type *x,
-    const typename std::conditional<FP64, double, float>::type *f, float tau, int &nfp64) {
-  using T = typename std::conditional<FP64, double, float>::type;
-  T xx[4] = {x[0], x[1], x[2], x[3]};
-  if constexpr (FP64) {
-    return inv_sum(xx, f);
-  } else {
-    return inv_sum_mixed(xx, f, tau, &nfp64);
-  }
-}
-
-// D0 - w for a frequency near the knots: with D0 = D0h + D0l and w = wh + wl split into
-// FP32 parts the difference keeps full relative precision however close D0 is to w
-__device__ __forceinline__ float near_shift(float D0h, float D0l, float wh, float wl) {
-  float sv, tv;
-  two_diff(D0h, wh, sv, tv);
-  return sv + (tv + (D0l - wl));
-}
-__device__ __forceinline__ double near_shift(double D0h, double, double wh, double) { return D0h - wh; }
-
-// evaluates a warp's near-field list: entry = 2 * frequency index + term; every entry of one
-// round has a different frequency index or term, and the two terms of one frequency go to
-// different rounds only through the list order, so each round adds to distinct slots.
-// Knots of the piece: d = D0 + e (sorted), D0 = D0h + D0l; term 0 is 1/(D - |w|) with knots
-// (D0 - |w|) + e, term 1 is 1/(D + |w|) with knots d + |w|.
-template <bool FP64>
-__device__ __forceinline__ void near_pass(const typename std::conditional<FP64, double, float>::type d[4],
-                                          const typename std::conditional<FP64, double, float>::type e[4],
-                                          typename std::conditional<FP64, double, float>::type D0h,
-                                          typename std::conditional<FP64, double, float>::type D0l,
-                                          const typename std::conditional<FP64, double, float>::type f[4],
-                                          typename std::conditional<FP64, double, float>::type vr,
-                                          const typename std::conditional<FP64, double, float>::type *s_w,
-                                          const typename std::conditional<FP64, double, float>::type *s_wl,
-                                          const short *list, int n,
-                                          typename std::conditional<FP64, double, float>::type *sR,
-                                          typename std::conditional<FP64, double, float>::type *cR,
-                                          typename std::conditional<FP64, double, float>::type *sI,
-                                          typename std::conditional<FP64, double, float>::type *cI, float tau,
-                                          int &nfp64) {
-  using T = typename std::conditional<FP64, double, float>::type;
-  const int lane = threadIdx.x & 31;
-  for (int base = 0; base < n; base += 32) {
-    const int k = base + lane;
-    if (k < n) {
-      const int ent = list[k];
-      const int iw = ent >> 1, sgn = ent & 1;
-      const T w = s_w[iw];
-      const bool neg = w < T(0);
-      const T om = neg ? -w : w;
-      T x[4];
-      if (sgn) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = d[i] + om;
-      } else {
-        const T sh = near_shift(D0h, D0l, om, FP64 ? T(0) : (neg ? -s_wl[iw] : s_wl[iw]));
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = sh + e[i];
-      }
-      // a frequency and its two terms may both be in this round: add them one term at a time
-      const T re = near_term<FP64>(x, f, tau, nfp64);
-      for (int t2 = 0; t2 < 2; ++t2) {
-        if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
-        __syncwarp(__activemask());
-      }
-      if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {  // |w| inside the knot range: the delta term too
-        const T im = delta_sum(x, f, T(0)) * T(3.141592653589793);
-        kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
-      }
-    }
-    __syncwarp();
-  }
-}
-
-template <bool FP64>
-__global__ void __launch_bounds__(kDynThreads) k_dynamic(Grid g, Tet tet, const void *__restrict__ Ek,
-                                                          const void *__restrict__ Ekq, Q q,
-                                                          const void *__restrict__ W2, int cma, float tau,
-                                                          const short *__restrict__ occ,
-                                                          const short *__restrict__ empq,
-                                                          const double *__restrict__ omega, int nw, DynBufs db,
-                                                          const float *__restrict__ Eklo,
-                                                          const float *__restrict__ Ekqlo,
-                                                          unsigned long long *__restrict__ counters) {
-  using T = typename std::conditional<FP64, double, float>::type;
-  constexpr int KM = FarK<T>::value;
-  __shared__ int s_c[kDynWarps][32][4], s_cq[kDynWarps][32][4];
-  __shared__ T s_vol[kDynWarps][32];
-  __shared__ int s_nlo[kDynWarps][32], s_nn[kDynWarps][32], s_pre[kDynWarps][33];
-  // FP32: final tetrahedra are buffered (kDynPB per warp) so that their far-field moments are
-  // computed one piece per lane instead of serially by one lane; FP64 evaluates each piece
-  // as it is carved (its moment arrays would not fit the buffer in shared memory)
-  constexpr int PB = FP64 ? 1 : kDynPB;
-  __shared__ T s_am[kDynWarps][PB][KM];
-  __shared__ T s_pe[kDynWarps][PB][4], s_pf[kDynWarps][PB][4], s_pv[kDynWarps][PB][3];
-  __shared__ int s_pk[kDynWarps][PB];
-  __shared__ T sR[kDynWarps][kNWPass], sI[kDynWarps][kNWPass];
-  __shared__ T cR[kDynWarps][kNWPass], cI[kDynWarps][kNWPass];  // compensation terms
-  __shared__ T s_w[kNWPass];
-  __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
-  __shared__ short s_near[kDynWarps][kNearCap];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int w = q.hi - q.lo;
-  const long long nbatch = (g.ntet + 31) / 32;
-  for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
-    s_w[iw] = (T)omega[iw];
-    if constexpr (!FP64) s_wl[iw] = (float)(omega[iw] - (double)s_w[iw]);
-  }
-  __syncthreads();
-  int nfp64 = 0, npieces = 0;
-  auto kadd = [](T &sum, T &comp, T x) {
-    const T t = sum + x;
-    if (tabs(sum) >= tabs(x)) comp += (sum - t) + x;
-    else comp += (x - t) + sum;
-    sum = t;
-  };
-  // one final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr) on
-  // every frequency of the pass, with its far-field moments am[0..K)
-  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K) {
-    T d[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
-    const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
-    // far field for both terms (Horner on the moments); near-field frequencies are
-    // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
-    unsigned nearm = 0u, nearp = 0u;
-    for (int iw = lane, itn = 0; iw < nw; iw += 32, ++itn) {
-      const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
-      T re = T(0);
-      const T rp = half / (c + om);
-      if (rp <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, -om, rp);
-      else nearp |= 1u << itn;
-      const T dm = c - om;
-      const T rm = half / (dm < T(0) ? -dm : dm);
-      if (rm <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, om, rm);
-      else nearm |= 1u << itn;
-      if (re != T(0)) kadd(sR[wib][iw], cR[wib][iw], vr * re);
-    }
-    // near field: compact the (frequency, term) pairs of the warp into a list
-    int nlist = 0;
-    const int nit = (nw + 31) >> 5;
-    for (int itn = 0; itn < nit; ++itn) {
-#pragma unroll
-      for (int sgn = 0; sgn < 2; ++sgn) {
-        const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
-        const unsigned bal = __ballot_sync(kFull, mine);
-        if (mine) s_near[wib][nlist + __popc(bal & ((1u << lane) - 1u))] = (short)((itn * 32 + lane) * 2 + sgn);
-        nlist += __popc(bal);
-      }
-      if (nlist > kNearCap - 64) {  // flush a full list
-        __syncwarp();
-        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
-                        cI[wib], tau, nfp64);
-        nlist = 0;
-        __syncwarp();
-      }
-    }
-    __syncwarp();
-    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
-                        cI[wib], tau, nfp64);
-    __syncwarp();
-  };
-  // buffered pieces (FP32): moments one piece per lane, then each piece on all frequencies
-  int npb = 0;
-  auto flush = [&]() {
-    __syncwarp();  // lane 0's buffer writes are visible to every lane
-    if (lane < npb) {
-      T d[4], ff[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        d[i] = s_pv[wib][lane][1] + s_pe[wib][lane][i];
-        ff[i] = s_pf[wib][lane][i];
-      }
-      s_pk[wib][lane] = far_moments<T, KM>(d, ff, s_am[wib][lane]);
-    }
-    __syncwarp();
-    for (int p = 0; p < npb; ++p) {
-      T ee[4], ff[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        ee[i] = s_pe[wib][p][i];
-        ff[i] = s_pf[wib][p][i];
-      }
-      eval_piece(ee, ff, s_pv[wib][p][0], s_pv[wib][p][1], s_pv[wib][p][2], s_am[wib][p], s_pk[wib][p]);
-    }
-    __syncwarp();
-    npb = 0;
-  };
-  for (;;) {
-    int batch = 0;
-    if (lane == 0) batch = atomicAdd(db.next, 1);
-    batch = __shfl_sync(kFull, batch, 0);
-    if (batch >= nbatch) break;
-    for (int iw = lane; iw < nw; iw += 32) {
-      sR[wib][iw] = T(0);
-      sI[wib][iw] = T(0);
-      cR[wib][iw] = T(0);
-      cI[wib][iw] = T(0);
-    }
-    const long long t = (long long)batch * 32 + lane;
-    int cnt = 0;
-    if (t < g.ntet) {
-      long long c[4], cq[4];
-      double vol;
-      tet_corners(g, tet, q, t, c, cq, vol);
-      int mhi = 0, nlo = g.nb;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        s_c[wib][lane][i] = (int)c[i];
-        s_cq[wib][lane][i] = (int)cq[i];
-        mhi = max(mhi, (int)occ[c[i]]);
-        nlo = min(nlo, (int)empq[cq[i]]);
-      }
-      mhi = min(mhi, q.hi);
-      nlo = max(nlo, q.lo);
-      const int nm = mhi - q.lo, nn = q.hi - nlo;
-      cnt = (nm > 0 && nn > 0) ? nm * nn : 0;
-      s_vol[wib][lane] = (T)vol;
-      s_nlo[wib][lane] = nlo;
-      s_nn[wib][lane] = nn;
-    }
-    int pre = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(kFull, pre, o);
-      if (lane >= o) pre += v;
-    }
-    s_pre[wib][lane + 1] = pre;
-    if (lane == 0) s_pre[wib][0] = 0;
-    const int total = __shfl_sync(kFull, pre, 31);
-    __syncwarp();
-    int l = 0;
-    auto item = [&](int it) {
-      while (s_pre[wib][l + 1] <= it) ++l;
-      const int loc = it - s_pre[wib][l];
-      const int nn = s_nn[wib][l];
-      const int mo = div_small(loc, nn, q.hi - q.lo);
-      const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
-      if (q.gamma && m == n) return;
-      // band pair: a = e^m_k - eF, D = D0 + e (e_0 = 0).  Mixed path: energies as FP32
-      // hi + lo pairs, so that D0 (hi + lo) and the corner offsets e come out to full FP32
-      // relative precision whatever the size of a and b
-      T a[4], e[4], f[4];
-      T D0h = T(0), D0l = T(0);
-      T amin = T(1e30), bmax = T(-1e30);
-      if constexpr (FP64) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
-          a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
-          const double b = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
-          e[i] = b - a[i];
-          amin = a[i] < amin ? a[i] : amin;
-          bmax = b > bmax ? b : bmax;
-        }
-      } else {
-        float al[4], bh[4], bl[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const long long ik = (long long)s_c[wib][l][i] * g.nb + m, iq = (long long)s_cq[wib][l][i] * g.nb + n;
-          a[i] = ((const float *)Ek)[ik];
-          al[i] = Eklo[ik];
-          bh[i] = ((const float *)Ekq)[iq];
-          bl[i] = Ekqlo[iq];
-          amin = a[i] < amin ? a[i] : amin;
-          bmax = bh[i] > bmax ? bh[i] : bmax;
-        }
-        float sv, tv;
-        two_diff(bh[0], a[0], sv, tv);
-        const float corr = tv + (bl[0] - al[0]);
-        D0h = sv + corr;
-        D0l = corr - (D0h - sv);
-        e[0] = 0.0f;
-#pragma unroll
-        for (int i = 1; i < 4; ++i) {
-          float sa, ta, sb, tb;
-          two_diff(a[i], a[0], sa, ta);
-          two_diff(bh[i], bh[0], sb, tb);
-          e[i] = (sb - sa) + ((tb - ta) + ((bl[i] - bl[0]) - (al[i] - al[0])));
-        }
-      }
-      if (!(amin < T(0) && bmax > T(0))) return;
-      const T *W2t = (const T *)W2;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
-      const T vol = s_vol[wib][l];
-      carve2_off<T>(a, e, D0h, f, [&](T r, T ee[4], T ff[4]) {
-        sort4(ee, ff);
-        ++npieces;
-        if (!(D0h + ee[3] > T(0))) return;
-        if constexpr (FP64) {
-          T d[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
-          __syncwarp();
-          int K = 0;
-          if (lane == 0) K = far_moments<T, KM>(d, ff, s_am[wib][0]);
-          K = __shfl_sync(kFull, K, 0);
-          __syncwarp();
-          eval_piece(ee, ff, vol * r, D0h, D0l, s_am[wib][0], K);
-        } else {
-          if (lane == 0) {  // every lane holds the same piece
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              s_pe[wib][npb][i] = ee[i];
-              s_pf[wib][npb][i] = ff[i];
-            }
-            s_pv[wib][npb][0] = vol * r;
-            s_pv[wib][npb][1] = D0h;
-            s_pv[wib][npb][2] = D0l;
-          }
-          ++npb;
-        }
-      });
-    };
-    for (int it = 0;; ++it) {  // warp-uniform; the pass after the last item flushes the buffer
-      const bool last = it >= total;
-      if (!last) item(it);
-      if constexpr (!FP64) {
-        if (last || npb > PB - 9) flush();  // an item adds at most 9 pieces
-      }
-      if (last) break;
-    }
-    __syncwarp();
-    for (int iw = lane; iw < nw; iw += 32) {
-      db.partR[(long long)batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
-      db.partI[(long long)batch * nw + iw] = (double)sI[wib][iw] + (double)cI[wib][iw];
-    }
-    __syncwarp();
-  }
-  if (counters) {
-    unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(kFull, a, o);
-      b += __shfl_xor_sync(kFull, b, o);
-    }
-    if (lane == 0) {
-      atomicAdd(&counters[0], a / 32);  // every lane counted each piece
-      atomicAdd(&counters[1], b);
-    }
-  }
-}
-
 // ---------------------------------------------------------------- Gamma DOS term
 __global__ void __launch_bounds__(kThreads) k_dos(Grid g, Tet tet, const double *__restrict__ E, int lo,
                                                    int hi, double *__restrict__ partial) {
@@ -917,6 +485,7 @@ constexpr int kRedThreads = 1024;
 __global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict__ partial, int nblocks, int nw,
                                                          double scale, const double *__restrict__ dos, int ndos,
                                                          const double *__restrict__ omega,
+                                                         const double *__restrict__ extra,
                                                          double *__restrict__ out) {
   const int k = blockIdx.x;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, sd = 0.0;
@@ -939,7 +508,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict
   if (threadIdx.x < 32) {
     v = red[threadIdx.x];
     v = warp_sum(v);
-    if (threadIdx.x == 0) out[k] = scale * v;
+    if (threadIdx.x == 0) out[k] = scale * (extra ? v + extra[k] : v);
   }
 }
 
@@ -947,7 +516,6 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict
 
 // ======================================================================= launchers
 int static_blocks() { return kStaticBlocks; }
-int dynamic_max_nw() { return kNWPass; }
 
 __global__ void __launch_bounds__(kThreads) k_c128_to_c64(const double2 *__restrict__ in, float2 *__restrict__ out,
                                                          long long n) {
@@ -1053,33 +621,6 @@ cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const v
   return cudaGetLastError();
 }
 
-cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
-                           const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
-                           const double *omega, int nw, const DynBufs &db, int nblocks,
-                           unsigned long long *counters, cudaStream_t s, const float *Eklo,
-                           const float *Ekqlo) {
-  if (nw > kNWPass || nw <= 0) return cudaErrorInvalidValue;
-  if (!fp64 && (!Eklo || !Ekqlo)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(db.next, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  if (fp64)
-    k_dynamic<true><<<nblocks, kDynThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db,
-                                                     Eklo, Ekqlo, counters);
-  else
-    k_dynamic<false><<<nblocks, kDynThreads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db,
-                                                      Eklo, Ekqlo, counters);
-  return cudaGetLastError();
-}
-
-int dynamic_max_ctas_per_sm(int fp64) {
-  int nb = 0;
-  cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<true>, kDynThreads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dynamic<false>, kDynThreads, 0);
-  return (e != cudaSuccess || nb < 1) ? 1 : nb;
-}
-
-int dynamic_persistent_blocks(int fp64) { return dynamic_max_ctas_per_sm(fp64) * device_sms(); }
-
 cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,
                        int nblocks, cudaStream_t s) {
   k_dos<<<nblocks, kThreads, 0, s>>>(g, tet, E, lo, hi, partial);
@@ -1087,8 +628,8 @@ cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, i
 }
 
 cudaError_t launch_reduce(const double *partial, int nblocks, int nw, double scale, const double *dos,
-                          int ndos, const double *omega, double *out, cudaStream_t s) {
-  k_reduce<<<nw, kRedThreads, 0, s>>>(partial, nblocks, nw, scale, dos, ndos, omega, out);
+                          int ndos, const double *omega, double *out, cudaStream_t s, const double *extra) {
+  k_reduce<<<nw, kRedThreads, 0, s>>>(partial, nblocks, nw, scale, dos, ndos, omega, extra, out);
   return cudaGetLastError();
 }
 

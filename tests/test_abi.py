@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(lib):
     assert ct.sizeof(lib.chi0_kgrid_t) == 4 * 3 + 4 * 3 + 8 + 8 + 4 + 4 + 8
     assert ct.sizeof(lib.chi0_q_t) == 12 + 4 + 8 + 8 + 8 + 4 + 4
     assert ct.sizeof(lib.chi0_opts_t) == 4 * 4 + 8 + 4 * 2 + 8 + 4 + 4 + 8 + 32
-    assert ct.sizeof(lib.chi0_stats_t) == 8 * 8 + 8 * 8 + 5 * 8
+    assert ct.sizeof(lib.chi0_stats_t) == 8 * 8 + 8 * 8 + 6 * 8
 
 
 def test_opts_default(lib):

@@ -148,6 +148,42 @@ def test_dynamic_tb(C, O, prec):
     assert nerr(gi, np.array(ref_i)) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dynamic_far_field_boxes(C, O, prec):
+    """A 12^3 mesh and 96 frequencies in [0, 2]: most final tetrahedra are narrow next to
+    u_max/32, so their principal-value terms go to boxes of D (fine boxes inside the frequency
+    range, geometric ones beyond it); every frequency against the oracle, and the counter
+    shows that the boxes were used."""
+    W = wl.tiny_tb(n=12, norb=4, nq=2, seed=wl.SEED_BASE + 49)
+    omega = np.linspace(0.0, 2.0, 96)
+    ref_r, ref_i = zip(*[O.chi0_q(W, q, omega=omega) for q in W.qs])
+    P = C.Plan(W, precision=prec, device=True, profile=True)
+    gr, gi = P.dynamic(omega)
+    cnt = P.counters()
+    P.close()
+    assert cnt["box_pieces"] > 0.25 * cnt["pieces"], cnt
+    assert nerr(gr.cpu().numpy(), np.array(ref_r)) < TOL[prec]
+    assert nerr(gi.cpu().numpy(), np.array(ref_i)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dynamic_boxes_match_direct_evaluation(C, prec):
+    """The same q on 64 frequencies, once as one pass (boxes stand in for far frequencies) and
+    once one frequency per call (a single frequency never uses boxes): the two algorithms
+    agree to the form's tolerance, negative frequencies included."""
+    W = wl.tiny_tb(n=10, norb=5, nq=1, seed=wl.SEED_BASE + 50)
+    omega = np.concatenate([np.linspace(0.0, 2.5, 60), [-0.3, -1.1, -2.0, 2.2]])
+    P = C.Plan(W, precision=prec, device=True, profile=True)
+    gr, gi = P.dynamic(omega)
+    assert P.counters()["box_pieces"] > 0
+    dr, di = zip(*[P.dynamic(omega[i:i + 1]) for i in range(omega.size)])
+    P.close()
+    dr = np.concatenate([x.cpu().numpy() for x in dr], axis=1)
+    di = np.concatenate([x.cpu().numpy() for x in di], axis=1)
+    assert nerr(gr.cpu().numpy(), dr) < TOL[prec]
+    assert nerr(gi.cpu().numpy(), di) < TOL[prec]
+
+
 def test_dynamic_many_frequencies_and_gamma(C, O):
     # 300 frequencies: two passes of the frequency loop; Gamma adds N(eF) at w = 0
     W = wl.tiny_tb(n=6, norb=3, nq=0, seed=wl.SEED_BASE + 48)
