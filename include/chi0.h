@@ -281,6 +281,21 @@ int chi0_tune(chi0_plan_t *plan, const chi0_q_t *q, int nq, const double *omega,
 int chi0_static_noalloc(const chi0_kgrid_t *kgrid, chi0_band_window_t window, const chi0_opts_t *opts,
                         const chi0_q_t *q, int nq, double *chi);
 
+/* Measured arithmetic peak of the current device (a measurement helper for rooflines; the
+ * paper has no counterpart).  kind: CHI0_PEAK_FP32_FMA / CHI0_PEAK_FP64_FMA (fused multiply-add
+ * chains on the CUDA cores of every SM), CHI0_PEAK_TF32_MMA / CHI0_PEAK_BF16_MMA (back-to-back
+ * tcgen05.mma, M = 128, N = 256, one 32-byte K step, from shared memory, one CTA per SM).
+ * iters: loop length (the run should last some milliseconds: about 2e5 for the FMA kinds,
+ * 2e5 for the MMA kinds).  One untimed warm-up launch, then one launch timed with CUDA events on
+ * the legacy default stream; *tflops = 2 flop per FMA (or M N K per MMA) / time, *ms the time.
+ * Synchronizes the device; allocates and frees a few bytes.  Errors: CHI0_EINVAL, CHI0_ENOMEM,
+ * CHI0_ECUDA (including a bounded tensor-core wait that ran out). */
+#define CHI0_PEAK_FP32_FMA 0
+#define CHI0_PEAK_FP64_FMA 1
+#define CHI0_PEAK_TF32_MMA 2
+#define CHI0_PEAK_BF16_MMA 3
+int chi0_peak(int kind, int iters, double *tflops, double *ms);
+
 /* Copies the plan's accumulated counters into *stats.  CHI0_EINVAL on NULL. */
 int chi0_plan_stats(const chi0_plan_t *plan, chi0_stats_t *stats);
 

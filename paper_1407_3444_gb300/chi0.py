@@ -92,7 +92,8 @@ _lib = None
 
 # every entry point declared in include/chi0.h (checked by the ABI test)
 EXPORTS = ["chi0_opts_default", "chi0_plan", "chi0_static", "chi0_dynamic", "chi0_plan_stats",
-           "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune"]
+           "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune", "chi0_peak"]
+CHI0_PEAK_FP32_FMA, CHI0_PEAK_FP64_FMA, CHI0_PEAK_TF32_MMA, CHI0_PEAK_BF16_MMA = 0, 1, 2, 3
 CHI0_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -127,6 +128,8 @@ def lib():
         L.chi0_tune.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
                                 ct.c_void_p, ct.POINTER(chi0_tune_t)]
         L.chi0_tune.restype = ct.c_int
+        L.chi0_peak.argtypes = [ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+        L.chi0_peak.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -191,6 +194,13 @@ def chi0_static_noalloc(kgrid: chi0_kgrid_t, window: chi0_band_window_t, opts: c
     """Static chi0 with device-resident inputs/outputs and no device allocation (the
     library's fixed work array); see include/chi0.h."""
     _check(lib().chi0_static_noalloc(ct.byref(kgrid), window, ct.byref(opts), q, nq, chi_ptr), None)
+
+
+def chi0_peak(kind: int, iters: int):
+    """Measured peak (TFLOP/s, ms) of one arithmetic kind on the current device."""
+    tf, ms = ct.c_double(), ct.c_double()
+    _check(lib().chi0_peak(int(kind), int(iters), ct.byref(tf), ct.byref(ms)), None)
+    return tf.value, ms.value
 
 
 # --------------------------------------------------------------- convenience wrapper

@@ -60,7 +60,7 @@ constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed pe
 template <bool FP64> struct DynShape {
   static constexpr int threads = FP64 ? 64 : 128;
   static constexpr int warps = threads / 32;
-  static constexpr int PB = FP64 ? 8 : 16;   // final tetrahedra buffered per warp
+  static constexpr int PB = FP64 ? 10 : 16;  // final tetrahedra buffered per warp (>= 9 + 1)
   static constexpr int KM = FP64 ? 64 : 32;  // own far-field moments kept per buffered piece
   static constexpr int KF = FP64 ? 40 : 24;  // moments of a fine box   (truncation 2^-KF)
   static constexpr int KG = FP64 ? 22 : 12;  // moments of a geometric box ((2/9)^KG)
@@ -271,6 +271,8 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   using S = DynShape<FP64>;
   constexpr int W = S::warps, PB = S::PB, KM = S::KM, KF = S::KF, KG = S::KG;
   constexpr int NS = box_slots<FP64>();
+  // the buffer is flushed once it holds more than PB - 9 pieces, and one item adds at most 9
+  static_assert(PB >= 10, "piece buffer must hold one item's nine pieces after a non-flushing item");
   __shared__ int s_c[W][32][4], s_cq[W][32][4];
   __shared__ T s_vol[W][32];
   __shared__ int s_nlo[W][32], s_nn[W][32], s_pre[W][33];

@@ -139,6 +139,8 @@ int overlap_tc_max_corners(int w, int norb, int mode);  // corners per MMA round
 // gcap > 0: at most gcap corners per MMA round (autotuner candidates)
 cudaError_t launch_overlap_tc(const Grid &g, const void *C32, int dtype, const Q &q, float *W2, int mode,
                               long long budget, int test_stall, int gcap, int *err, cudaStream_t s);
+// tensor-core throughput (TFLOP/s) of `iters` back-to-back MMAs per SM, M = 128, N = 256
+cudaError_t tc_peak(int mode, int iters, double *tflops, double *ms);
 // resident CTAs per SM of the weight kernels (occupancy limit) and SMs of the device
 int static_max_ctas_per_sm(int fp64, int variant);
 int static_variants(int fp64);                      // block shapes of the static weight kernel

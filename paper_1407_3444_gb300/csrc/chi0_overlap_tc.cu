@@ -427,7 +427,90 @@ cudaError_t launch_tc(const Grid &g, const float2 *Ck, const CTq *Cb, int explic
   return cudaGetLastError();
 }
 
+// Tensor-core throughput: one CTA per SM issues `iters` MMAs (M = 128, N = 256, one K step of
+// 32 bytes) from fixed zeroed shared-memory operands into one tensor-memory accumulator, then
+// commits them and waits (bounded).  The large shared-memory request keeps one CTA per SM.
+constexpr int kPeakSmem = 160 * 1024;
+__global__ void __launch_bounds__(128, 1) k_tc_peak(int mode, int iters, long long budget, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int kN = 256;
+  unsigned char *sA = smem, *sB = smem + kTcM * 32;
+  uint64_t *bar = (uint64_t *)(sB + kN * 32);
+  uint32_t *tslot = (uint32_t *)(sB + kN * 32 + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < (kTcM + kN) * 32 / 16; i += blockDim.x) ((uint4 *)smem)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint64_t da = sdesc(smem_u32(sA), 128, 2 * 128), db = sdesc(smem_u32(sB), 128, 2 * 128);
+    const uint32_t id = idesc(mode, kN);
+    for (int i = 0; i < iters; ++i) mma(tmem, da, db, id, i > 0 ? 1u : 0u, mode);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+  }
+  const int got = mbar_wait(smem_u32(bar), 0, budget) ? 1 : 0;
+  if (!__syncthreads_and(got)) {
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(smem_u32(bar), 0, budget);  // the MMAs may still run: wait once more, bounded
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN) : "memory");
+}
+
 }  // namespace
+
+cudaError_t tc_peak(int mode, int iters, double *tflops, double *ms_out) {
+  int *err = nullptr;
+  cudaError_t e = cudaMalloc(&err, sizeof(int));
+  if (e != cudaSuccess) return e;
+  cudaMemset(err, 0, sizeof(int));
+  e = cudaFuncSetAttribute(k_tc_peak, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakSmem);
+  if (e != cudaSuccess) {
+    cudaFree(err);
+    return e;
+  }
+  const int sms = device_sms();
+  const long long budget = 1LL << 32;  // about two seconds: far above the run's length
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_tc_peak<<<sms, 128, kPeakSmem>>>(mode, iters / 8 + 1, budget, err);  // warm-up
+  cudaEventRecord(e0);
+  k_tc_peak<<<sms, 128, kPeakSmem>>>(mode, iters, budget, err);
+  cudaEventRecord(e1);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(err);
+  if (e != cudaSuccess) return e;
+  if (herr) return cudaErrorTimeout;
+  const double kel = mode == TC_TF32 ? 8.0 : 16.0;  // K elements of one 32-byte K step
+  const double flops = 2.0 * kTcM * 256.0 * kel * (double)iters * sms;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  *ms_out = ms;
+  return cudaSuccess;
+}
 
 size_t overlap_tc_smem(int w, int norb, int mode) {
   const TcShape sh = tc_shape(w, norb, mode, 0);
