@@ -15,15 +15,17 @@
 //     = v 6 k!/(k+4)! sum_j f_j h_k(e_1..e_4, e_j)  (e = (d - C_b)/R_b; Dirichlet moments of
 //     the simplex, h_k the complete homogeneous symmetric polynomials);
 //   1/(D -+ u) = 1/(C_b -+ u) sum_k (-z)^k eps^k,  z = R_b/(C_b -+ u),  |z| <= 1/2 where the
-//     box stands in for its pieces, so the box's share of Re(u) is sum_k M_k (-z)^k/(C_b -+ u),
+//     box stands in for its pieces (1/3 in FP64), so the box's share of Re(u) is
+//     sum_k M_k (-z)^k/(C_b -+ u),
 //     evaluated once per (box, frequency) in FP64 after the moments of all warps are summed.
 //
 // Boxes (rebuilt each pass from u_max = max |w| of the pass):
 //   fine boxes, levels l = 0..3 of width w_l = (u_max/32) 2^l: centres (j + 1/2) w_l, radius
 //     w_l; a piece of half-width s <= w_l/2 whose centre lies in [j w_l, (j+1) w_l) fits.  For a
-//     frequency with |C_b - u| < 2 R_b (the - term) or C_b + u < 2 R_b (the + term) the box does
-//     not stand in: its pieces evaluate that term themselves (own far-field series about their
-//     midpoint, or the divided-difference table near their knots);
+//     frequency with |C_b - u| < F R_b (the - term) or C_b + u < F R_b (the + term), F = 2 in
+//     the FP32 kernel and 3 in the FP64 kernel (|z| <= 1/F elsewhere), the box does not stand
+//     in: its pieces evaluate that term themselves (own far-field series about their midpoint,
+//     or the divided-difference table near their knots);
 //   geometric boxes past u_max: x = c - u_max in [x_b, 1.25 x_b), x_0 = 5 u_max/32, centre
 //     u_max + 1.125 x_b, radius x_b/4, pieces with s <= x_b/8; every frequency of the pass is
 //     far (|z| <= 2/9), so their pieces evaluate nothing per frequency;
@@ -31,10 +33,16 @@
 // Every (piece, frequency, term) is taken exactly once, either by the piece or by its box;
 // the predicate that decides is computed in the kernels' precision from the same table.
 //
-// The moments of a warp's pieces go to per-warp sums in shared memory (one lane per moment
-// index, no atomics), added after every batch into per-warp FP64 partials in global memory.
-// Batches are assigned to warps statically (batch = warp + k * warps), and every sum runs in
-// a fixed order, so results are bitwise reproducible for a given launch shape.
+// Work layout.  A warp takes a batch of 32 tetrahedra; the batch's (m, n) items are sorted
+// into whole-tetrahedron and cut lists and carved 32 at a time, one item per lane, in warp-
+// uniform steps that emit at most one final tetrahedron per lane.  Each piece finds its box
+// and moments in its lane; the moments go to per-warp sums in shared memory (one lane per
+// moment index, pieces in lane order: no atomics), added after every batch into per-warp FP64
+// partials in global memory.  Pieces that evaluate frequencies themselves (fine boxes, or no
+// box) go to a per-warp ring queue that the whole warp evaluates, lanes owning frequencies,
+// over the frequency range its box leaves to it.  Batches are assigned to warps statically
+// (batch = warp + k * warps), and every sum runs in a fixed order, so results are bitwise
+// reproducible for a given launch shape.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -60,9 +68,10 @@ constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed pe
 template <bool FP64> struct DynShape {
   static constexpr int threads = FP64 ? 64 : 128;
   static constexpr int warps = threads / 32;
-  static constexpr int PB = FP64 ? 10 : 16;  // final tetrahedra buffered per warp (>= 9 + 1)
-  static constexpr int KM = FP64 ? 64 : 32;  // own far-field moments kept per buffered piece
-  static constexpr int KF = FP64 ? 40 : 24;  // moments of a fine box   (truncation 2^-KF)
+  static constexpr int DC = FP64 ? 16 : 32;  // queued pieces evaluated per round
+  static constexpr int KM = FP64 ? 64 : 32;  // own far-field moments kept per queued piece
+  static constexpr int NF = FP64 ? 3 : 2;    // a fine box stands in beyond NF radii
+  static constexpr int KF = FP64 ? 32 : 24;  // moments of a fine box   (truncation NF^-KF)
   static constexpr int KG = FP64 ? 22 : 12;  // moments of a geometric box ((2/9)^KG)
 };
 
@@ -189,7 +198,7 @@ template <typename T> __device__ __forceinline__ void box_moments(const T e[4], 
 // only near themselves; geometric boxes always.  Same expression in both kernels.
 template <typename T> __device__ __forceinline__ bool box_far(T C, T R, int b, T om, int term) {
   if (b >= kBoxFine) return true;
-  const T r2 = R + R;
+  const T r2 = R * T(DynShape<sizeof(T) == 8>::NF);
   if (term) return !(C + om < r2);
   return !(tabs(C - om) < r2);
 }
@@ -269,27 +278,34 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
               unsigned long long *__restrict__ counters) {
   using T = typename std::conditional<FP64, double, float>::type;
   using S = DynShape<FP64>;
-  constexpr int W = S::warps, PB = S::PB, KM = S::KM, KF = S::KF, KG = S::KG;
+  constexpr int W = S::warps, KM = S::KM, KF = S::KF, KG = S::KG, DC = S::DC;
+  constexpr int QC = 64;  // queue of final tetrahedra that evaluate frequencies themselves
   constexpr int NS = box_slots<FP64>();
-  // the buffer is flushed once it holds more than PB - 9 pieces, and one item adds at most 9
-  static_assert(PB >= 10, "piece buffer must hold one item's nine pieces after a non-flushing item");
+  constexpr int KU = DC * KM > 32 * KF ? DC * KM : 32 * KF;  // per-warp scratch (T elements)
+  static_assert(QC >= DC + 32, "one carving step adds at most 32 queued pieces");
   __shared__ int s_c[W][32][4], s_cq[W][32][4];
   __shared__ T s_vol[W][32];
   __shared__ int s_nlo[W][32], s_nn[W][32], s_pre[W][33];
-  // buffered final tetrahedra: offsets e from D0 (sorted), values f, (weight, D0h, D0l), their
-  // own far-field moments (K of them) and box moments (box id; -1 none)
-  __shared__ T s_pe[W][PB][4], s_pf[W][PB][4], s_pv[W][PB][3];
-  __shared__ T s_am[W][PB][KM], s_bm[W][PB][KF];
-  __shared__ int s_pk[W][PB], s_bx[W][PB];
+  __shared__ int s_list[W][2][64], s_nl[W][2];  // item lists (whole / cut): l << 24 | m << 12 | n
+  // scratch: box moments of one carving step's pieces (32 x KF), or the own far-field moments
+  // of the queued pieces being evaluated (DC x KM)
+  __shared__ T s_scr[W][KU];
+  __shared__ int s_pk[W][DC];
+  // ring queue: offsets e from D0 (sorted), values f, (weight, D0h, D0l), box
+  __shared__ T s_qe[W][QC][4], s_qf[W][QC][4], s_qv[W][QC][3];
+  __shared__ int s_qb[W][QC];
   __shared__ T sR[W][kNWPass], sI[W][kNWPass];
   __shared__ T cR[W][kNWPass], cI[W][kNWPass];  // compensation terms
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
   __shared__ short s_near[W][kNearCap];
+  __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
   extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   T *acc = (T *)s_dyn + (size_t)wib * NS;
+  T *scr = s_scr[wib];
   const int w = q.hi - q.lo;
   const long long nbatch = (g.ntet + 31) / 32;
   const long long gwarp = (long long)blockIdx.x * W + wib, nwarps = (long long)gridDim.x * W;
@@ -305,20 +321,47 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   }
   for (int i = lane; i < NS; i += 32) acc[i] = T(0);
   __syncthreads();
+  // frequency ranges of the fine boxes: contiguous when |w| ascends along the grid (an
+  // interval for the - term, a prefix for the + term); otherwise the whole grid, the
+  // predicate deciding each frequency
+  bool sorted = true;
+  for (int i = threadIdx.x; i + 1 < nw; i += blockDim.x) sorted = sorted && tabs(s_w[i]) <= tabs(s_w[i + 1]);
+  sorted = __syncthreads_and(sorted) != 0;
+  for (int b = threadIdx.x; b < kBoxFine; b += blockDim.x) {
+    int lo = 0, hi = nw;
+    if (sorted) {
+      lo = nw;
+      hi = 0;
+      for (int i = 0; i < nw; ++i) {
+        const T om = tabs(s_w[i]);
+        if (!box_far(s_tab.C[b], s_tab.R[b], b, om, 0) || !box_far(s_tab.C[b], s_tab.R[b], b, om, 1)) {
+          lo = lo < i ? lo : i;
+          hi = i + 1;
+        }
+      }
+      if (hi <= lo) lo = hi = 0;
+    }
+    s_rng[b][0] = (short)lo;
+    s_rng[b][1] = (short)hi;
+  }
+  __syncthreads();
   const bool boxes = s_tab.on != 0;
   int nfp64 = 0, npieces = 0, nboxed = 0;
-  // one final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr, own
-  // far-field moments am[0..K)) on the frequencies its box (b >= 0) does not stand in for
+  int qh = 0, qt = 0;  // ring queue head and tail (warp-uniform)
+  // one queued final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr,
+  // own far-field moments am[0..K)) on the frequencies its box (b >= 0) leaves to it, or on
+  // all of them (b < 0); lanes own frequencies
   auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b) {
     T d[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
     const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
     const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
+    const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
     // far field for both terms (Horner on the moments); near-field frequencies are
     // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
     unsigned nearm = 0u, nearp = 0u;
-    for (int iw = lane, itn = 0; iw < nw; iw += 32, ++itn) {
+    for (int iw = lo + lane, itn = 0; iw < hi; iw += 32, ++itn) {
       const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
       T re = T(0);
       if (b < 0 || !box_far(Cb, Rb, b, om, 1)) {
@@ -336,13 +379,13 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
     // near field: compact the (frequency, term) pairs of the warp into a list
     int nlist = 0;
-    const int nit = (nw + 31) >> 5;
+    const int nit = (hi - lo + 31) >> 5;
     for (int itn = 0; itn < nit; ++itn) {
 #pragma unroll
       for (int sgn = 0; sgn < 2; ++sgn) {
         const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
         const unsigned bal = __ballot_sync(kFull, mine);
-        if (mine) s_near[wib][nlist + __popc(bal & ((1u << lane) - 1u))] = (short)((itn * 32 + lane) * 2 + sgn);
+        if (mine) s_near[wib][nlist + __popc(bal & lt)] = (short)((lo + itn * 32 + lane) * 2 + sgn);
         nlist += __popc(bal);
       }
       if (nlist > kNearCap - 64) {  // flush a full list
@@ -358,57 +401,200 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
                     tau, nfp64);
     __syncwarp();
   };
-  // buffered pieces: box and moments one piece per lane, box sums one moment per lane, then
-  // each piece on the frequencies its box leaves to it
-  int npb = 0;
-  auto flush = [&]() {
-    __syncwarp();  // lane 0's buffer writes are visible to every lane
-    if (lane < npb) {
+  // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then each piece
+  // on its frequencies with the whole warp
+  auto drain = [&](int n) {
+    if (lane < n) {
+      const int sl = (qh + lane) % QC;
+      T d[4], ff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        d[i] = s_qv[wib][sl][1] + s_qe[wib][sl][i];
+        ff[i] = s_qf[wib][sl][i];
+      }
+      s_pk[wib][lane] = far_moments<T, KM>(d, ff, scr + lane * KM);
+    }
+    __syncwarp();
+    for (int p = 0; p < n; ++p) {
+      const int sl = (qh + p) % QC;
       T ee[4], ff[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        ee[i] = s_pe[wib][lane][i];
-        ff[i] = s_pf[wib][lane][i];
+        ee[i] = s_qe[wib][sl][i];
+        ff[i] = s_qf[wib][sl][i];
       }
-      const T vr = s_pv[wib][lane][0], D0h = s_pv[wib][lane][1], D0l = s_pv[wib][lane][2];
+      eval_piece(ee, ff, s_qv[wib][sl][0], s_qv[wib][sl][1], s_qv[wib][sl][2], scr + p * KM, s_pk[wib][p],
+                 s_qb[wib][sl]);
+    }
+    qh += n;
+    __syncwarp();
+  };
+  // one carving step: at most one final tetrahedron per lane (has).  Its box and moments, the
+  // box sums (one moment index per lane, pieces in lane order), and the queue for pieces that
+  // evaluate frequencies themselves.
+  auto piece = [&](bool has, T ee[4], T ff[4], T vr, T D0h, T D0l) {
+    int b = -1;
+    if (has) {
+      sort4(ee, ff);
+      ++npieces;
+      has = D0h + ee[3] > T(0);
+    }
+    if (has) {
       const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
-      const int b = boxes ? box_of(c, half, s_tab) : -1;
-      s_bx[wib][lane] = b;
-      nboxed += b >= 0;
+      b = boxes ? box_of(c, half, s_tab) : -1;
       if (b >= 0) {
         const T ri = T(1) / s_tab.R[b], base = (D0h - s_tab.C[b]) + D0l;
         T e[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) e[i] = (base + ee[i]) * ri;
-        box_moments(e, ff, vr, s_bm[wib][lane], b < kBoxFine ? KF : KG);
-      }
-      if (b < kBoxFine) {  // the piece evaluates some frequencies itself
-        T d[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
-        s_pk[wib][lane] = far_moments<T, KM>(d, ff, s_am[wib][lane]);
+        box_moments(e, ff, vr, scr + lane * KF, b < kBoxFine ? KF : KG);
+        ++nboxed;
       }
     }
     __syncwarp();
-    for (int p = 0; p < npb; ++p) {  // lane k adds moment k: no two lanes share a slot
-      const int b = s_bx[wib][p];
-      if (b < 0) continue;
-      const int K = b < kBoxFine ? KF : KG, base = slot_base<FP64>(b);
-      for (int k = lane; k < K; k += 32) acc[base + k] += s_bm[wib][p][k];
+    unsigned mask = __ballot_sync(kFull, has && b >= 0);
+    while (mask) {  // warp-uniform
+      const int p = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const int bp = __shfl_sync(kFull, b, p);
+      const int K = bp < kBoxFine ? KF : KG, base = slot_base<FP64>(bp);
+      for (int k = lane; k < K; k += 32) acc[base + k] += scr[p * KF + k];
     }
-    for (int p = 0; p < npb; ++p) {
-      const int b = s_bx[wib][p];
-      if (b >= kBoxFine) continue;
-      T ee[4], ff[4];
+    const bool queue = has && b < kBoxFine;
+    const unsigned qm = __ballot_sync(kFull, queue);
+    if (queue) {
+      const int sl = (qt + __popc(qm & lt)) % QC;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        ee[i] = s_pe[wib][p][i];
-        ff[i] = s_pf[wib][p][i];
+        s_qe[wib][sl][i] = ee[i];
+        s_qf[wib][sl][i] = ff[i];
       }
-      eval_piece(ee, ff, s_pv[wib][p][0], s_pv[wib][p][1], s_pv[wib][p][2], s_am[wib][p], s_pk[wib][p], b);
+      s_qv[wib][sl][0] = vr;
+      s_qv[wib][sl][1] = D0h;
+      s_qv[wib][sl][2] = D0l;
+      s_qb[wib][sl] = b;
     }
+    qt += __popc(qm);
     __syncwarp();
-    npb = 0;
+    while (qt - qh >= DC) drain(DC);
+  };
+  // item data of (tetrahedron l of the batch, bands m, n): a = e^m_k - eF, D = D0 + e (e_0 = 0)
+  // and |M|^2 at the corners.  Mixed path: energies as FP32 hi + lo pairs, so that D0 (hi + lo)
+  // and the corner offsets e come out to full FP32 relative precision whatever the size of a, b
+  auto load_item = [&](int l, int m, int n, T a[4], T e[4], T f[4], T &D0h, T &D0l) {
+    D0h = T(0);
+    D0l = T(0);
+    if constexpr (FP64) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
+        a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
+        e[i] = (((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef) - a[i];
+      }
+    } else {
+      float al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const long long ik = (long long)s_c[wib][l][i] * g.nb + m, iq = (long long)s_cq[wib][l][i] * g.nb + n;
+        a[i] = ((const float *)Ek)[ik];
+        al[i] = Eklo[ik];
+        bh[i] = ((const float *)Ekq)[iq];
+        bl[i] = Ekqlo[iq];
+      }
+      float sv, tv;
+      two_diff(bh[0], a[0], sv, tv);
+      const float corr = tv + (bl[0] - al[0]);
+      D0h = sv + corr;
+      D0l = corr - (D0h - sv);
+      e[0] = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 4; ++i) {
+        float sa, ta, sb, tb;
+        two_diff(a[i], a[0], sa, ta);
+        two_diff(bh[i], bh[0], sb, tb);
+        e[i] = (sb - sa) + ((tb - ta) + ((bl[i] - bl[0]) - (al[i] - al[0])));
+      }
+    }
+    const T *W2t = (const T *)W2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
+  };
+  // up to 32 items, one per lane: both carvings of Sec. II as warp-uniform loops over the
+  // pieces of the first and second cut, one final tetrahedron per lane and step
+  auto carve_items = [&](bool has, int l, int m, int n) {
+    T a[4] = {T(0), T(0), T(0), T(0)}, e[4] = {T(0), T(0), T(0), T(0)}, f[4] = {T(0), T(0), T(0), T(0)};
+    T D0h = T(0), D0l = T(0);
+    if (has) load_item(l, m, n, a, e, f, D0h, D0l);
+    const T vol = has ? s_vol[wib][l] : T(0);
+    bool whole = false;
+    if (has) {
+      const T amax = fmax(fmax(a[0], a[1]), fmax(a[2], a[3]));
+      const T bmin = fmin(fmin(a[0] + D0h + e[0], a[1] + D0h + e[1]), fmin(a[2] + D0h + e[2], a[3] + D0h + e[3]));
+      whole = amax < T(0) && bmin > T(0);  // occupied at k and empty at k+q everywhere: no cut
+    }
+    if (!__any_sync(kFull, has && !whole)) {
+      piece(whole, e, f, vol, D0h, D0l);
+      return;
+    }
+    // general case (whole items emit their one piece at the first step)
+    Vt<T> V[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) V[i] = Vt<T>{a[i], e[i], f[i]};
+    const bool cut = has && !whole;
+    Vt<T> P0[4];
+    T r0 = T(0);
+    const int n1 = cut ? cut_piece<0>(V, 0, P0, r0) : 0;
+    const int n1max = __reduce_max_sync(kFull, whole ? 1 : n1);
+#pragma unroll 1
+    for (int i1 = 0; i1 < n1max; ++i1) {
+      Vt<T> P[4];
+      T r1 = T(0);
+      bool ok1 = false;
+      if (cut && i1 < n1) {
+        cut_piece<0>(V, i1, P, r1);
+        ok1 = r1 > T(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) P[i].a += D0h;  // second-cut key -(a + e) is now -b
+      }
+      int n2 = 0;
+      if (ok1) {
+        Vt<T> Qd[4];
+        T rd;
+        n2 = cut_piece<1>(P, 0, Qd, rd);
+      }
+      const int n2max = __reduce_max_sync(kFull, (whole && i1 == 0) ? 1 : n2);
+#pragma unroll 1
+      for (int i2 = 0; i2 < n2max; ++i2) {
+        T ee[4], ff[4], vr = T(0);
+        bool okp = false;
+        if (whole) {
+          okp = i1 == 0 && i2 == 0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            ee[i] = e[i];
+            ff[i] = f[i];
+          }
+          vr = vol;
+        } else if (ok1 && i2 < n2) {
+          Vt<T> Qv[4];
+          T r2 = T(0);
+          cut_piece<1>(P, i2, Qv, r2);
+          const T r = r1 * r2;
+          okp = r > T(0);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            ee[i] = Qv[i].D > -D0h ? Qv[i].D : -D0h;  // clamped to D >= 0
+            ff[i] = Qv[i].f;
+          }
+          vr = vol * r;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) ee[i] = ff[i] = T(0);
+        }
+        piece(okp, ee, ff, vr, D0h, D0l);
+      }
+    }
   };
   bool first = true;  // this warp's first batch writes its box partials, later ones add to them
   for (long long batch = gwarp; batch < nbatch; batch += nwarps) {
@@ -440,7 +626,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       s_nlo[wib][lane] = nlo;
       s_nn[wib][lane] = nn;
     }
-    int pre = cnt;
+    int pre = cnt;  // inclusive prefix sum over the lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_up_sync(kFull, pre, o);
@@ -449,86 +635,84 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     s_pre[wib][lane + 1] = pre;
     if (lane == 0) s_pre[wib][0] = 0;
     const int total = __shfl_sync(kFull, pre, 31);
+    if (lane < 2) s_nl[wib][lane] = 0;
     __syncwarp();
-    int l = 0;
-    auto item = [&](int it) {
-      while (s_pre[wib][l + 1] <= it) ++l;
-      const int loc = it - s_pre[wib][l];
-      const int nn = s_nn[wib][l];
-      const int mo = div_small(loc, nn, q.hi - q.lo);
-      const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
-      if (q.gamma && m == n) return;
-      // band pair: a = e^m_k - eF, D = D0 + e (e_0 = 0).  Mixed path: energies as FP32
-      // hi + lo pairs, so that D0 (hi + lo) and the corner offsets e come out to full FP32
-      // relative precision whatever the size of a and b
-      T a[4], e[4], f[4];
-      T D0h = T(0), D0l = T(0);
-      T amin = T(1e30), bmax = T(-1e30);
-      if constexpr (FP64) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int ck = s_c[wib][l][i], cq = s_cq[wib][l][i];
-          a[i] = ((const double *)Ek)[(long long)ck * g.nb + m] - g.ef;
-          const double b = ((const double *)Ekq)[(long long)cq * g.nb + n] - g.ef;
-          e[i] = b - a[i];
-          amin = a[i] < amin ? a[i] : amin;
-          bmax = b > bmax ? b : bmax;
-        }
-      } else {
-        float al[4], bh[4], bl[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const long long ik = (long long)s_c[wib][l][i] * g.nb + m, iq = (long long)s_cq[wib][l][i] * g.nb + n;
-          a[i] = ((const float *)Ek)[ik];
-          al[i] = Eklo[ik];
-          bh[i] = ((const float *)Ekq)[iq];
-          bl[i] = Ekqlo[iq];
-          amin = a[i] < amin ? a[i] : amin;
-          bmax = bh[i] > bmax ? bh[i] : bmax;
-        }
-        float sv, tv;
-        two_diff(bh[0], a[0], sv, tv);
-        const float corr = tv + (bl[0] - al[0]);
-        D0h = sv + corr;
-        D0l = corr - (D0h - sv);
-        e[0] = 0.0f;
-#pragma unroll
-        for (int i = 1; i < 4; ++i) {
-          float sa, ta, sb, tb;
-          two_diff(a[i], a[0], sa, ta);
-          two_diff(bh[i], bh[0], sb, tb);
-          e[i] = (sb - sa) + ((tb - ta) + ((bl[i] - bl[0]) - (al[i] - al[0])));
-        }
+    // Items are sorted into two per-warp lists, whole-tetrahedron items and items whose
+    // tetrahedron a Fermi surface cuts, and each list is carved 32 items at a time, so that the
+    // lanes of a warp mostly run the same path.
+    auto drain_items = [&](bool final) {
+      for (;;) {  // warp-uniform
+        const int nf = s_nl[wib][0], nc = s_nl[wib][1];
+        int which;
+        if (nf >= 32) which = 0;
+        else if (nc >= 32) which = 1;
+        else if (final && nf > 0) which = 0;
+        else if (final && nc > 0) which = 1;
+        else break;
+        const int cntl = which ? nc : nf;
+        const int take = cntl < 32 ? cntl : 32;
+        int code = 0;
+        if (lane < take) code = s_list[wib][which][cntl - take + lane];
+        __syncwarp();
+        if (lane == 0) s_nl[wib][which] = cntl - take;
+        __syncwarp();
+        const unsigned u = (unsigned)code;
+        carve_items(lane < take, (int)(u >> 24), (int)((u >> 12) & 0xFFFu), (int)(u & 0xFFFu));
       }
-      if (!(amin < T(0) && bmax > T(0))) return;
-      const T *W2t = (const T *)W2;
+    };
+    for (int base = 0;; base += 32) {  // warp-uniform; the pass after the last items drains
+      const bool last = base >= total;
+      const int it = base + lane;
+      int kind = -1, code = 0;  // 0: whole tetrahedron (likely), 1: cut, -1: nothing to do
+      if (it < total) {
+        int lo_ = 0, hi_ = 32;  // owner: largest l with s_pre[l] <= it
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        f[i] = cma ? T(1) : W2t[((long long)s_c[wib][l][i] * w + (m - q.lo)) * w + (n - q.lo)];
-      const T vol = s_vol[wib][l];
-      carve2_off<T>(a, e, D0h, f, [&](T r, T ee[4], T ff[4]) {
-        sort4(ee, ff);
-        ++npieces;
-        if (!(D0h + ee[3] > T(0))) return;
-        if (lane == 0) {  // every lane holds the same piece
+        for (int step = 0; step < 5; ++step) {
+          const int mid = (lo_ + hi_) >> 1;
+          if (s_pre[wib][mid] <= it) lo_ = mid;
+          else hi_ = mid;
+        }
+        const int l = lo_;
+        const int loc = it - s_pre[wib][l];
+        const int nn = s_nn[wib][l];
+        const int mo = div_small(loc, nn, q.hi - q.lo);
+        const int m = q.lo + mo, n = s_nlo[wib][l] + (loc - mo * nn);
+        if (!(q.gamma && m == n)) {  // intraband at Gamma: replaced by the DOS limit
+          T amin = T(1e30), amax = T(-1e30), bmin = T(1e30), bmax = T(-1e30);
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            s_pe[wib][npb][i] = ee[i];
-            s_pf[wib][npb][i] = ff[i];
+            T a, b;
+            if constexpr (FP64) {
+              a = ((const double *)Ek)[(long long)s_c[wib][l][i] * g.nb + m] - g.ef;
+              b = ((const double *)Ekq)[(long long)s_cq[wib][l][i] * g.nb + n] - g.ef;
+            } else {
+              a = ((const float *)Ek)[(long long)s_c[wib][l][i] * g.nb + m];
+              b = ((const float *)Ekq)[(long long)s_cq[wib][l][i] * g.nb + n];
+            }
+            amin = a < amin ? a : amin;
+            amax = a > amax ? a : amax;
+            bmin = b < bmin ? b : bmin;
+            bmax = b > bmax ? b : bmax;
           }
-          s_pv[wib][npb][0] = vol * r;
-          s_pv[wib][npb][1] = D0h;
-          s_pv[wib][npb][2] = D0l;
+          if (amin < T(0) && bmax > T(0)) {
+            kind = (amax < T(0) && bmin > T(0)) ? 0 : 1;
+            code = (l << 24) | (m << 12) | n;
+          }
         }
-        ++npb;
-      });
-    };
-    for (int it = 0;; ++it) {  // warp-uniform; the pass after the last item flushes the buffer
-      const bool last = it >= total;
-      if (!last) item(it);
-      if (last || npb > PB - 9) flush();  // an item adds at most 9 pieces
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const unsigned bal = __ballot_sync(kFull, kind == k);
+        if (kind == k) s_list[wib][k][s_nl[wib][k] + __popc(bal & lt)] = code;
+        __syncwarp();
+        if (lane == 0) s_nl[wib][k] += __popc(bal);
+        __syncwarp();
+      }
+      drain_items(last);
       if (last) break;
     }
+    while (qt > qh) drain(qt - qh < DC ? qt - qh : DC);  // the batch's last queued pieces
+    qh = qt = 0;
     __syncwarp();
     for (int iw = lane; iw < nw; iw += 32) {
       db.partR[batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
@@ -557,9 +741,9 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       x += __shfl_xor_sync(kFull, x, o);
     }
     if (lane == 0) {
-      atomicAdd(&counters[0], a / 32);  // every lane counted each piece
+      atomicAdd(&counters[0], a);  // each lane counted its own pieces
       atomicAdd(&counters[1], b);
-      atomicAdd(&counters[3], x);       // each lane counted its own buffered pieces
+      atomicAdd(&counters[3], x);
     }
   }
 }

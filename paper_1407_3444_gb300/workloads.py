@@ -110,6 +110,35 @@ class Workload:
         return self.ntet * tot * w
 
 
+def builtin_tetra(n: Sequence[int], ids: np.ndarray):
+    """Corner indices [len(ids), 4] (int32) and fractional volumes of tetrahedra ``ids`` of the
+    periodic mesh n split 6 per cube: tetrahedron 6*cube + p = {000, e_a, e_a + e_b, 111} for
+    the p-th axis order (a, b, .) of the permutations of (0, 1, 2) in lexicographic order,
+    cube = (i0*n1 + i1)*n2 + i2.  Used to hand a sample of the builtin mesh to both sides as an
+    explicit tetrahedron list."""
+    import itertools
+    n = [int(x) for x in n]
+    ids = np.asarray(ids, dtype=np.int64)
+    cube, p = ids // 6, ids % 6
+    i2 = cube % n[2]
+    r = cube // n[2]
+    i1 = r % n[1]
+    i0 = r // n[1]
+    perms = np.array(list(itertools.permutations(range(3))))
+    a, b = perms[p, 0], perms[p, 1]
+    base = np.stack([i0, i1, i2], axis=1)
+    o1 = np.zeros_like(base)
+    o1[np.arange(len(ids)), a] = 1
+    o2 = o1.copy()
+    o2[np.arange(len(ids)), b] = 1
+    corners = []
+    for off in (np.zeros_like(base), o1, o2, np.ones_like(base)):
+        x = (base + off) % np.asarray(n)
+        corners.append((x[:, 0] * n[1] + x[:, 1]) * n[2] + x[:, 2])
+    vol = np.full(len(ids), 1.0 / (6.0 * n[0] * n[1] * n[2]))
+    return np.stack(corners, axis=1).astype(np.int32), vol
+
+
 # ----------------------------------------------------------------------------------------
 # linear algebra for the generators (LAPACK through numpy)
 # ----------------------------------------------------------------------------------------
