@@ -227,46 +227,91 @@ __device__ __forceinline__ float near_shift(float D0h, float D0l, float wh, floa
 }
 __device__ __forceinline__ double near_shift(double D0h, double, double wh, double) { return D0h - wh; }
 
-// evaluates a warp's near-field list: entry = 2 * frequency index + term; every entry of one
-// round has a different frequency index or term, and the two terms of one frequency go to
-// different rounds only through the list order, so each round adds to distinct slots.
-// Knots of the piece: d = D0 + e (sorted), D0 = D0h + D0l; term 0 is 1/(D - |w|) with knots
-// (D0 - |w|) + e, term 1 is 1/(D + |w|) with knots d + |w|.
+// knots of near-field entry ent (= 2 * frequency index + term) of a piece with knots
+// d = D0 + e (sorted), D0 = D0h + D0l: term 0 is 1/(D - |w|) with knots (D0 - |w|) + e, term 1
+// is 1/(D + |w|) with knots d + |w|
+template <bool FP64, typename T>
+__device__ __forceinline__ void near_knots(int ent, const T d[4], const T e[4], T D0h, T D0l, const T *s_w,
+                                           const T *s_wl, T x[4], bool &neg) {
+  const int iw = ent >> 1, sgn = ent & 1;
+  const T w = s_w[iw];
+  neg = w < T(0);
+  const T om = neg ? -w : w;
+  if (sgn) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = d[i] + om;
+  } else {
+    const T sh = near_shift(D0h, D0l, om, FP64 ? T(0) : (neg ? -s_wl[iw] : s_wl[iw]));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = sh + e[i];
+  }
+}
+
+// adds one near-field result: the two terms of a frequency may both be in one round, so they
+// are added one term at a time; the delta term where |w| lies inside the knot range
+template <typename T>
+__device__ __forceinline__ void near_add(int ent, T re, const T x[4], const T f[4], T vr, bool neg, T *sR, T *cR,
+                                         T *sI, T *cI) {
+  const int iw = ent >> 1, sgn = ent & 1;
+  for (int t2 = 0; t2 < 2; ++t2) {
+    if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
+    __syncwarp(__activemask());
+  }
+  if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {
+    const T im = delta_sum(x, f, T(0)) * T(3.141592653589793);
+    kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
+  }
+}
+
+// evaluates a warp's near-field list, one entry per lane and round: first the shared
+// divided-difference table (all branches alike); the entries it leaves (clustered or tied
+// knots) are compacted into a second list, evaluated by the branchy per-vertex path in full
+// rounds.  Entries of one round are distinct, so each round adds to distinct slots.
 template <bool FP64, typename T>
 __device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D0l, const T f[4], T vr,
-                                          const T *s_w, const T *s_wl, const short *list, int n, T *sR, T *cR,
-                                          T *sI, T *cI, float tau, int &nfp64) {
+                                          const T *s_w, const T *s_wl, const short *list, int n, short *fb,
+                                          T *sR, T *cR, T *sI, T *cI, float tau, int &nfp64) {
   const int lane = threadIdx.x & 31;
+  int nfb = 0;
+  auto fallback = [&]() {  // warp-uniform
+    for (int base = 0; base < nfb; base += 32) {
+      const int k = base + lane;
+      if (k < nfb) {
+        const int ent = fb[k];
+        T x[4];
+        bool neg;
+        near_knots<FP64>(ent, d, e, D0h, D0l, s_w, s_wl, x, neg);
+        near_add(ent, near_term<FP64>(x, f, tau, nfp64), x, f, vr, neg, sR, cR, sI, cI);
+      }
+      __syncwarp();
+    }
+    nfb = 0;
+  };
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
+    bool left = false;
+    int ent = 0;
     if (k < n) {
-      const int ent = list[k];
-      const int iw = ent >> 1, sgn = ent & 1;
-      const T w = s_w[iw];
-      const bool neg = w < T(0);
-      const T om = neg ? -w : w;
+      ent = list[k];
       T x[4];
-      if (sgn) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = d[i] + om;
+      bool neg;
+      near_knots<FP64>(ent, d, e, D0h, D0l, s_w, s_wl, x, neg);
+      T re;
+      if (series_ok(x, T(Num<T>::kappa))) {
+        near_add(ent, series_sum(x, f), x, f, vr, neg, sR, cR, sI, cI);
+      } else if (inv_sum_shared(x, f, re)) {
+        near_add(ent, re, x, f, vr, neg, sR, cR, sI, cI);
       } else {
-        const T sh = near_shift(D0h, D0l, om, FP64 ? T(0) : (neg ? -s_wl[iw] : s_wl[iw]));
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = sh + e[i];
-      }
-      // a frequency and its two terms may both be in this round: add them one term at a time
-      const T re = near_term<FP64>(x, f, tau, nfp64);
-      for (int t2 = 0; t2 < 2; ++t2) {
-        if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
-        __syncwarp(__activemask());
-      }
-      if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {  // |w| inside the knot range: the delta term too
-        const T im = delta_sum(x, f, T(0)) * T(3.141592653589793);
-        kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
+        left = true;
       }
     }
+    const unsigned bal = __ballot_sync(kFull, left);
+    if (left) fb[nfb + __popc(bal & ((1u << lane) - 1u))] = (short)ent;
+    nfb += __popc(bal);
     __syncwarp();
+    if (nfb > 32 * 7) fallback();  // the second list holds 256 entries
   }
+  fallback();
 }
 
 template <bool FP64>
@@ -299,6 +344,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
   __shared__ short s_near[W][kNearCap];
+  __shared__ short s_fb[W][256];  // near-field entries the shared table leaves
   __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
   extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
@@ -390,15 +436,15 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       }
       if (nlist > kNearCap - 64) {  // flush a full list
         __syncwarp();
-        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib],
-                        cI[wib], tau, nfp64);
+        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, s_fb[wib], sR[wib], cR[wib],
+                        sI[wib], cI[wib], tau, nfp64);
         nlist = 0;
         __syncwarp();
       }
     }
     __syncwarp();
-    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, sR[wib], cR[wib], sI[wib], cI[wib],
-                    tau, nfp64);
+    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, s_fb[wib], sR[wib], cR[wib], sI[wib],
+                    cI[wib], tau, nfp64);
     __syncwarp();
   };
   // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then each piece

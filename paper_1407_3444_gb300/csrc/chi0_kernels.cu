@@ -192,7 +192,7 @@ template <bool FP64>
 __device__ __noinline__ double piece_eval(const Piece<typename std::conditional<FP64, double, float>::type> &pc,
                                           float tau, int &nfp64) {
   if constexpr (FP64) {
-    return pc.w * inv_sum_table(pc.d, pc.f);
+    return pc.w * inv_sum_fast(pc.d, pc.f);
   } else {
     float x[4];
     if (!mixed_knots(x, pc.d, tau)) return (double)(pc.w * inv_sum_long(x, pc.f));
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
     for (int slot = lane; slot < n; slot += 32) {
       const Piece<T> pc = tq[b * sb.tcap + slot];
       if constexpr (FP64) {
-        acc += pc.w * inv_sum_table(pc.d, pc.f);
+        acc += pc.w * inv_sum_fast(pc.d, pc.f);
       } else if (pc.i64 >= 0) {
         any64 = 1u;  // near-degenerate knots: the FP64 table, below
       } else {

@@ -298,6 +298,84 @@ template <typename T> __device__ T inv_sum_table(const T xin[4], const T f[4]) {
   return acc * si;
 }
 
+// sum_j f_j (1/V) int lambda_j / X for sorted knots x (PV across X = 0) by one shared
+// divided-difference table: with u = x/s (s = max|x|) and g(t) = t^3 ln|t|, the 4-knot entries
+// G[p..r] are common to all j, and the entries with knot j doubled follow the same recursion,
+//   H_j[p..r] = ((p < j ? H_j[p+1..r] : G[p..r]) - (r > j ? H_j[p..r-1] : G[p..r])) / (u_r - u_p),
+//   H_j[j..j] = g'(u_j) = 3 u_j^2 ln|u_j| + u_j^2,
+// so all four fourth divided differences g[u, u_j] = H_j[0..3] take four logarithms and six
+// reciprocals (the per-vertex table below takes twenty and forty divisions).  The result is
+// sum_j f_j H_j[0..3] / s.  Returns false, leaving the work to the per-vertex table (Taylor
+// branch for clusters), where two adjacent knots of one sign lie within 1/16 of their
+// magnitude (measured on random knots near a frequency: the recursion then stays within a
+// few times the per-vertex table's FP32 error), two knots are equal or three knots are 0.
+constexpr double kRhoShared = 0.0625;  // adjacent knots this close (relative) go to the table
+template <typename T> __device__ __forceinline__ bool inv_sum_shared(const T x[4], const T f[4], T &out) {
+  const T s = tabs(x[0]) > tabs(x[3]) ? tabs(x[0]) : tabs(x[3]);
+  if (s == T(0)) {
+    out = T(0);
+    return true;
+  }
+  const T rho = T(kRhoShared);
+  const T si = T(1) / s;
+  T u[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) u[i] = x[i] * si;
+  int nz = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) nz += u[i] == T(0);
+  if (nz >= 3) return false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T a = u[i], b = u[i + 1];
+    if (!(b > a)) return false;                                       // equal knots
+    if ((a > T(0) && b - a <= rho * a) || (b < T(0) && b - a <= rho * (-b))) return false;  // cluster
+  }
+  T g[4], gp[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const T t = u[i], t2 = t * t;
+    const T L = t == T(0) ? T(0) : Num<T>::lg(tabs(t));
+    g[i] = t2 * t * L;
+    gp[i] = T(3) * t2 * L + t2;
+  }
+  const T r01 = rcp(u[1] - u[0]), r12 = rcp(u[2] - u[1]), r23 = rcp(u[3] - u[2]);
+  const T r02 = rcp(u[2] - u[0]), r13 = rcp(u[3] - u[1]), r03 = rcp(u[3] - u[0]);
+  const T G01 = (g[1] - g[0]) * r01, G12 = (g[2] - g[1]) * r12, G23 = (g[3] - g[2]) * r23;
+  const T G012 = (G12 - G01) * r02, G123 = (G23 - G12) * r13;
+  const T G0123 = (G123 - G012) * r03;
+  T R[4];
+  {  // j = 0
+    const T h01 = (G01 - gp[0]) * r01;
+    const T h02 = (G012 - h01) * r02;
+    R[0] = (G0123 - h02) * r03;
+  }
+  {  // j = 1
+    const T h01 = (gp[1] - G01) * r01, h12 = (G12 - gp[1]) * r12;
+    const T h02 = (h12 - h01) * r02, h13 = (G123 - h12) * r13;
+    R[1] = (h13 - h02) * r03;
+  }
+  {  // j = 2
+    const T h12 = (gp[2] - G12) * r12, h23 = (G23 - gp[2]) * r23;
+    const T h02 = (h12 - G012) * r02, h13 = (h23 - h12) * r13;
+    R[2] = (h13 - h02) * r03;
+  }
+  {  // j = 3
+    const T h23 = (gp[3] - G23) * r23;
+    const T h13 = (h23 - G123) * r13;
+    R[3] = (h13 - G0123) * r03;
+  }
+  out = (f[0] * R[0] + f[1] * R[1] + f[2] * R[2] + f[3] * R[3]) * si;
+  return true;
+}
+
+// the shared table where it applies, else the per-vertex table
+template <typename T> __device__ __forceinline__ T inv_sum_fast(const T x[4], const T f[4]) {
+  T r;
+  if (inv_sum_shared(x, f, r)) return r;
+  return inv_sum_table(x, f);
+}
+
 // series branch: sorted knots of one sign with (x3 - x0) <= kappa |x0 + x3|
 template <typename T> __device__ __forceinline__ bool series_ok(const T x[4], T kappa) {
   return (x[0] > T(0) || x[3] < T(0)) && (x[3] - x[0]) <= kappa * tabs(x[0] + x[3]);
@@ -306,7 +384,7 @@ template <typename T> __device__ __forceinline__ bool series_ok(const T x[4], T 
 // sum_j f_j (1/V) int_S lambda_j / X, sorted knots x (FP64 or FP32 throughout)
 template <typename T> __device__ __forceinline__ T inv_sum(const T x[4], const T f[4]) {
   if (series_ok(x, T(Num<T>::kappa))) return series_sum(x, f);
-  return inv_sum_table(x, f);
+  return inv_sum_fast(x, f);
 }
 
 // Mixed precision, knots of a final tetrahedron that missed the short series: the D = 0
@@ -332,7 +410,7 @@ __device__ __forceinline__ bool mixed_knots(float x[4], const float d[4], float 
 // FP32 evaluation of queued knots: the long series where it converges, else the table
 __device__ __forceinline__ float inv_sum_long(const float x[4], const float f[4]) {
   if (series_ok(x, Num<float>::kappa_long)) return series_sum(x, f);
-  return inv_sum_table(x, f);
+  return inv_sum_fast(x, f);
 }
 
 // mixed precision, all branches in one place (dynamic kernel)
