@@ -1,22 +1,27 @@
 """Benchmark: chi0 (tetra x band-pair x q x omega) evals/s on one GB300.
 
-Default workload: the Cr-like 9-orbital static run (48^3 k mesh, 663,552 tetrahedra,
-9 bands, 256 q on Gamma-X-M-Gamma with explicit k+q eigen-data).  One step = chi0
-for all 256 q through the C-ABI, every stage (overlaps, carving + weights, reduction)
-in the CUDA library.  ``value`` is the mixed-precision form with inputs resident in
-HBM; the all-FP64 GPU form is timed on the same inputs and reported beside it with
-the normwise error between the two, and the FP64 CPU oracle is timed on a bounded
-sample of the same workload (``cpu_baseline``).
+Default workload: the large mixed-precision run -- an 80-band seeded tight-binding model on a
+72^3 k mesh (2,239,488 tetrahedra, complex64 eigenvectors, 19.1 GB), 128 on-grid q points and
+256 frequencies in [0, 2] eV.  One step = the dynamic chi0 (Re and Im, Eqs. 1-3) of a stated
+subset of the 128 q points (``--nq``, default 1) at all 256 frequencies, every stage in the
+CUDA library: tensor-core overlaps (split-BF16, three pieces), carving and frequency-resolved
+weights (FP32 with FP64 near-degenerate branches), reduction.  ``value`` is that mixed form
+with inputs resident in HBM; the all-FP64 GPU form is timed on the same inputs and reported
+beside it with the normwise error between the two; the FP64 CPU oracle is timed on a bounded,
+seeded sample of the builtin tetrahedra of the same q (``cpu_baseline``), and the GPU forms run
+on the same sample are compared with it (``error.vs_oracle``).
 
-``--impl reference`` times the oracle alone (host cores) on the same metric.
-Under torchrun every rank runs its own replica of the workload (independent q sets:
-no data-path collective); rank 0 prints the JSON line.
+Other workloads (``--workload``): cr (Cr-like 9-band static, 48^3, 256 q), free (free-electron
+Lindhard), fese (FeSe-like dynamic, 512 w), sweep (40-band window sweep, static).
+
+``--impl reference`` times the oracle alone (host cores) on the same metric.  Under torchrun
+every rank runs its own replica of the workload (independent q sets: no data-path
+collective); rank 0 prints the JSON line.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -32,6 +37,7 @@ sys.path.insert(0, ROOT)
 from paper_1407_3444_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "chi0 (tetra x band-pair x q x omega) evals/s, mixed vs all-FP64 GPU at 1e-6 rel"
+LARGE_NQ = 128  # q points of the large run (a step takes a stated subset)
 
 
 def parse():
@@ -42,24 +48,25 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-tune", action="store_true",
                     help="skip chi0_tune (launch-shape autotuner) before the warm-up steps")
-    ap.add_argument("--overlap", default="fp32", choices=["fp32", "bf16x3", "bf16x6", "tf32"],
-                    help="matrix elements of the mixed form: FP32 on the CUDA cores (default) or the "
-                         "tensor cores (BF16 split in two pieces / three pieces, or one TF32 product)")
-    ap.add_argument("--workload", default="cr", choices=["cr", "free", "fese", "sweep", "large"],
-                    help="cr: Cr-like 9-orbital static (default); free: free-electron Lindhard; fese: "
-                         "FeSe-like dynamic; sweep: 40-band window sweep (static); large: 80-band 72^3 dynamic")
-    ap.add_argument("--nw", type=int, default=0,
-                    help="dynamic workloads: use the first NW frequencies of the workload's grid "
-                         "(a bounded sample of the 80-band 72^3 run)")
-    ap.add_argument("--nq", type=int, default=None, help="q points per step (default: the workload's)")
+    ap.add_argument("--overlap", default="auto", choices=["auto", "fp32", "bf16x3", "bf16x6", "tf32"],
+                    help="matrix elements of the mixed form: auto = three-piece split-BF16 on the tensor cores "
+                         "for the 80-band run, FP32 on the CUDA cores for the small windows of the others")
+    ap.add_argument("--workload", default="large", choices=["large", "cr", "free", "fese", "sweep"],
+                    help="large: 80-band 72^3 dynamic (default); cr: Cr-like 9-orbital static; free: "
+                         "free-electron Lindhard; fese: FeSe-like dynamic; sweep: 40-band window sweep (static)")
+    ap.add_argument("--nw", type=int, default=0, help="dynamic workloads: the first NW frequencies only")
+    ap.add_argument("--nq", type=int, default=None,
+                    help="q points per step (large: a subset of its 128, default 1; others: the workload's)")
     ap.add_argument("--n", type=int, default=None, help="k mesh cubes per axis (cubic workloads)")
-    ap.add_argument("--cpu-sample-w", type=int, default=16, help="frequencies in the CPU sample (dynamic)")
-    ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-q", type=int, default=None,
-                    help="q points of the oracle's timed sample (default: static workloads 8 for the "
-                         "cpu_baseline, ~10-15 s on 16 cores, and 2 per --impl reference step; dynamic 1)")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-q", type=int, default=None,
+                    help="static workloads: q points of the oracle's timed sample (default 8; 2 per "
+                         "--impl reference step)")
+    ap.add_argument("--cpu-sample-w", type=int, default=16, help="dynamic workloads: frequencies of the oracle sample")
+    ap.add_argument("--cpu-tets", type=int, default=None,
+                    help="large: tetrahedra of the oracle sample (default 192; 48 per --impl reference step)")
     ap.add_argument("--profile-out", default="")
     return ap.parse_args()
 
@@ -89,6 +96,12 @@ def whole_job_rate(world_size: int, units_per_rank: float, max_ms: float) -> flo
     return world_size * units_per_rank / (max_ms * 1e-3)
 
 
+def overlap_mode(args):
+    if args.overlap != "auto":
+        return args.overlap
+    return "bf16x6" if args.workload == "large" else "fp32"
+
+
 def make_workload(args, nproc):
     """The selected workload (the five synthetic stand-ins of the paper's materials)."""
     k = args.workload
@@ -99,13 +112,16 @@ def make_workload(args, nproc):
     if k == "fese":
         nq = args.nq or 64
         n = (args.n, args.n, max(1, args.n // 4)) if args.n else (64, 64, 16)
-        return wl.fese_like(n=n, nq=64, nproc=nproc,
-                            qfracs=[np.array([0.5, 0.5, 0.0]) * (j + 1) / 64 for j in range(64)][:nq])
-    if k == "sweep":
+        W = wl.fese_like(n=n, nq=64, nproc=nproc,
+                         qfracs=[np.array([0.5, 0.5, 0.0]) * (j + 1) / 64 for j in range(64)][:nq])
+    elif k == "sweep":
         W = wl.band_sweep(n=args.n or 32, nq=args.nq or 128, nproc=nproc)
         W.omega = None  # the static sweep (the dynamic one: chi0_dynamic on the same plan)
         return W
-    W = wl.large_mixed(n=args.n or 72, nq=args.nq or 128, nproc=nproc)
+    else:
+        W = wl.large_mixed(n=args.n or 72, nq=LARGE_NQ, nproc=nproc)
+        W.meta["nq_total"] = len(W.qs)
+        W.qs = W.qs[:args.nq or 1]
     if args.nw:
         W.omega = W.omega[:args.nw]
     return W
@@ -116,27 +132,52 @@ def workload_config(W, args):
              "free": "free-electron static Lindhard chi0 (open [-pi,pi]^3 mesh, |M|^2 = 1, 32 q along (100))",
              "fese": "FeSe-like 10-orbital dynamic chi0 (Gamma-M, explicit k+q, 512 w in [0,2] eV, E_F at 6/10)",
              "sweep": "40-band random model, static chi0, on-grid q with per-q band windows 4..40",
-             "large": "80-band random model, dynamic chi0, on-grid q, 256 w in [0,2] eV"}
+             "large": "80-band random model, dynamic chi0 (Re and Im), on-grid q, w in [0,2] eV, E_F at half filling"}
     nw = 1 if W.omega is None else len(W.omega)
     inb = sum((q.Cq.nbytes if q.Cq is not None else 0) + (q.Eq.nbytes if q.Eq is not None else 0) for q in W.qs)
     inb += W.E.nbytes + (W.C.nbytes if W.C is not None else 0)
+    qs = "%d q" % len(W.qs)
+    if "nq_total" in W.meta:
+        qs = "q points 1..%d of its %d per step" % (len(W.qs), W.meta["nq_total"])
+    ovl = overlap_mode(args)
     return {
-        "workload": "%s: %s k mesh (%d tetrahedra), %d bands, %d q, %d w" % (
-            names[args.workload], "x".join(str(x) for x in W.n), W.ntet, W.nb, len(W.qs), nw),
+        "workload": "%s: %s k mesh (%d tetrahedra), %d bands, %s, %d w" % (
+            names[args.workload], "x".join(str(x) for x in W.n), W.ntet, W.nb, qs, nw),
         "ntet": W.ntet, "nbands": W.nb, "nq": len(W.qs), "nomega": nw,
         "nominal_evals_per_step": W.nominal_evals(),
         "evec_dtype": str(W.C.dtype) if W.C is not None else None,
         "overlap": {"fp32": "FP32 on the CUDA cores", "bf16x3": "tensor cores, BF16 2 pieces, 3 products",
-                    "bf16x6": "tensor cores, BF16 3 pieces, 6 products", "tf32": "tensor cores, TF32"}[args.overlap],
+                    "bf16x6": "tensor cores, BF16 3 pieces, 6 products", "tf32": "tensor cores, TF32"}[ovl],
         "l2": "inputs larger than L2 (%.1f GB of eigen-data read per step)" % (inb / 1e9),
     }
 
 
-def cpu_sample(W, nq_sample, nthreads, nw_sample=16):
-    """Oracle on q points 1 .. nq_sample (whole tetrahedron set; q 0 is Gamma on the paths);
-    dynamic workloads: the first nw_sample frequencies."""
+def tet_sample(W, count, seed):
+    """A seeded sample of the builtin tetrahedra as an explicit list (corners, volumes)."""
+    rng = np.random.default_rng(seed)
+    ids = np.sort(rng.choice(W.ntet, size=min(count, W.ntet), replace=False))
+    return wl.builtin_tetra(W.n, ids)
+
+
+def sample_freqs(W, nw_sample):
+    return np.unique(np.linspace(0, len(W.omega) - 1, nw_sample).round().astype(int))
+
+
+def cpu_sample(W, nq_sample, nthreads, nw_sample=16, tets=None):
+    """The oracle on a bounded sample.  With ``tets``: the first q of the step, those tetrahedra,
+    nw_sample frequencies spread over the grid.  Without: q points 1 .. nq_sample (whole
+    tetrahedron set; q 0 is Gamma on the paths), the first nw_sample frequencies (dynamic)."""
     import oracle
     oracle.build()
+    if tets is not None:
+        tet, vol = tets
+        idx = sample_freqs(W, nw_sample)
+        q = W.qs[0]
+        t0 = time.perf_counter()
+        vals = [oracle.chi0_q(W, q, omega=W.omega[idx], nthreads=nthreads, tet=tet, tvol=vol)]
+        dt = time.perf_counter() - t0
+        lo, hi = q.window or W.window
+        return vals, dt, len(tet) * (hi - lo) ** 2 * len(idx)
     qs = W.qs[1:1 + nq_sample] if len(W.qs) > 1 else W.qs[:1]
     om = None if W.omega is None else W.omega[:nw_sample]
     t0 = time.perf_counter()
@@ -210,22 +251,34 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 FMA lanes: 152 SMs x 128 lanes x 2 flop per FMA at the maximum SM clock
-def fp32_peak_tflops(sm_mhz):
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def arithmetic_peaks(chi0):
+    """FP32 and FP64 FMA and tcgen05 TF32 / BF16 MMA throughput of this GPU, measured by the
+    library's micro-kernels (chi0_peak) with CUDA events, before the timed region."""
+    out = {}
+    for name, kind, iters in (("fp32_fma_tflops", chi0.CHI0_PEAK_FP32_FMA, 20000),
+                              ("fp64_fma_tflops", chi0.CHI0_PEAK_FP64_FMA, 300),
+                              ("tf32_mma_tflops", chi0.CHI0_PEAK_TF32_MMA, 100000),
+                              ("bf16_mma_tflops", chi0.CHI0_PEAK_BF16_MMA, 200000)):
+        try:
+            out[name] = chi0.chi0_peak(kind, iters)[0]
+        except Exception as e:  # reported, not hidden
+            out[name] = None
+            out.setdefault("errors", []).append("%s: %s" % (name, e))
+    out["source"] = "chi0_peak micro-kernels in this run (CUDA events, every SM busy)"
+    return out
 
 
-# FP32 operations (FFMA counted twice, FADD, FMUL) of the mixed static weight kernels per
-# final tetrahedron on the Cr-like 48^3 workload, from ncu's instruction counters of
-# k_static + k_static_tab (one q of an 8-q run, 13.65 M final tetrahedra per launch); and
-# their DRAM bytes per final tetrahedron.
+# Executed FP32 operations (FFMA counted twice, FADD, FMUL) per final tetrahedron of the mixed
+# static weight kernels on the Cr-like 48^3 workload (ncu instruction counters of k_static +
+# k_static_tab) and their DRAM bytes per final tetrahedron.
 FLOPS_PER_PIECE_MIXED = 202.6
 TRAFFIC_PER_PIECE_MIXED = 3.58
-# The same for k_dynamic per (final tetrahedron, frequency) on the FeSe-like model (ncu
-# counters of the four k_dynamic launches of one step on its 32x32x8 mesh, 2 q x 512 w:
-# 1.40 M final tetrahedra x 256 w per launch).
-FLOPS_PER_PIECE_W_DYN = 169.3
-TRAFFIC_PER_PIECE_W_DYN = None  # counted (0.0139 B) on the kernel before its piece buffering
+# The same for the dynamic weight kernel per final tetrahedron over one pass of 256 frequencies
+# (ncu counters of k_dynamic on the 80-band model, 24^3 mesh, one q; the FP64 kernel's FP64
+# operations likewise).  None until counted on the current kernel.
+FLOPS_PER_PIECE_DYN32 = None
+FLOPS_PER_PIECE_DYN64 = None
+TRAFFIC_PER_PIECE_DYN32 = None
 
 
 def run_step(P, W):
@@ -253,6 +306,14 @@ def rel_err(a, b):
     return float(np.max(np.max(np.abs(a - b), axis=1) / scale))
 
 
+def sample_desc(args, W, tets, dt):
+    if tets is not None:
+        return ("q point 1 of the step, %d seeded tetrahedra of the %d-tetrahedron mesh, %d of the %d w, "
+                "%.1f s" % (len(tets[0]), W.ntet, len(sample_freqs(W, args.cpu_sample_w)), len(W.omega), dt))
+    return "q points 1..%d of the workload (all %d tetrahedra%s), %.1f s" % (
+        args.cpu_sample_q, W.ntet, "" if W.omega is None else ", first %d w" % args.cpu_sample_w, dt)
+
+
 # ------------------------------------------------------------------------------ main
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -260,13 +321,17 @@ def run_reference(args):
         return 0
     nproc = wl.default_nproc()
     W = make_workload(args, nproc)
+    tets = None
+    if args.workload == "large":
+        tets = tet_sample(W, args.cpu_tets or 48, wl.SEED_BASE + 77)
+        args.cpu_sample_w = min(args.cpu_sample_w, 8)
     if args.cpu_sample_q is None:
         args.cpu_sample_q = 2 if W.omega is None else 1
     cores = len(os.sched_getaffinity(0))
     times = []
     evals = 0
     for s in range(args.warmup + args.steps):
-        _, dt, ev = cpu_sample(W, args.cpu_sample_q, cores, args.cpu_sample_w)
+        _, dt, ev = cpu_sample(W, args.cpu_sample_q, cores, args.cpu_sample_w, tets)
         if s >= args.warmup:
             times.append(dt)
             evals = ev
@@ -277,8 +342,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(W, args),
             "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": "q points 1..%d of the workload, all tetrahedra%s" % (
-                                 args.cpu_sample_q, "" if W.omega is None else ", first %d w" % args.cpu_sample_w)},
+                             "sample": sample_desc(args, W, tets, T)},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -287,18 +351,18 @@ def run_reference(args):
 def run_ours(args):
     ws, rank, local = dist_env()
     nproc = max(1, wl.default_nproc() // max(1, ws))
+    ovl = overlap_mode(args)
     # inputs (and the oracle sample) before any CUDA call: the generator uses a spawn pool
     W = make_workload(args, nproc)
+    tets = tet_sample(W, args.cpu_tets or 192, wl.SEED_BASE + 77) if args.workload == "large" else None
     if args.cpu_sample_q is None:
         args.cpu_sample_q = 8 if W.omega is None else 1
     cpu = None
     if rank == 0 and not args.no_cpu:
         cores = len(os.sched_getaffinity(0))
-        vals, dt, ev = cpu_sample(W, args.cpu_sample_q, cores, args.cpu_sample_w)
+        vals, dt, ev = cpu_sample(W, args.cpu_sample_q, cores, args.cpu_sample_w, tets)
         cpu = {"value": ev / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
-               "sample": "q points 1..%d of the workload (all %d tetrahedra%s), %.1f s"
-                         % (args.cpu_sample_q, W.ntet, "" if W.omega is None else ", first %d w" % args.cpu_sample_w,
-                            dt)}
+               "sample": sample_desc(args, W, tets, dt)}
         oracle_vals = vals
     import torch
     import torch.distributed as dist
@@ -313,9 +377,9 @@ def run_ours(args):
             dist.barrier()
 
     stream = torch.cuda.current_stream()
+    peaks_run = arithmetic_peaks(chi0)
     dev = chi0.DeviceInputs(W)
-    Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev, overlap=args.overlap)
-    Pd = chi0.Plan(W, precision="fp64", device=True, profile=False, staged=dev) if args.fp64_steps > 0 else None
+    Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev, overlap=ovl)
     nominal = W.nominal_evals()
     tuned = None
     if not args.no_tune:  # untimed: picks the weight kernel's block shape and grid, and the
@@ -340,31 +404,34 @@ def run_ours(args):
     ms = reduce_max(e0.elapsed_time(e1) / args.steps)
     s1 = Pm.stats()
     value = whole_job_rate(ws, nominal, ms)
-    def stage_ms(k):
-        n = s1.launches[k] - s0.launches[k]
-        return (s1.time_ms[k] - s0.time_ms[k]) / n if n else None
 
-    k_static_ms = stage_ms(chi0.CHI0_K_STATIC)
+    def stage_ms(s_a, s_b, k):
+        n = s_b.launches[k] - s_a.launches[k]
+        return (s_b.time_ms[k] - s_a.time_ms[k]) / n if n else None
+
     launches = s1.kernels - s0.kernels
     pieces_timed = s1.pieces - s0.pieces
-    # non-empty work: final tetrahedra times the frequencies each is evaluated on, per second
     w_eval = 1.0 if W.omega is None else len(W.omega) / max(1, -(-len(W.omega) // chi0.DYNAMIC_MAX_NW))
     nonzero_rate = whole_job_rate(ws, pieces_timed / args.steps * w_eval, ms)
-    static_launches = s1.launches[chi0.CHI0_K_STATIC] - s0.launches[chi0.CHI0_K_STATIC]
-    stages = {name: stage_ms(k) for name, k in (("overlap", chi0.CHI0_K_OVERLAP), ("weights", chi0.CHI0_K_STATIC),
-                                                 ("dynamic", chi0.CHI0_K_DYNAMIC),
-                                                 ("reduce", chi0.CHI0_K_REDUCE), ("bands", chi0.CHI0_K_BANDS),
-                                                 ("dos", chi0.CHI0_K_DOS))}
+    stages = {name: stage_ms(s0, s1, k) for name, k in (
+        ("overlap", chi0.CHI0_K_OVERLAP), ("weights", chi0.CHI0_K_STATIC), ("dynamic", chi0.CHI0_K_DYNAMIC),
+        ("reduce", chi0.CHI0_K_REDUCE), ("bands", chi0.CHI0_K_BANDS), ("dos", chi0.CHI0_K_DOS))}
     counters = Pm.counters()
+    counters_step = {"final_tetrahedra": pieces_timed // args.steps,
+                     "box_pieces": (s1.box_pieces - s0.box_pieces) // args.steps,
+                     "fp64_branch_evals": (s1.fp64_evals - s0.fp64_evals) // args.steps}
     mixed = to_host(out_m)
 
     # all-FP64 GPU form on the same resident inputs
     fp64 = None
     ms64 = None
     err_mixed = None
-    if Pd is not None:
-        run_step(Pd, W)
+    dyn64_ms = None
+    pieces64 = None
+    if args.fp64_steps > 0:
+        Pd = chi0.Plan(W, precision="fp64", device=True, profile=True, staged=dev)
         torch.cuda.synchronize()
+        d0 = Pd.stats()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -372,9 +439,28 @@ def run_ours(args):
             out_d = run_step(Pd, W)
         f1.record(stream)
         torch.cuda.synchronize()
+        d1 = Pd.stats()
         ms64 = f0.elapsed_time(f1) / args.fp64_steps
         fp64 = to_host(out_d)
         err_mixed = rel_err(mixed, fp64)
+        dyn64_ms = stage_ms(d0, d1, chi0.CHI0_K_DYNAMIC if W.omega is not None else chi0.CHI0_K_STATIC)
+        pieces64 = (d1.pieces - d0.pieces) / max(1, (d1.launches[chi0.CHI0_K_DYNAMIC if W.omega is not None
+                                                                   else chi0.CHI0_K_STATIC]
+                                                      - d0.launches[chi0.CHI0_K_DYNAMIC if W.omega is not None
+                                                                    else chi0.CHI0_K_STATIC]))
+        Pd.close()
+
+    # the GPU forms on the oracle's tetrahedron sample (large run): same q, same frequencies
+    gpu_on_sample = None
+    if tets is not None and cpu is not None:
+        idx = sample_freqs(W, args.cpu_sample_w)
+        gpu_on_sample = {}
+        for prec in ("mixed", "fp64"):
+            Ps = chi0.Plan(W, precision=prec, device=True, staged=dev, tetra=tets, qs=W.qs[:1],
+                           overlap=ovl if prec == "mixed" else "fp32")
+            re, im = Ps.dynamic(W.omega)
+            gpu_on_sample[prec] = (re.cpu().numpy()[:, idx], im.cpu().numpy()[:, idx])
+            Ps.close()
 
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
@@ -384,7 +470,7 @@ def run_ours(args):
         for s in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Ph = chi0.Plan(W, precision="mixed", device=False, staged=host)
+            Ph = chi0.Plan(W, precision="mixed", device=False, staged=host, overlap=ovl)
             out_h = run_step(Ph, W)
             Ph.close()
             t1 = time.perf_counter()
@@ -397,84 +483,99 @@ def run_ours(args):
         del host
 
     peaks, kind = measured_peaks()
-    smax = float(peaks.get("sm_max_mhz", 2070.0))
-    pk = fp32_peak_tflops(smax)
-    peak_src = "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % smax
+    fp32_pk = peaks_run.get("fp32_fma_tflops")
+    fp64_pk = peaks_run.get("fp64_fma_tflops")
     if W.omega is None:
-        pieces_per_launch = pieces_timed / max(1, static_launches)
-        ach = (FLOPS_PER_PIECE_MIXED * pieces_per_launch / (k_static_ms * 1e-3) / 1e12
-               if k_static_ms and args.workload == "cr" else None)
-        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk if ach is not None else None,
-                "traffic": (TRAFFIC_PER_PIECE_MIXED * pieces_per_launch
-                            if TRAFFIC_PER_PIECE_MIXED and args.workload == "cr" else None),
-                "kernel": "static weights (k_static + k_static_tab, mixed)",
-                "kernel_ms": k_static_ms, "units_per_launch": pieces_per_launch,
-                "flops_per_unit": FLOPS_PER_PIECE_MIXED, "unit_name": "final tetrahedron",
-                "peak_source": peak_src}
+        k_ms = stage_ms(s0, s1, chi0.CHI0_K_STATIC)
+        launches_w = s1.launches[chi0.CHI0_K_STATIC] - s0.launches[chi0.CHI0_K_STATIC]
+        fpu, tpu, kname = (FLOPS_PER_PIECE_MIXED if args.workload == "cr" else None,
+                           TRAFFIC_PER_PIECE_MIXED if args.workload == "cr" else None,
+                           "static weights (k_static + k_static_tab, mixed)")
+        uname = "final tetrahedron"
     else:
-        # k_dynamic: one launch = one pass of <= 256 frequencies over every final tetrahedron
-        dyn_launches = s1.launches[chi0.CHI0_K_DYNAMIC] - s0.launches[chi0.CHI0_K_DYNAMIC]
-        k_dyn_ms = stage_ms(chi0.CHI0_K_DYNAMIC)
-        pieces_per_launch = pieces_timed / max(1, dyn_launches)
-        w_per_launch = len(W.omega) / max(1, -(-len(W.omega) // chi0.DYNAMIC_MAX_NW))
-        units = pieces_per_launch * w_per_launch
-        ach = (FLOPS_PER_PIECE_W_DYN * units / (k_dyn_ms * 1e-3) / 1e12
-               if k_dyn_ms and FLOPS_PER_PIECE_W_DYN and args.workload == "fese" else None)
-        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk if ach is not None else None,
-                "traffic": (TRAFFIC_PER_PIECE_W_DYN * units
-                            if TRAFFIC_PER_PIECE_W_DYN and args.workload == "fese" else None),
-                "kernel": "dynamic weights (k_dynamic, mixed)",
-                "kernel_ms": k_dyn_ms, "units_per_launch": units,
-                "flops_per_unit": FLOPS_PER_PIECE_W_DYN, "unit_name": "(final tetrahedron, w)",
-                "peak_source": peak_src}
-    # the overlap kernel is bound by HBM: eigenvector blocks at k (complex64 copy) and at k+q
-    # (complex128 inputs) read once, |M|^2 written once
+        k_ms = stage_ms(s0, s1, chi0.CHI0_K_DYNAMIC)
+        launches_w = s1.launches[chi0.CHI0_K_DYNAMIC] - s0.launches[chi0.CHI0_K_DYNAMIC]
+        fpu, tpu, kname = (FLOPS_PER_PIECE_DYN32 if args.workload == "large" else None,
+                           TRAFFIC_PER_PIECE_DYN32 if args.workload == "large" else None,
+                           "dynamic weights (k_dynamic + box sums/evaluation, mixed)")
+        uname = "final tetrahedron over a pass of <= 256 w"
+    units = pieces_timed / max(1, launches_w)
+    ach = fpu * units / (k_ms * 1e-3) / 1e12 if (fpu and k_ms) else None
+    roof = {"bound": "alu", "achieved": ach, "peak": fp32_pk, "unit": "TFLOP/s",
+            "frac": ach / fp32_pk if (ach is not None and fp32_pk) else None,
+            "traffic": tpu * units if tpu else None, "kernel": kname, "kernel_ms": k_ms,
+            "units_per_launch": units, "unit_name": uname, "flops_per_unit": fpu,
+            "final_tetrahedra_per_s_per_sm": units / (k_ms * 1e-3) / 152.0 if k_ms else None,
+            "peak_source": "measured FP32 FMA peak of this GPU (chi0_peak, this run)"}
+    roof64 = None
+    if dyn64_ms and pieces64:
+        f64 = FLOPS_PER_PIECE_DYN64 if (W.omega is not None and args.workload == "large") else None
+        a64 = f64 * pieces64 / (dyn64_ms * 1e-3) / 1e12 if f64 else None
+        roof64 = {"bound": "alu", "achieved": a64, "peak": fp64_pk, "unit": "TFLOP/s (FP64)",
+                  "frac": a64 / fp64_pk if (a64 is not None and fp64_pk) else None,
+                  "kernel_ms": dyn64_ms, "units_per_launch": pieces64, "flops_per_unit": f64,
+                  "peak_source": "measured FP64 FMA peak of this GPU (chi0_peak, this run)"}
+    # the overlap kernel: HBM bytes (eigenvector blocks at k and k+q read, |M|^2 written) and the
+    # tensor-core products (8 w^2 norb flops per corner for the complex GEMM, times the products
+    # of the split form)
     ovl_ms = stages["overlap"]
-    ovl = None
+    ovl_roof = None
     if ovl_ms and W.C is not None:
-        nc, no, w = W.ncorner, W.norb, W.nb
+        nc, no = W.ncorner, W.norb
+        lo, hi = W.qs[0].window or W.window
+        w = hi - lo
         kq = W.qs[0].Cq.itemsize if W.qs[0].Cq is not None else 8
         ovl_bytes = nc * no * w * (8 + kq) + nc * w * w * 4
-        ovl = {"bound": "hbm", "achieved": ovl_bytes / (ovl_ms * 1e-3) / 1e9, "peak": float(peaks.get("hbm_gbs", 6800.0)),
-               "unit": "GB/s", "bytes_per_launch": ovl_bytes, "kernel_ms": ovl_ms}
-        ovl["frac"] = ovl["achieved"] / ovl["peak"]
+        prods = {"bf16x6": 6, "bf16x3": 3, "tf32": 1, "fp32": 0}[ovl]
+        tflop = 8.0 * w * w * no * nc * prods / (ovl_ms * 1e-3) / 1e12 if prods else None
+        tpk = peaks_run.get("tf32_mma_tflops" if ovl == "tf32" else "bf16_mma_tflops")
+        ovl_roof = {"bound": "hbm", "achieved": ovl_bytes / (ovl_ms * 1e-3) / 1e9,
+                    "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "bytes_per_launch": ovl_bytes,
+                    "kernel_ms": ovl_ms, "kernel": "k_overlap_tc" if prods else "k_overlap_small / k_overlap",
+                    "tensor_tflops": tflop, "tensor_peak_tflops": tpk,
+                    "tensor_frac": tflop / tpk if (tflop and tpk) else None}
+        ovl_roof["frac"] = ovl_roof["achieved"] / ovl_roof["peak"]
 
     if rank == 0:
         err_oracle = None
         if cpu is not None:
-            nq = len(oracle_vals)
-            i0 = 1 if len(W.qs) > 1 else 0
+            if tets is not None:
+                ref = tuple(np.asarray(oracle_vals[0][k])[None, :] for k in (0, 1))
+                err_oracle = {"mixed_gpu": rel_err(gpu_on_sample["mixed"], ref),
+                              "fp64_gpu": rel_err(gpu_on_sample["fp64"], ref),
+                              "sample": "the cpu_baseline sample (explicit tetrahedron list, same q, same w)"}
+            else:
+                nq = len(oracle_vals)
+                i0 = 1 if len(W.qs) > 1 else 0
 
-            def sample(x):
-                if isinstance(x, tuple):
-                    return tuple(y[i0:i0 + nq, :args.cpu_sample_w] for y in x)
-                return x[i0:i0 + nq]
+                def sample(x):
+                    if isinstance(x, tuple):
+                        return tuple(y[i0:i0 + nq, :args.cpu_sample_w] for y in x)
+                    return x[i0:i0 + nq]
 
-            ref = (tuple(np.array([v[k] for v in oracle_vals]) for k in (0, 1))
-                   if W.omega is not None else np.array(oracle_vals))
-            err_oracle = {"mixed_gpu": rel_err(sample(mixed), ref), "q_points": nq}
-            if fp64 is not None:
-                err_oracle["fp64_gpu"] = rel_err(sample(fp64), ref)
+                ref = (tuple(np.array([v[k] for v in oracle_vals]) for k in (0, 1))
+                       if W.omega is not None else np.array(oracle_vals))
+                err_oracle = {"mixed_gpu": rel_err(sample(mixed), ref), "q_points": nq}
+                if fp64 is not None:
+                    err_oracle["fp64_gpu"] = rel_err(sample(fp64), ref)
+        dtype = "f32+f64" if ovl == "fp32" else "%s+f32+f64" % ovl
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": workload_config(W, args),
                 "fp64_gpu": ({"value": nominal / (ms64 * 1e-3), "unit": "evals/s", "ms_per_step": ms64,
                               "mixed_speedup": ms64 / ms} if ms64 else None),
                 "error": {"mixed_vs_fp64_gpu_max_rel": err_mixed, "vs_oracle": err_oracle},
-                "roofline": roof, "roofline_overlap": ovl, "stage_ms_per_q": stages,
+                "roofline": roof, "roofline_fp64": roof64, "roofline_overlap": ovl_roof,
+                "stage_ms_per_q": stages, "peaks_run": peaks_run,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "tuned": tuned,
                 "nonzero": {"value": nonzero_rate, "unit": "(final tetrahedron, w) evaluations/s"},
-                "counters": counters, "clocks": ck, "peaks_source": kind}
+                "counters_per_step": counters_step, "counters": counters, "clocks": ck, "peaks_source": kind}
         print(json.dumps(line), flush=True)
         if args.profile_out:
             with open(args.profile_out, "w") as f:
                 json.dump(line, f, indent=1)
     Pm.close()
-    if Pd is not None:
-        Pd.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
