@@ -71,7 +71,8 @@ template <bool FP64> struct DynShape {
   static constexpr int DC = FP64 ? 16 : 32;  // queued pieces evaluated per round
   static constexpr int KM = FP64 ? 64 : 32;  // own far-field moments kept per queued piece
   static constexpr int NF = FP64 ? 3 : 2;    // a fine box stands in beyond NF radii
-  static constexpr int KF = FP64 ? 32 : 24;  // moments of a fine box   (truncation NF^-KF)
+  static constexpr int KF = FP64 ? 28 : 24;  // moments of a fine box   (truncation NF^-KF)
+  static constexpr int FB = FP64 ? 576 : 640;  // near-field entries left to the per-vertex table
   static constexpr int KG = FP64 ? 22 : 12;  // moments of a geometric box ((2/9)^KG)
 };
 
@@ -263,30 +264,16 @@ __device__ __forceinline__ void near_add(int ent, T re, const T x[4], const T f[
   }
 }
 
-// evaluates a warp's near-field list, one entry per lane and round: first the shared
-// divided-difference table (all branches alike); the entries it leaves (clustered or tied
-// knots) are compacted into a second list, evaluated by the branchy per-vertex path in full
-// rounds.  Entries of one round are distinct, so each round adds to distinct slots.
+// evaluates one piece's near-field list, one entry per lane and round, by the shared
+// divided-difference table (all branches alike).  Entries it leaves (three clustered knots,
+// three zero knots) are appended to the drain's fallback list as (queue slot << 10 | entry),
+// evaluated later for all pieces of the drain together.  Entries of one round are distinct, so
+// each round adds to distinct slots.
 template <bool FP64, typename T>
 __device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D0l, const T f[4], T vr,
-                                          const T *s_w, const T *s_wl, const short *list, int n, short *fb,
-                                          T *sR, T *cR, T *sI, T *cI, float tau, int &nfp64) {
+                                          const T *s_w, const T *s_wl, const short *list, int n, int slot,
+                                          int *fb, int &nfb, T *sR, T *cR, T *sI, T *cI) {
   const int lane = threadIdx.x & 31;
-  int nfb = 0;
-  auto fallback = [&]() {  // warp-uniform
-    for (int base = 0; base < nfb; base += 32) {
-      const int k = base + lane;
-      if (k < nfb) {
-        const int ent = fb[k];
-        T x[4];
-        bool neg;
-        near_knots<FP64>(ent, d, e, D0h, D0l, s_w, s_wl, x, neg);
-        near_add(ent, near_term<FP64>(x, f, tau, nfp64), x, f, vr, neg, sR, cR, sI, cI);
-      }
-      __syncwarp();
-    }
-    nfb = 0;
-  };
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
     bool left = false;
@@ -306,12 +293,10 @@ __device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D
       }
     }
     const unsigned bal = __ballot_sync(kFull, left);
-    if (left) fb[nfb + __popc(bal & ((1u << lane) - 1u))] = (short)ent;
+    if (left) fb[nfb + __popc(bal & ((1u << lane) - 1u))] = (slot << 10) | ent;
     nfb += __popc(bal);
     __syncwarp();
-    if (nfb > 32 * 7) fallback();  // the second list holds 256 entries
   }
-  fallback();
 }
 
 template <bool FP64>
@@ -323,7 +308,8 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
               unsigned long long *__restrict__ counters) {
   using T = typename std::conditional<FP64, double, float>::type;
   using S = DynShape<FP64>;
-  constexpr int W = S::warps, KM = S::KM, KF = S::KF, KG = S::KG, DC = S::DC;
+  constexpr int W = S::warps, KM = S::KM, KF = S::KF, KG = S::KG, DC = S::DC, kFbCap = S::FB;
+  static_assert(kFbCap >= kNearCap + 32, "one piece's near list must fit the fallback list");
   constexpr int QC = 64;  // queue of final tetrahedra that evaluate frequencies themselves
   constexpr int NS = box_slots<FP64>();
   constexpr int KU = DC * KM > 32 * KF ? DC * KM : 32 * KF;  // per-warp scratch (T elements)
@@ -344,7 +330,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
   __shared__ short s_near[W][kNearCap];
-  __shared__ short s_fb[W][256];  // near-field entries the shared table leaves
+  __shared__ int s_fb[W][kFbCap];  // near-field entries the shared table leaves (slot << 10 | entry)
   __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
   extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
@@ -397,7 +383,49 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   // one queued final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr,
   // own far-field moments am[0..K)) on the frequencies its box (b >= 0) leaves to it, or on
   // all of them (b < 0); lanes own frequencies
-  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b) {
+  int nfb = 0;  // entries in the drain's fallback list
+  // the fallback list: per-vertex table, one entry per lane and round; results added one lane
+  // at a time in lane order (entries of one round may share a frequency)
+  auto fallback_drain = [&]() {
+    for (int base = 0; base < nfb; base += 32) {
+      const int k = base + lane;
+      T re = T(0), im = T(0);
+      int iw = 0;
+      bool has_im = false;
+      if (k < nfb) {
+        const int code = s_fb[wib][k], sl = code >> 10, ent = code & 1023;
+        T ee[4], ff[4], d[4], x[4];
+        const T D0h = s_qv[wib][sl][1], D0l = s_qv[wib][sl][2], vr = s_qv[wib][sl][0];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ee[i] = s_qe[wib][sl][i];
+          ff[i] = s_qf[wib][sl][i];
+          d[i] = D0h + ee[i];
+        }
+        bool neg;
+        near_knots<FP64>(ent, d, ee, D0h, D0l, s_w, s_wl, x, neg);
+        re = vr * near_term<FP64>(x, ff, tau, nfp64);
+        iw = ent >> 1;
+        if ((ent & 1) == 0 && x[0] < T(0) && x[3] > T(0)) {
+          has_im = true;
+          im = vr * delta_sum(x, ff, T(0)) * T(3.141592653589793);
+          if (neg) im = -im;
+        }
+      }
+      unsigned m = __ballot_sync(kFull, k < nfb);
+      while (m) {  // warp-uniform
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        if (lane == src) {
+          kadd_t(sR[wib][iw], cR[wib][iw], re);
+          if (has_im) kadd_t(sI[wib][iw], cI[wib][iw], im);
+        }
+        __syncwarp();
+      }
+    }
+    nfb = 0;
+  };
+  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b, int slot) {
     T d[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
@@ -436,15 +464,17 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       }
       if (nlist > kNearCap - 64) {  // flush a full list
         __syncwarp();
-        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, s_fb[wib], sR[wib], cR[wib],
-                        sI[wib], cI[wib], tau, nfp64);
+        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib],
+                        cR[wib], sI[wib], cI[wib]);
+        if (nfb > kFbCap - kNearCap) fallback_drain();
         nlist = 0;
         __syncwarp();
       }
     }
     __syncwarp();
-    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, s_fb[wib], sR[wib], cR[wib], sI[wib],
-                    cI[wib], tau, nfp64);
+    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib], cR[wib],
+                    sI[wib], cI[wib]);
+    if (nfb > kFbCap - kNearCap) fallback_drain();
     __syncwarp();
   };
   // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then each piece
@@ -470,8 +500,9 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         ff[i] = s_qf[wib][sl][i];
       }
       eval_piece(ee, ff, s_qv[wib][sl][0], s_qv[wib][sl][1], s_qv[wib][sl][2], scr + p * KM, s_pk[wib][p],
-                 s_qb[wib][sl]);
+                 s_qb[wib][sl], sl);
     }
+    fallback_drain();  // the ring slots of this round are still valid
     qh += n;
     __syncwarp();
   };

@@ -305,11 +305,19 @@ template <typename T> __device__ T inv_sum_table(const T xin[4], const T f[4]) {
 //   H_j[j..j] = g'(u_j) = 3 u_j^2 ln|u_j| + u_j^2,
 // so all four fourth divided differences g[u, u_j] = H_j[0..3] take four logarithms and six
 // reciprocals (the per-vertex table below takes twenty and forty divisions).  The result is
-// sum_j f_j H_j[0..3] / s.  Returns false, leaving the work to the per-vertex table (Taylor
-// branch for clusters), where two adjacent knots of one sign lie within 1/16 of their
-// magnitude (measured on random knots near a frequency: the recursion then stays within a
-// few times the per-vertex table's FP32 error), two knots are equal or three knots are 0.
-constexpr double kRhoShared = 0.0625;  // adjacent knots this close (relative) go to the table
+// sum_j f_j H_j[0..3] / s.
+// A pair of adjacent knots a < b of one sign with y = (b - a)/a small (|y| <= 1/8, ties
+// included) would cancel in the recursion; its three entries g[a,b], g[a,a,b], g[a,b,b] are
+// taken from the Taylor series about a instead (d = b - a):
+//   g[a,b]   = g'(a) + d g2(a)/2 + d^2 g3(a)/6 + d sum_{k>=4} T_k
+//   g[a,a,b] = g2(a)/2 + d g3(a)/6 + sum_{k>=4} T_k
+//   g[a,b,b] = g2(a)/2 + d g3(a)/3 + sum_{k>=4} (k-1) T_k
+// with the second and third derivatives g2 = 6t ln|t| + 5t, g3 = 6 ln|t| + 11, the higher ones
+// 6 (-1)^k (k-4)!/a^(k-3) (k >= 4), and T_k = (k-th derivative at a) d^(k-2)/k! =
+// 6 (-1)^k (k-4)!/k! a y^(k-2), which falls like y^k.  Returns false, leaving the work to the
+// per-vertex table, where two adjacent pairs both cluster (three knots together) or three knots
+// are 0.
+constexpr double kRhoShared = 0.125;  // adjacent knots this close (relative): series entries
 template <typename T> __device__ __forceinline__ bool inv_sum_shared(const T x[4], const T f[4], T &out) {
   const T s = tabs(x[0]) > tabs(x[3]) ? tabs(x[0]) : tabs(x[3]);
   if (s == T(0)) {
@@ -325,44 +333,67 @@ template <typename T> __device__ __forceinline__ bool inv_sum_shared(const T x[4
 #pragma unroll
   for (int i = 0; i < 4; ++i) nz += u[i] == T(0);
   if (nz >= 3) return false;
+  bool cl[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const T a = u[i], b = u[i + 1];
-    if (!(b > a)) return false;                                       // equal knots
-    if ((a > T(0) && b - a <= rho * a) || (b < T(0) && b - a <= rho * (-b))) return false;  // cluster
+    cl[i] = (a > T(0) && b - a <= rho * a) || (b < T(0) && b - a <= rho * (-b));
   }
-  T g[4], gp[4];
+  if ((cl[0] && cl[1]) || (cl[1] && cl[2])) return false;  // three knots together
+  T g[4], gp[4], L[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const T t = u[i], t2 = t * t;
-    const T L = t == T(0) ? T(0) : Num<T>::lg(tabs(t));
-    g[i] = t2 * t * L;
-    gp[i] = T(3) * t2 * L + t2;
+    L[i] = t == T(0) ? T(0) : Num<T>::lg(tabs(t));
+    g[i] = t2 * t * L[i];
+    gp[i] = T(3) * t2 * L[i] + t2;
   }
-  const T r01 = rcp(u[1] - u[0]), r12 = rcp(u[2] - u[1]), r23 = rcp(u[3] - u[2]);
+  // first-level entries of every adjacent pair: G1 = g[u_p, u_p+1], HL = g[u_p, u_p, u_p+1],
+  // HR = g[u_p, u_p+1, u_p+1]
+  T G1[3], HL[3], HR[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const T d = u[p + 1] - u[p];
+    if (!cl[p]) {
+      const T r = rcp(d);
+      G1[p] = (g[p + 1] - g[p]) * r;
+      HL[p] = (G1[p] - gp[p]) * r;
+      HR[p] = (gp[p + 1] - G1[p]) * r;
+    } else {
+      const T a = u[p], y = d / a, Lp = L[p];
+      const T g2 = T(6) * a * Lp + T(5) * a, g3 = T(6) * Lp + T(11);
+      // T_4 = a y^2 / 4; successive terms: T_{k+1} = -T_k (k-3) y / (k+1)
+      T t = T(0.25) * a * y * y;
+      T s0 = T(0), s1 = T(0);
+      for (int k = 4; k < 4 + Num<T>::kmax; ++k) {
+        s0 += t;
+        s1 += T(k - 1) * t;
+        if (tabs(t) <= Num<T>::tol * (tabs(s0) + tabs(g2) + tabs(g3))) break;
+        t *= -T(k - 3) * y / T(k + 1);
+      }
+      HL[p] = T(0.5) * g2 + d * g3 * T(1.0 / 6.0) + s0;
+      HR[p] = T(0.5) * g2 + d * g3 * T(1.0 / 3.0) + s1;
+      G1[p] = gp[p] + d * (T(0.5) * g2 + d * g3 * T(1.0 / 6.0) + s0);
+    }
+  }
   const T r02 = rcp(u[2] - u[0]), r13 = rcp(u[3] - u[1]), r03 = rcp(u[3] - u[0]);
-  const T G01 = (g[1] - g[0]) * r01, G12 = (g[2] - g[1]) * r12, G23 = (g[3] - g[2]) * r23;
-  const T G012 = (G12 - G01) * r02, G123 = (G23 - G12) * r13;
+  const T G012 = (G1[1] - G1[0]) * r02, G123 = (G1[2] - G1[1]) * r13;
   const T G0123 = (G123 - G012) * r03;
   T R[4];
   {  // j = 0
-    const T h01 = (G01 - gp[0]) * r01;
-    const T h02 = (G012 - h01) * r02;
+    const T h02 = (G012 - HL[0]) * r02;
     R[0] = (G0123 - h02) * r03;
   }
   {  // j = 1
-    const T h01 = (gp[1] - G01) * r01, h12 = (G12 - gp[1]) * r12;
-    const T h02 = (h12 - h01) * r02, h13 = (G123 - h12) * r13;
+    const T h02 = (HL[1] - HR[0]) * r02, h13 = (G123 - HL[1]) * r13;
     R[1] = (h13 - h02) * r03;
   }
   {  // j = 2
-    const T h12 = (gp[2] - G12) * r12, h23 = (G23 - gp[2]) * r23;
-    const T h02 = (h12 - G012) * r02, h13 = (h23 - h12) * r13;
+    const T h02 = (HR[1] - G012) * r02, h13 = (HL[2] - HR[1]) * r13;
     R[2] = (h13 - h02) * r03;
   }
   {  // j = 3
-    const T h23 = (gp[3] - G23) * r23;
-    const T h13 = (h23 - G123) * r13;
+    const T h13 = (HR[2] - G123) * r13;
     R[3] = (h13 - G0123) * r03;
   }
   out = (f[0] * R[0] + f[1] * R[1] + f[2] * R[2] + f[3] * R[3]) * si;
