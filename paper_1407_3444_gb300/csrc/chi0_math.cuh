@@ -314,9 +314,9 @@ template <typename T> __device__ T inv_sum_table(const T xin[4], const T f[4]) {
 //   g[a,b,b] = g2(a)/2 + d g3(a)/3 + sum_{k>=4} (k-1) T_k
 // with the second and third derivatives g2 = 6t ln|t| + 5t, g3 = 6 ln|t| + 11, the higher ones
 // 6 (-1)^k (k-4)!/a^(k-3) (k >= 4), and T_k = (k-th derivative at a) d^(k-2)/k! =
-// 6 (-1)^k (k-4)!/k! a y^(k-2), which falls like y^k.  Returns false, leaving the work to the
-// per-vertex table, where two adjacent pairs both cluster (three knots together) or three knots
-// are 0.
+// 6 (-1)^k (k-4)!/k! a y^(k-2), which falls like y^k.  Two knots at 0 give the limits
+// g'(0) = g''(0)/2 = 0.  Returns false, leaving the work to the per-vertex table, where two
+// adjacent pairs both cluster (three knots together) or three knots are 0.
 constexpr double kRhoShared = 0.125;  // adjacent knots this close (relative): series entries
 template <typename T> __device__ __forceinline__ bool inv_sum_shared(const T x[4], const T f[4], T &out) {
   const T s = tabs(x[0]) > tabs(x[3]) ? tabs(x[0]) : tabs(x[3]);
@@ -354,7 +354,11 @@ template <typename T> __device__ __forceinline__ bool inv_sum_shared(const T x[4
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const T d = u[p + 1] - u[p];
-    if (!cl[p]) {
+    if (!cl[p] && !(d > T(0))) {  // two knots at 0 (a tie elsewhere is clustered): the limits
+      G1[p] = T(0);               // g'(0) = 0 and g''(0)/2 = 0
+      HL[p] = T(0);
+      HR[p] = T(0);
+    } else if (!cl[p]) {
       const T r = rcp(d);
       G1[p] = (g[p + 1] - g[p]) * r;
       HL[p] = (G1[p] - gp[p]) * r;
