@@ -207,19 +207,6 @@ def test_dynamic_free_electron_open_grid(C, O):
     assert nerr(gi[1:], np.array(ref_i)[1:]) < 1e-12
 
 
-# ------------------------------------------------------------------------ full sizes (sampled)
-def test_cr_like_full_size_sampled_q(C, O):
-    """The bench workload's mesh and bands (48^3, 663,552 tetrahedra, 9 bands) at two of its
-    q points (one on Gamma-X, one on M-Gamma), FP64 and mixed, against the oracle."""
-    import os
-    qs = wl.path_points([(0, 0, 0), (0.5, 0, 0), (0.5, 0.5, 0), (0, 0, 0)], 256)[[37, 201]]
-    W = wl.cr_like(n=48, nq=2, qfracs=qs, nproc=min(16, os.cpu_count() or 1))
-    ref = np.array([O.chi0_q(W, q) for q in W.qs])
-    for prec in ("fp64", "mixed"):
-        got = run_static(C, W, prec)
-        assert nerr(got[:, None], ref[:, None]) < TOL[prec], (prec, got, ref)
-
-
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_band_sweep_40_bands_windows(C, O, prec):
     """40-band random model (the band-truncation sweep's generator) on a 10^3 mesh: on-grid
@@ -282,50 +269,3 @@ def test_autotuner_picks_a_shape_and_keeps_results(C, O):
     assert nerr(gi.cpu().numpy(), np.array(ref_i)) < TOL["mixed"]
     P.close()
     P2.close()
-
-
-def _sampled_err(got, ref, static_ref):
-    """max |got - ref| over sampled frequencies, relative to max(|sampled ref|, |static chi0|):
-    the normwise error of the full frequency grid has max_w |chi0| >= |chi0(w = 0)| in its
-    denominator, which the static value bounds from below without the whole grid; for Im the
-    same scale states absolute errors in units of the static value."""
-    got, ref = np.ravel(got), np.ravel(ref)
-    scale = max(float(np.max(np.abs(ref))), abs(float(static_ref)))
-    return float(np.max(np.abs(got - ref))) / scale
-
-
-def test_fese_like_full_size_sampled_w(C, O):
-    """The FeSe-like dynamic workload at its full mesh (64x64x16, 393,216 tetrahedra, 10 bands)
-    and full 512-frequency grid (two passes of the dynamic kernel, as the bench runs it) for one
-    q on Gamma-M; one sampled frequency of the second pass against the oracle."""
-    import os
-    W = wl.fese_like(n=(64, 64, 16), nq=64, qfracs=[np.array([0.5, 0.5, 0.0]) * 5 / 64],
-                     nproc=min(16, os.cpu_count() or 1))
-    omega, W.omega = W.omega, None
-    static_ref = O.chi0_q(W, W.qs[0])
-    pick = np.array([300])
-    ref_r, ref_i = O.chi0_q(W, W.qs[0], omega=omega[pick])
-    gr, gi = run_dynamic(C, W, "mixed", omega)
-    gr, gi = np.reshape(gr, (1, -1)), np.reshape(gi, (1, -1))
-    assert _sampled_err(gr[0][pick], ref_r, static_ref) < TOL["mixed"]
-    assert _sampled_err(gi[0][pick], ref_i, static_ref) < TOL["mixed"]
-
-
-def test_band_sweep_full_size_sampled_q(C, O):
-    """The 40-band sweep at its full mesh (32^3) with all 128 q and their windows in one call
-    (static, as the bench runs it) and one q dynamic on the full 128-frequency grid; the q with
-    the narrowest window and two of its frequencies sampled against the oracle."""
-    import os
-    W = wl.band_sweep(n=32, nb=40, nq=128, nw=128, nproc=min(16, os.cpu_count() or 1))
-    omega, W.omega = W.omega, None
-    iq = int(np.argmin([q.window[1] - q.window[0] for q in W.qs]))
-    ref = O.chi0_q(W, W.qs[iq])
-    got = np.ravel(run_static(C, W, "mixed"))
-    assert abs(got[iq] - ref) < TOL["mixed"] * abs(ref)
-    W.qs = [W.qs[iq]]
-    pick = np.array([31, 100])
-    ref_r, ref_i = O.chi0_q(W, W.qs[0], omega=omega[pick])
-    gr, gi = run_dynamic(C, W, "mixed", omega)
-    gr, gi = np.reshape(gr, (1, -1)), np.reshape(gi, (1, -1))
-    assert _sampled_err(gr[0][pick], ref_r, ref) < TOL["mixed"]
-    assert _sampled_err(gi[0][pick], ref_i, ref) < TOL["mixed"]
