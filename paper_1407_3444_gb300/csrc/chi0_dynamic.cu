@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   constexpr int kListCap = 256;  // far / near drain list entries per warp (flushed above 192)
   constexpr int QC = 64;  // queue of final tetrahedra that evaluate frequencies themselves
   constexpr int NS = box_slots<FP64>();
-  constexpr int KU = DC * KM > 32 * KF ? DC * KM : 32 * KF;  // per-warp scratch (T elements)
+  constexpr int SKM = KM + 1, SKF = KF + 1;  // per-lane strides of the scratch (odd: no bank conflicts)
+  constexpr int KU = DC * SKM > 32 * SKF ? DC * SKM : 32 * SKF;  // per-warp scratch (T elements)
   static_assert(QC >= DC + 32, "one carving step adds at most 32 queued pieces");
   __shared__ int s_c[W][32][4], s_cq[W][32][4];
   __shared__ T s_vol[W][32];
@@ -271,15 +272,14 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   __shared__ T s_scr[W][KU];
   __shared__ int s_pk[W][DC];
   // ring queue: offsets e from D0 (sorted), values f, (weight, D0h, D0l), box
-  __shared__ T s_qe[W][QC][4], s_qf[W][QC][4], s_qv[W][QC][3];
+  __shared__ T s_qe[W][4][QC], s_qf[W][4][QC], s_qv[W][3][QC];
   __shared__ int s_qb[W][QC];
   __shared__ T sR[W][kNWPass], sI[W][kNWPass];
   __shared__ T cR[W][kNWPass], cI[W][kNWPass];  // compensation terms
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
-  // drain lists (far, near) and the near entries the shared table leaves (fallback)
-  __shared__ int s_fl[W][kListCap], s_nl2[W][kListCap], s_fb[W][kFbCap];
-  __shared__ T s_pc[W][DC], s_ph[W][DC];  // midpoint and half-width of the drained pieces
+  // the drain's near list and the near entries the shared table leaves (fallback)
+  __shared__ int s_nl2[W][kListCap], s_fb[W][kFbCap];
   __shared__ T s_gv[W][32], s_gi[W][32];  // one round's values, summed per frequency
   __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
@@ -330,13 +330,12 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   const bool boxes = s_tab.on != 0;
   int nfp64 = 0, npieces = 0, nboxed = 0;
   int qh = 0, qt = 0;  // ring queue head and tail (warp-uniform)
-  // Queued pieces are evaluated in drains of up to DC: every (piece, frequency, term) that its
-  // box leaves to it becomes an entry of one of two warp lists, the far list (own moment series
-  // about the piece's midpoint, Horner) or the near list (divided-difference table, and the delta
-  // term inside the knot range); each list is then evaluated 32 entries per round, one per lane,
-  // whatever piece they come from.  Entries of one round that hit the same frequency are summed
-  // in lane order by the lowest of them before the compensated add (deterministic).
-  int nfb = 0, nfar = 0, nnear = 0;
+  // Queued pieces are evaluated in drains of up to DC.  The near-field entries (divided-difference
+  // table, and the delta term inside the knot range) of all pieces of a drain go to one list
+  // evaluated 32 entries per round, one per lane, whatever piece they come from; entries of one
+  // round that hit the same frequency are summed in lane order by the lowest of them before the
+  // compensated add (deterministic).
+  int nfb = 0, nnear = 0;
   auto group_add = [&](bool act, int iw, T re, T im) {
     const int key = act ? iw : -1 - lane;  // inactive lanes: keys of their own
     const unsigned grp = __match_any_sync(kFull, key);
@@ -364,11 +363,11 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       if (k < nfb) {
         const int code = s_fb[wib][k], sl = code >> 10, ent = code & 1023;
         T ee[4], ff[4], d[4], x[4];
-        const T D0h = s_qv[wib][sl][1], D0l = s_qv[wib][sl][2], vr = s_qv[wib][sl][0];
+        const T D0h = s_qv[wib][1][sl], D0l = s_qv[wib][2][sl], vr = s_qv[wib][0][sl];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          ee[i] = s_qe[wib][sl][i];
-          ff[i] = s_qf[wib][sl][i];
+          ee[i] = s_qe[wib][i][sl];
+          ff[i] = s_qf[wib][i][sl];
           d[i] = D0h + ee[i];
         }
         bool neg;
@@ -396,11 +395,11 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         code = s_nl2[wib][k];
         const int sl = code >> 10, ent = code & 1023;
         T ee[4], ff[4], d[4], x[4];
-        const T D0h = s_qv[wib][sl][1], D0l = s_qv[wib][sl][2], vr = s_qv[wib][sl][0];
+        const T D0h = s_qv[wib][1][sl], D0l = s_qv[wib][2][sl], vr = s_qv[wib][0][sl];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          ee[i] = s_qe[wib][sl][i];
-          ff[i] = s_qf[wib][sl][i];
+          ee[i] = s_qe[wib][i][sl];
+          ff[i] = s_qf[wib][i][sl];
           d[i] = D0h + ee[i];
         }
         bool neg;
@@ -431,77 +430,59 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
     nnear = 0;
   };
-  // the far list: entry = drained piece << 10 | (2 * frequency + term)
-  auto far_drain = [&]() {
-    for (int base = 0; base < nfar; base += 32) {
-      const int k = base + lane;
-      T re = T(0);
-      int iw = 0;
-      if (k < nfar) {
-        const int code = s_fl[wib][k], p = code >> 10, ent = code & 1023;
-        iw = ent >> 1;
-        const T om = tabs(s_w[iw]), c = s_pc[wib][p], half = s_ph[wib][p];
-        const T sh = (ent & 1) ? -om : om;
-        const T den = c - sh;
-        re = s_qv[wib][(qh + p) % QC][0] * far_eval(scr + p * KM, s_pk[wib][p], c, sh, half / tabs(den));
-      }
-      group_add(k < nfar, iw, re, T(0));
-    }
-    nfar = 0;
-  };
-  // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then the entries
-  // of every piece, sorted into the two lists and evaluated in full rounds
+  // evaluates n <= DC queued pieces: own far-field moments one piece per lane; then each piece
+  // on the frequencies its box leaves to it, lanes owning frequencies: the own moment series
+  // (Horner) where the piece is far from the frequency, otherwise an entry of the near list,
+  // which collects the entries of all pieces of the drain and is evaluated in full rounds
   auto drain = [&](int n) {
     if (lane < n) {
       const int sl = (qh + lane) % QC;
       T d[4], ff[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        d[i] = s_qv[wib][sl][1] + s_qe[wib][sl][i];
-        ff[i] = s_qf[wib][sl][i];
+        d[i] = s_qv[wib][1][sl] + s_qe[wib][i][sl];
+        ff[i] = s_qf[wib][i][sl];
       }
-      s_pk[wib][lane] = far_moments<T, KM>(d, ff, scr + lane * KM);
-      const T D0h = s_qv[wib][sl][1];
-      s_pc[wib][lane] = D0h + (s_qe[wib][sl][0] + s_qe[wib][sl][3]) * T(0.5);
-      s_ph[wib][lane] = (s_qe[wib][sl][3] - s_qe[wib][sl][0]) * T(0.5);
+      s_pk[wib][lane] = far_moments<T, KM>(d, ff, scr + lane * SKM);
     }
     __syncwarp();
     for (int p = 0; p < n; ++p) {  // warp-uniform
       const int sl = (qh + p) % QC;
       const int b = s_qb[wib][sl];
-      const T c = s_pc[wib][p], half = s_ph[wib][p];
+      const T D0h = s_qv[wib][1][sl], vr = s_qv[wib][0][sl];
+      const T c = D0h + (s_qe[wib][0][sl] + s_qe[wib][3][sl]) * T(0.5);
+      const T half = (s_qe[wib][3][sl] - s_qe[wib][0][sl]) * T(0.5);
+      const T *am = scr + p * SKM;
+      const int K = s_pk[wib][p];
       const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
       const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
       for (int iw0 = lo; iw0 < hi; iw0 += 32) {
         const int iw = iw0 + lane;
-        bool far_t[2] = {false, false}, near_t[2] = {false, false};
+        bool near_t[2] = {false, false};
         if (iw < hi) {
           const T om = tabs(s_w[iw]);
+          T re = T(0);
 #pragma unroll
           for (int term = 0; term < 2; ++term) {
             if (b < 0 || !box_far(Cb, Rb, b, om, term)) {
-              const T den = term ? c + om : c - om;
-              const T ratio = half / tabs(den);
-              if (ratio <= T(Num<T>::kappa_far)) far_t[term] = true;
+              const T sh = term ? -om : om;
+              const T ratio = half / tabs(c - sh);
+              if (ratio <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, sh, ratio);
               else near_t[term] = true;
             }
           }
+          if (re != T(0)) kadd_t(sR[wib][iw], cR[wib][iw], vr * re);
         }
 #pragma unroll
         for (int term = 0; term < 2; ++term) {
-          const unsigned bf = __ballot_sync(kFull, far_t[term]);
-          if (far_t[term]) s_fl[wib][nfar + __popc(bf & lt)] = (p << 10) | (iw * 2 + term);
-          nfar += __popc(bf);
           const unsigned bn = __ballot_sync(kFull, near_t[term]);
           if (near_t[term]) s_nl2[wib][nnear + __popc(bn & lt)] = (sl << 10) | (iw * 2 + term);
           nnear += __popc(bn);
         }
         __syncwarp();
-        if (nfar > kListCap - 64) far_drain();
         if (nnear > kListCap - 64) near_drain();
       }
     }
-    far_drain();
     near_drain();
     fallback_drain();  // the ring slots of this drain are still valid
     qh += n;
@@ -525,7 +506,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         T e[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) e[i] = (base + ee[i]) * ri;
-        box_moments(e, ff, vr, scr + lane * KF, b < kBoxFine ? KF : KG);
+        box_moments(e, ff, vr, scr + lane * SKF, b < kBoxFine ? KF : KG);
         ++nboxed;
       }
     }
@@ -536,7 +517,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       mask &= mask - 1u;
       const int bp = __shfl_sync(kFull, b, p);
       const int K = bp < kBoxFine ? KF : KG, base = slot_base<FP64>(bp);
-      for (int k = lane; k < K; k += 32) acc[base + k] += scr[p * KF + k];
+      for (int k = lane; k < K; k += 32) acc[base + k] += scr[p * SKF + k];
     }
     const bool queue = has && b < kBoxFine;
     const unsigned qm = __ballot_sync(kFull, queue);
@@ -544,12 +525,12 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       const int sl = (qt + __popc(qm & lt)) % QC;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        s_qe[wib][sl][i] = ee[i];
-        s_qf[wib][sl][i] = ff[i];
+        s_qe[wib][i][sl] = ee[i];
+        s_qf[wib][i][sl] = ff[i];
       }
-      s_qv[wib][sl][0] = vr;
-      s_qv[wib][sl][1] = D0h;
-      s_qv[wib][sl][2] = D0l;
+      s_qv[wib][0][sl] = vr;
+      s_qv[wib][1][sl] = D0h;
+      s_qv[wib][2][sl] = D0l;
       s_qb[wib][sl] = b;
     }
     qt += __popc(qm);
