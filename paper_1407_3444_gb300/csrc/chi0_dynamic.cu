@@ -63,6 +63,7 @@ using grid::kFull;
 using grid::tet_corners;
 
 constexpr int kNWPass = 256;   // frequencies per dynamic pass
+constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed per warp
 
 template <bool FP64> struct DynShape {
   static constexpr int threads = FP64 ? 64 : 128;
@@ -71,7 +72,7 @@ template <bool FP64> struct DynShape {
   static constexpr int KM = FP64 ? 64 : 32;  // own far-field moments kept per queued piece
   static constexpr int NF = FP64 ? 3 : 2;    // a fine box stands in beyond NF radii
   static constexpr int KF = FP64 ? 28 : 24;  // moments of a fine box   (truncation NF^-KF)
-  static constexpr int FB = 256;             // near-field entries left to the per-vertex table
+  static constexpr int FB = FP64 ? 576 : 640;  // near-field entries left to the per-vertex table
   static constexpr int KG = FP64 ? 22 : 12;  // moments of a geometric box ((2/9)^KG)
 };
 
@@ -176,7 +177,7 @@ template <typename T> __device__ __forceinline__ int box_of(T c, T s, const BoxT
 }
 
 // moments m_k = v 6 k!/(k+4)! sum_j f_j h_k(e, e_j), k < K, of a piece about a box (e = (d - C)/R)
-template <typename T> __device__ __forceinline__ void box_moments(const T e[4], const T f[4], T v, T *m, int K) {
+template <typename T> __device__ __noinline__ void box_moments_ol(const T e[4], const T f[4], T v, T *m, int K) {
   T H[4] = {T(1), T(1), T(1), T(1)};
   T P[4] = {T(1), T(1), T(1), T(1)};
   m[0] = v * T(0.25) * (f[0] + f[1] + f[2] + f[3]);
@@ -193,6 +194,20 @@ template <typename T> __device__ __forceinline__ void box_moments(const T e[4], 
     m[k] = v * tabs(series_coef<T>(k)) * sj;
   }
 }
+
+// Out-of-line copies of the large per-piece helpers: the weight kernel calls each from a few
+// places, and inlined copies made its body overflow the instruction cache (ncu: 45% of the issue
+// stalls waiting for instructions).
+template <typename T, int KM>
+__device__ __noinline__ int far_moments_ol(const T d[4], const T f[4], T *a) { return far_moments<T, KM>(d, f, a); }
+template <typename T> __device__ __noinline__ T far_eval_ol(const T *a, int K, T c, T w, T rho) {
+  return far_eval(a, K, c, w, rho);
+}
+template <typename T> __device__ __noinline__ bool inv_sum_shared_ol(const T x[4], const T f[4], T &out) {
+  return inv_sum_shared(x, f, out);
+}
+template <typename T> __device__ __noinline__ T series_sum_ol(const T x[4], const T f[4]) { return series_sum(x, f); }
+template <typename T> __device__ __noinline__ T delta_sum_ol(const T d[4], const T f[4]) { return delta_sum(d, f, T(0)); }
 
 // does box b stand in for term (0: 1/(D - u), 1: 1/(D + u)) at frequency u = om?  Fine boxes
 // only near themselves; geometric boxes always.  Same expression in both kernels.
@@ -247,6 +262,57 @@ __device__ __forceinline__ void near_knots(int ent, const T d[4], const T e[4], 
   }
 }
 
+// adds one near-field result: the two terms of a frequency may both be in one round, so they
+// are added one term at a time; the delta term where |w| lies inside the knot range
+template <typename T>
+__device__ __forceinline__ void near_add(int ent, T re, const T x[4], const T f[4], T vr, bool neg, T *sR, T *cR,
+                                         T *sI, T *cI) {
+  const int iw = ent >> 1, sgn = ent & 1;
+  for (int t2 = 0; t2 < 2; ++t2) {
+    if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
+    __syncwarp(__activemask());
+  }
+  if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {
+    const T im = delta_sum_ol(x, f) * T(3.141592653589793);
+    kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
+  }
+}
+
+// evaluates one piece's near-field list, one entry per lane and round, by the shared
+// divided-difference table (all branches alike).  Entries it leaves (three clustered knots,
+// three zero knots) are appended to the drain's fallback list as (queue slot << 10 | entry),
+// evaluated later for all pieces of the drain together.  Entries of one round are distinct, so
+// each round adds to distinct slots.
+template <bool FP64, typename T>
+__device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D0l, const T f[4], T vr,
+                                          const T *s_w, const T *s_wl, const short *list, int n, int slot,
+                                          int *fb, int &nfb, T *sR, T *cR, T *sI, T *cI) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    const int k = base + lane;
+    bool left = false;
+    int ent = 0;
+    if (k < n) {
+      ent = list[k];
+      T x[4];
+      bool neg;
+      near_knots<FP64>(ent, d, e, D0h, D0l, s_w, s_wl, x, neg);
+      T re;
+      if (series_ok(x, T(Num<T>::kappa))) {
+        near_add(ent, series_sum_ol(x, f), x, f, vr, neg, sR, cR, sI, cI);
+      } else if (inv_sum_shared_ol(x, f, re)) {
+        near_add(ent, re, x, f, vr, neg, sR, cR, sI, cI);
+      } else {
+        left = true;
+      }
+    }
+    const unsigned bal = __ballot_sync(kFull, left);
+    if (left) fb[nfb + __popc(bal & ((1u << lane) - 1u))] = (slot << 10) | ent;
+    nfb += __popc(bal);
+    __syncwarp();
+  }
+}
+
 template <bool FP64>
 __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     k_dynamic(Grid g, Tet tet, const void *__restrict__ Ek, const void *__restrict__ Ekq, Q q,
@@ -257,7 +323,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   using T = typename std::conditional<FP64, double, float>::type;
   using S = DynShape<FP64>;
   constexpr int W = S::warps, KM = S::KM, KF = S::KF, KG = S::KG, DC = S::DC, kFbCap = S::FB;
-  constexpr int kListCap = 256;  // far / near drain list entries per warp (flushed above 192)
+  static_assert(kFbCap >= kNearCap + 32, "one piece's near list must fit the fallback list");
   constexpr int QC = 64;  // queue of final tetrahedra that evaluate frequencies themselves
   constexpr int NS = box_slots<FP64>();
   constexpr int SKM = KM + 1, SKF = KF + 1;  // per-lane strides of the scratch (odd: no bank conflicts)
@@ -272,15 +338,14 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   __shared__ T s_scr[W][KU];
   __shared__ int s_pk[W][DC];
   // ring queue: offsets e from D0 (sorted), values f, (weight, D0h, D0l), box
-  __shared__ T s_qe[W][4][QC], s_qf[W][4][QC], s_qv[W][3][QC];
+  __shared__ T s_qe[W][QC][4], s_qf[W][QC][4], s_qv[W][QC][3];
   __shared__ int s_qb[W][QC];
   __shared__ T sR[W][kNWPass], sI[W][kNWPass];
   __shared__ T cR[W][kNWPass], cI[W][kNWPass];  // compensation terms
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
-  // the drain's near list and the near entries the shared table leaves (fallback)
-  __shared__ int s_nl2[W][kListCap], s_fb[W][kFbCap];
-  __shared__ T s_gv[W][32], s_gi[W][32];  // one round's values, summed per frequency
+  __shared__ short s_near[W][kNearCap];
+  __shared__ int s_fb[W][kFbCap];  // near-field entries the shared table leaves (slot << 10 | entry)
   __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
   extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
@@ -330,44 +395,26 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   const bool boxes = s_tab.on != 0;
   int nfp64 = 0, npieces = 0, nboxed = 0;
   int qh = 0, qt = 0;  // ring queue head and tail (warp-uniform)
-  // Queued pieces are evaluated in drains of up to DC.  The near-field entries (divided-difference
-  // table, and the delta term inside the knot range) of all pieces of a drain go to one list
-  // evaluated 32 entries per round, one per lane, whatever piece they come from; entries of one
-  // round that hit the same frequency are summed in lane order by the lowest of them before the
-  // compensated add (deterministic).
-  int nfb = 0, nnear = 0;
-  auto group_add = [&](bool act, int iw, T re, T im) {
-    const int key = act ? iw : -1 - lane;  // inactive lanes: keys of their own
-    const unsigned grp = __match_any_sync(kFull, key);
-    s_gv[wib][lane] = re;
-    s_gi[wib][lane] = im;
-    __syncwarp();
-    if (act && lane == __ffs(grp) - 1) {
-      T sr = T(0), si = T(0);
-      for (unsigned m = grp; m; m &= m - 1u) {
-        const int src = __ffs(m) - 1;
-        sr += s_gv[wib][src];
-        si += s_gi[wib][src];
-      }
-      kadd_t(sR[wib][iw], cR[wib][iw], sr);
-      if (si != T(0)) kadd_t(sI[wib][iw], cI[wib][iw], si);
-    }
-    __syncwarp();
-  };
-  // the fallback list (three clustered or three zero knots): the per-vertex table
+  // one queued final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr,
+  // own far-field moments am[0..K)) on the frequencies its box (b >= 0) leaves to it, or on
+  // all of them (b < 0); lanes own frequencies
+  int nfb = 0;  // entries in the drain's fallback list
+  // the fallback list: per-vertex table, one entry per lane and round; results added one lane
+  // at a time in lane order (entries of one round may share a frequency)
   auto fallback_drain = [&]() {
     for (int base = 0; base < nfb; base += 32) {
       const int k = base + lane;
       T re = T(0), im = T(0);
       int iw = 0;
+      bool has_im = false;
       if (k < nfb) {
         const int code = s_fb[wib][k], sl = code >> 10, ent = code & 1023;
         T ee[4], ff[4], d[4], x[4];
-        const T D0h = s_qv[wib][1][sl], D0l = s_qv[wib][2][sl], vr = s_qv[wib][0][sl];
+        const T D0h = s_qv[wib][sl][1], D0l = s_qv[wib][sl][2], vr = s_qv[wib][sl][0];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          ee[i] = s_qe[wib][i][sl];
-          ff[i] = s_qf[wib][i][sl];
+          ee[i] = s_qe[wib][sl][i];
+          ff[i] = s_qf[wib][sl][i];
           d[i] = D0h + ee[i];
         }
         bool neg;
@@ -375,116 +422,102 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         re = vr * near_term<FP64>(x, ff, tau, nfp64);
         iw = ent >> 1;
         if ((ent & 1) == 0 && x[0] < T(0) && x[3] > T(0)) {
-          im = vr * delta_sum(x, ff, T(0)) * T(3.141592653589793);
+          has_im = true;
+          im = vr * delta_sum_ol(x, ff) * T(3.141592653589793);
           if (neg) im = -im;
         }
       }
-      group_add(k < nfb, iw, re, im);
+      unsigned m = __ballot_sync(kFull, k < nfb);
+      while (m) {  // warp-uniform
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        if (lane == src) {
+          kadd_t(sR[wib][iw], cR[wib][iw], re);
+          if (has_im) kadd_t(sI[wib][iw], cI[wib][iw], im);
+        }
+        __syncwarp();
+      }
     }
     nfb = 0;
   };
-  // the near list: entry = ring slot << 10 | (2 * frequency + term)
-  auto near_drain = [&]() {
-    for (int base = 0; base < nnear; base += 32) {
-      const int k = base + lane;
-      T re = T(0), im = T(0);
-      int iw = 0;
-      bool act = false, left = false;
-      int code = 0;
-      if (k < nnear) {
-        code = s_nl2[wib][k];
-        const int sl = code >> 10, ent = code & 1023;
-        T ee[4], ff[4], d[4], x[4];
-        const T D0h = s_qv[wib][1][sl], D0l = s_qv[wib][2][sl], vr = s_qv[wib][0][sl];
+  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b, int slot) {
+    T d[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          ee[i] = s_qe[wib][i][sl];
-          ff[i] = s_qf[wib][i][sl];
-          d[i] = D0h + ee[i];
-        }
-        bool neg;
-        near_knots<FP64>(ent, d, ee, D0h, D0l, s_w, s_wl, x, neg);
-        iw = ent >> 1;
-        T v;
-        if (series_ok(x, T(Num<T>::kappa))) {
-          v = series_sum(x, ff);
-          act = true;
-        } else if (inv_sum_shared(x, ff, v)) {
-          act = true;
-        } else {
-          left = true;
-        }
-        if (act) {
-          re = vr * v;
-          if ((ent & 1) == 0 && x[0] < T(0) && x[3] > T(0)) {
-            im = vr * delta_sum(x, ff, T(0)) * T(3.141592653589793);
-            if (neg) im = -im;
-          }
-        }
+    for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
+    const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
+    const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
+    const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
+    // far field for both terms (Horner on the moments); near-field frequencies are
+    // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
+    unsigned nearm = 0u, nearp = 0u;
+    for (int iw = lo + lane, itn = 0; iw < hi; iw += 32, ++itn) {
+      const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
+      T re = T(0);
+      if (b < 0 || !box_far(Cb, Rb, b, om, 1)) {
+        const T rp = half / (c + om);
+        if (rp <= T(Num<T>::kappa_far)) re += far_eval_ol(am, K, c, -om, rp);
+        else nearp |= 1u << itn;
       }
-      const unsigned bal = __ballot_sync(kFull, left);
-      if (left) s_fb[wib][nfb + __popc(bal & lt)] = code;
-      nfb += __popc(bal);
-      group_add(act, iw, re, im);
-      if (nfb > kFbCap - 32) fallback_drain();
+      if (b < 0 || !box_far(Cb, Rb, b, om, 0)) {
+        const T dm = c - om;
+        const T rm = half / (dm < T(0) ? -dm : dm);
+        if (rm <= T(Num<T>::kappa_far)) re += far_eval_ol(am, K, c, om, rm);
+        else nearm |= 1u << itn;
+      }
+      if (re != T(0)) kadd_t(sR[wib][iw], cR[wib][iw], vr * re);
     }
-    nnear = 0;
+    // near field: compact the (frequency, term) pairs of the warp into a list
+    int nlist = 0;
+    const int nit = (hi - lo + 31) >> 5;
+    for (int itn = 0; itn < nit; ++itn) {
+#pragma unroll
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
+        const unsigned bal = __ballot_sync(kFull, mine);
+        if (mine) s_near[wib][nlist + __popc(bal & lt)] = (short)((lo + itn * 32 + lane) * 2 + sgn);
+        nlist += __popc(bal);
+      }
+      if (nlist > kNearCap - 64) {  // flush a full list
+        __syncwarp();
+        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib],
+                        cR[wib], sI[wib], cI[wib]);
+        if (nfb > kFbCap - kNearCap) fallback_drain();
+        nlist = 0;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib], cR[wib],
+                    sI[wib], cI[wib]);
+    if (nfb > kFbCap - kNearCap) fallback_drain();
+    __syncwarp();
   };
-  // evaluates n <= DC queued pieces: own far-field moments one piece per lane; then each piece
-  // on the frequencies its box leaves to it, lanes owning frequencies: the own moment series
-  // (Horner) where the piece is far from the frequency, otherwise an entry of the near list,
-  // which collects the entries of all pieces of the drain and is evaluated in full rounds
+  // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then each piece
+  // on its frequencies with the whole warp
   auto drain = [&](int n) {
     if (lane < n) {
       const int sl = (qh + lane) % QC;
       T d[4], ff[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        d[i] = s_qv[wib][1][sl] + s_qe[wib][i][sl];
-        ff[i] = s_qf[wib][i][sl];
+        d[i] = s_qv[wib][sl][1] + s_qe[wib][sl][i];
+        ff[i] = s_qf[wib][sl][i];
       }
-      s_pk[wib][lane] = far_moments<T, KM>(d, ff, scr + lane * SKM);
+      s_pk[wib][lane] = far_moments_ol<T, KM>(d, ff, scr + lane * SKM);
     }
     __syncwarp();
-    for (int p = 0; p < n; ++p) {  // warp-uniform
+    for (int p = 0; p < n; ++p) {
       const int sl = (qh + p) % QC;
-      const int b = s_qb[wib][sl];
-      const T D0h = s_qv[wib][1][sl], vr = s_qv[wib][0][sl];
-      const T c = D0h + (s_qe[wib][0][sl] + s_qe[wib][3][sl]) * T(0.5);
-      const T half = (s_qe[wib][3][sl] - s_qe[wib][0][sl]) * T(0.5);
-      const T *am = scr + p * SKM;
-      const int K = s_pk[wib][p];
-      const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
-      const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
-      for (int iw0 = lo; iw0 < hi; iw0 += 32) {
-        const int iw = iw0 + lane;
-        bool near_t[2] = {false, false};
-        if (iw < hi) {
-          const T om = tabs(s_w[iw]);
-          T re = T(0);
+      T ee[4], ff[4];
 #pragma unroll
-          for (int term = 0; term < 2; ++term) {
-            if (b < 0 || !box_far(Cb, Rb, b, om, term)) {
-              const T sh = term ? -om : om;
-              const T ratio = half / tabs(c - sh);
-              if (ratio <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, sh, ratio);
-              else near_t[term] = true;
-            }
-          }
-          if (re != T(0)) kadd_t(sR[wib][iw], cR[wib][iw], vr * re);
-        }
-#pragma unroll
-        for (int term = 0; term < 2; ++term) {
-          const unsigned bn = __ballot_sync(kFull, near_t[term]);
-          if (near_t[term]) s_nl2[wib][nnear + __popc(bn & lt)] = (sl << 10) | (iw * 2 + term);
-          nnear += __popc(bn);
-        }
-        __syncwarp();
-        if (nnear > kListCap - 64) near_drain();
+      for (int i = 0; i < 4; ++i) {
+        ee[i] = s_qe[wib][sl][i];
+        ff[i] = s_qf[wib][sl][i];
       }
+      eval_piece(ee, ff, s_qv[wib][sl][0], s_qv[wib][sl][1], s_qv[wib][sl][2], scr + p * SKM, s_pk[wib][p],
+                 s_qb[wib][sl], sl);
     }
-    near_drain();
-    fallback_drain();  // the ring slots of this drain are still valid
+    fallback_drain();  // the ring slots of this round are still valid
     qh += n;
     __syncwarp();
   };
@@ -506,7 +539,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         T e[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) e[i] = (base + ee[i]) * ri;
-        box_moments(e, ff, vr, scr + lane * SKF, b < kBoxFine ? KF : KG);
+        box_moments_ol(e, ff, vr, scr + lane * SKF, b < kBoxFine ? KF : KG);
         ++nboxed;
       }
     }
@@ -525,12 +558,12 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       const int sl = (qt + __popc(qm & lt)) % QC;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        s_qe[wib][i][sl] = ee[i];
-        s_qf[wib][i][sl] = ff[i];
+        s_qe[wib][sl][i] = ee[i];
+        s_qf[wib][sl][i] = ff[i];
       }
-      s_qv[wib][0][sl] = vr;
-      s_qv[wib][1][sl] = D0h;
-      s_qv[wib][2][sl] = D0l;
+      s_qv[wib][sl][0] = vr;
+      s_qv[wib][sl][1] = D0h;
+      s_qv[wib][sl][2] = D0l;
       s_qb[wib][sl] = b;
     }
     qt += __popc(qm);
