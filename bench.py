@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-tune", action="store_true",
                     help="skip chi0_tune (launch-shape autotuner) before the warm-up steps")
+    ap.add_argument("--tune", action="store_true", help="run chi0_tune on the large run too (skipped by default)")
     ap.add_argument("--overlap", default="auto", choices=["auto", "fp32", "bf16x3", "bf16x6", "tf32"],
                     help="matrix elements of the mixed form: auto = three-piece split-BF16 on the tensor cores "
                          "for the 80-band run, FP32 on the CUDA cores for the small windows of the others")
@@ -382,7 +383,10 @@ def run_ours(args):
     Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev, overlap=ovl)
     nominal = W.nominal_evals()
     tuned = None
-    if not args.no_tune:  # untimed: picks the weight kernel's block shape and grid, and the
+    if args.workload == "large" and not args.tune:
+        tuned = {"skipped": "the autotuner times one whole step per candidate launch shape (about a minute on "
+                            "this run); --tune runs it"}
+    elif not args.no_tune:  # untimed: picks the weight kernel's block shape and grid, and the
         tuned = Pm.tune(W.omega)  # tensor-core corner packing, on one call of the step
     for _ in range(args.warmup):
         run_step(Pm, W)
