@@ -206,7 +206,9 @@ template <typename T> __device__ __noinline__ T far_eval_ol(const T *a, int K, T
 template <typename T> __device__ __noinline__ bool inv_sum_shared_ol(const T x[4], const T f[4], T &out) {
   return inv_sum_shared(x, f, out);
 }
-template <typename T> __device__ __noinline__ T series_sum_ol(const T x[4], const T f[4]) { return series_sum(x, f); }
+template <typename T> __device__ __noinline__ T delta_sum_pre_ol(const T x[4], const T f[4], const T *rs) {
+  return delta_sum_pre(x, f, rs);
+}
 template <typename T> __device__ __noinline__ T delta_sum_ol(const T d[4], const T f[4]) { return delta_sum(d, f, T(0)); }
 
 // does box b stand in for term (0: 1/(D - u), 1: 1/(D + u)) at frequency u = om?  Fine boxes
@@ -266,14 +268,14 @@ __device__ __forceinline__ void near_knots(int ent, const T d[4], const T e[4], 
 // are added one term at a time; the delta term where |w| lies inside the knot range
 template <typename T>
 __device__ __forceinline__ void near_add(int ent, T re, const T x[4], const T f[4], T vr, bool neg, T *sR, T *cR,
-                                         T *sI, T *cI) {
+                                         T *sI, T *cI, const T *rs) {
   const int iw = ent >> 1, sgn = ent & 1;
   for (int t2 = 0; t2 < 2; ++t2) {
     if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
     __syncwarp(__activemask());
   }
   if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {
-    const T im = delta_sum_ol(x, f) * T(3.141592653589793);
+    const T im = delta_sum_pre_ol(x, f, rs) * T(3.141592653589793);
     kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
   }
 }
@@ -286,7 +288,7 @@ __device__ __forceinline__ void near_add(int ent, T re, const T x[4], const T f[
 template <bool FP64, typename T>
 __device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D0l, const T f[4], T vr,
                                           const T *s_w, const T *s_wl, const short *list, int n, int slot,
-                                          int *fb, int &nfb, T *sR, T *cR, T *sI, T *cI) {
+                                          int *fb, int &nfb, T *sR, T *cR, T *sI, T *cI, const T *rs) {
   const int lane = threadIdx.x & 31;
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
@@ -297,14 +299,11 @@ __device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D
       T x[4];
       bool neg;
       near_knots<FP64>(ent, d, e, D0h, D0l, s_w, s_wl, x, neg);
+      // (a near entry has the frequency within two half-widths of the piece's midpoint, where
+      // the moment series about the knot midpoint does not apply)
       T re;
-      if (series_ok(x, T(Num<T>::kappa))) {
-        near_add(ent, series_sum_ol(x, f), x, f, vr, neg, sR, cR, sI, cI);
-      } else if (inv_sum_shared_ol(x, f, re)) {
-        near_add(ent, re, x, f, vr, neg, sR, cR, sI, cI);
-      } else {
-        left = true;
-      }
+      if (inv_sum_shared_ol(x, f, re)) near_add(ent, re, x, f, vr, neg, sR, cR, sI, cI, rs);
+      else left = true;
     }
     const unsigned bal = __ballot_sync(kFull, left);
     if (left) fb[nfb + __popc(bal & ((1u << lane) - 1u))] = (slot << 10) | ent;
@@ -447,6 +446,9 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
     const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
     const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
+    // reciprocal knot spans 01, 12, 23, 02, 13, 03 (the same for every frequency; the delta term)
+    const T rs[6] = {rcp(ee[1] - ee[0]), rcp(ee[2] - ee[1]), rcp(ee[3] - ee[2]),
+                     rcp(ee[2] - ee[0]), rcp(ee[3] - ee[1]), rcp(ee[3] - ee[0])};
     // far field for both terms (Horner on the moments); near-field frequencies are
     // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
     unsigned nearm = 0u, nearp = 0u;
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       if (nlist > kNearCap - 64) {  // flush a full list
         __syncwarp();
         near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib],
-                        cR[wib], sI[wib], cI[wib]);
+                        cR[wib], sI[wib], cI[wib], rs);
         if (nfb > kFbCap - kNearCap) fallback_drain();
         nlist = 0;
         __syncwarp();
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
     __syncwarp();
     near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib], cR[wib],
-                    sI[wib], cI[wib]);
+                    sI[wib], cI[wib], rs);
     if (nfb > kFbCap - kNearCap) fallback_drain();
     __syncwarp();
   };

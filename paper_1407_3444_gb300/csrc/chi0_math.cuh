@@ -548,6 +548,45 @@ template <typename T> __device__ __forceinline__ T delta_sum(const T d[4], const
   return T(0.25) * acc;
 }
 
+// delta_sum at w = 0 for knots x already shifted by the frequency, with the reciprocals rs of the
+// knot spans 01, 12, 23, 02, 13, 03 given (they do not depend on the shift): the same de Boor-Cox
+// recursion per vertex, multiplying by the reciprocal spans instead of dividing.  (The B-spline
+// recursion combines nonnegative terms, so spans from the unshifted knots cost no accuracy; the
+// divided-difference table of the principal value keeps the differences of its own rounded knots.)
+template <typename T> __device__ __forceinline__ T delta_sum_pre(const T x[4], const T f[4], const T rs[6]) {
+  if (!(x[0] < T(0) && x[3] > T(0))) return T(0);
+  // reciprocal span of original knots a <= b (0 for a == b)
+  auto R = [&](int a, int b) -> T {
+    if (a == b) return T(0);
+    const int k = b - a;
+    return k == 1 ? rs[a] : (k == 2 ? rs[3 + a] : rs[5]);
+  };
+  T acc = T(0);
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    int id[5];
+    T t[5];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      id[l] = l <= jj ? l : l - 1;
+      t[l] = x[id[l]];
+    }
+    T M[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) M[i] = (t[i] <= T(0) && T(0) < t[i + 1]) ? R(id[i], id[i + 1]) : T(0);
+#pragma unroll
+    for (int k = 2; k <= 4; ++k) {
+#pragma unroll
+      for (int i = 0; i + k <= 4; ++i) {
+        const T den = t[i + k] - t[i];
+        M[i] = den > T(0) ? (T(k) / T(k - 1)) * ((-t[i]) * M[i] + t[i + k] * M[i + 1]) * R(id[i], id[i + k]) : T(0);
+      }
+    }
+    acc += f[jj] * M[0];
+  }
+  return T(0.25) * acc;
+}
+
 // Tetrahedron density of states at eF for one band: M(0; a_0..a_3), quadratic B-spline
 template <typename T> __device__ __forceinline__ T dos4(T a0, T a1, T a2, T a3) {
   T t[4] = {a0, a1, a2, a3};
