@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--cpu-sample-w", type=int, default=16, help="dynamic workloads: frequencies of the oracle sample")
     ap.add_argument("--cpu-tets", type=int, default=None,
                     help="large: tetrahedra of the oracle sample (default 192; 48 per --impl reference step)")
+    ap.add_argument("--tets", type=int, default=0,
+                    help="large: the step on a seeded sample of TETS of the mesh's tetrahedra (the full mesh's mix "
+                         "of final tetrahedra at a fraction of its size, for profiler counters); nominal evals "
+                         "scale by TETS / ntet")
     ap.add_argument("--profile-out", default="")
     return ap.parse_args()
 
@@ -380,8 +384,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     peaks_run = arithmetic_peaks(chi0)
     dev = chi0.DeviceInputs(W)
-    Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev, overlap=ovl)
-    nominal = W.nominal_evals()
+    sub = tet_sample(W, args.tets, wl.SEED_BASE + 78) if args.tets else None
+    Pm = chi0.Plan(W, precision="mixed", device=True, profile=True, staged=dev, overlap=ovl, tetra=sub)
+    nominal = W.nominal_evals() * (len(sub[1]) / W.ntet if sub is not None else 1.0)
     tuned = None
     if args.workload == "large" and not args.tune:
         tuned = {"skipped": "the autotuner times one whole step per candidate launch shape (about a minute on "
@@ -433,7 +438,7 @@ def run_ours(args):
     dyn64_ms = None
     pieces64 = None
     if args.fp64_steps > 0:
-        Pd = chi0.Plan(W, precision="fp64", device=True, profile=True, staged=dev)
+        Pd = chi0.Plan(W, precision="fp64", device=True, profile=True, staged=dev, tetra=sub)
         torch.cuda.synchronize()
         d0 = Pd.stats()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -474,7 +479,7 @@ def run_ours(args):
         for s in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Ph = chi0.Plan(W, precision="mixed", device=False, staged=host, overlap=ovl)
+            Ph = chi0.Plan(W, precision="mixed", device=False, staged=host, overlap=ovl, tetra=sub)
             out_h = run_step(Ph, W)
             Ph.close()
             t1 = time.perf_counter()
@@ -499,8 +504,9 @@ def run_ours(args):
     else:
         k_ms = stage_ms(s0, s1, chi0.CHI0_K_DYNAMIC)
         launches_w = s1.launches[chi0.CHI0_K_DYNAMIC] - s0.launches[chi0.CHI0_K_DYNAMIC]
-        fpu, tpu, kname = (FLOPS_PER_PIECE_DYN32 if args.workload == "large" else None,
-                           TRAFFIC_PER_PIECE_DYN32 if args.workload == "large" else None,
+        at72 = args.workload == "large" and (args.n or 72) == 72
+        fpu, tpu, kname = (FLOPS_PER_PIECE_DYN32 if at72 else None,
+                           TRAFFIC_PER_PIECE_DYN32 if at72 else None,
                            "dynamic weights (k_dynamic + box sums/evaluation, mixed)")
         uname = "final tetrahedron over a pass of <= 256 w"
     units = pieces_timed / max(1, launches_w)
@@ -513,7 +519,8 @@ def run_ours(args):
             "peak_source": "measured FP32 FMA peak of this GPU (chi0_peak, this run)"}
     roof64 = None
     if dyn64_ms and pieces64:
-        f64 = FLOPS_PER_PIECE_DYN64 if (W.omega is not None and args.workload == "large") else None
+        f64 = FLOPS_PER_PIECE_DYN64 if (W.omega is not None and args.workload == "large"
+                                        and (args.n or 72) == 72) else None
         a64 = f64 * pieces64 / (dyn64_ms * 1e-3) / 1e12 if f64 else None
         roof64 = {"bound": "alu", "achieved": a64, "peak": fp64_pk, "unit": "TFLOP/s (FP64)",
                   "frac": a64 / fp64_pk if (a64 is not None and fp64_pk) else None,
@@ -566,7 +573,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-                "config": workload_config(W, args),
+                "config": dict(workload_config(W, args), **({"tetra_sample": len(sub[1])} if sub is not None else {})),
                 "fp64_gpu": ({"value": nominal / (ms64 * 1e-3), "unit": "evals/s", "ms_per_step": ms64,
                               "mixed_speedup": ms64 / ms} if ms64 else None),
                 "error": {"mixed_vs_fp64_gpu_max_rel": err_mixed, "vs_oracle": err_oracle},

@@ -51,6 +51,7 @@ struct chi0_plan {
   double *box_part_d = nullptr;               // per-warp box moments, their totals and the
   double *box_tot_d = nullptr;                // boxes' share of Re per frequency
   double *far_d = nullptr;
+  void *fb_d = nullptr;                       // dynamic weights: per-warp fallback entries
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
   int static_grid = 0, dynamic_grid = 0;  // persistent CTAs of the weight kernels
@@ -148,6 +149,7 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->box_part_d);
   cudaFree(p->box_tot_d);
   cudaFree(p->far_d);
+  cudaFree(p->fb_d);
 }
 
 extern "C" void chi0_destroy(chi0_plan_t *p) {
@@ -300,6 +302,7 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     CK(p, cudaMalloc(&p->box_part_d, sizeof(double) * warps * dynamic_box_slots(fp64)));
     CK(p, cudaMalloc(&p->box_tot_d, sizeof(double) * dynamic_box_slots(fp64)));
     CK(p, cudaMalloc(&p->far_d, sizeof(double) * dynamic_max_nw()));
+    CK(p, cudaMalloc(&p->fb_d, warps * dynamic_fb_bytes(fp64)));
   }
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, p->stream));
   CK(p, cudaStreamSynchronize(p->stream));
@@ -486,7 +489,7 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
       const int maxw = dynamic_max_nw();
       for (int w0 = 0; w0 < nw; w0 += maxw) {
         const int nwc = nw - w0 < maxw ? nw - w0 : maxw;
-        DynBufs db{p->partR, p->partI, p->box_tab_d, p->box_part_d, p->box_tot_d, p->far_d};
+        DynBufs db{p->partR, p->partI, p->box_tab_d, p->box_part_d, p->box_tot_d, p->far_d, p->fb_d};
         tm.start(CHI0_K_DYNAMIC);
         CK(p, launch_dynamic(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
                              om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s, Eklo, Ekqlo));

@@ -64,6 +64,15 @@ using grid::tet_corners;
 
 constexpr int kNWPass = 256;   // frequencies per dynamic pass
 constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed per warp
+constexpr int kFbCap = 1024;   // near-field entries left to the per-vertex table, per warp
+static_assert(kFbCap >= 4 * kNWPass, "the fallback buffer keeps room for two pieces' entries");
+
+// a near-field entry the shared table leaves: knots x (sorted), values f, weight v, and
+// code = frequency index << 2 | term << 1 | (w < 0)
+template <typename T> struct FbEnt {
+  T x[4], f[4], v;
+  int code;
+};
 
 template <bool FP64> struct DynShape {
   static constexpr int threads = FP64 ? 64 : 128;
@@ -72,7 +81,6 @@ template <bool FP64> struct DynShape {
   static constexpr int KM = FP64 ? 64 : 32;  // own far-field moments kept per queued piece
   static constexpr int NF = FP64 ? 3 : 2;    // a fine box stands in beyond NF radii
   static constexpr int KF = FP64 ? 28 : 24;  // moments of a fine box   (truncation NF^-KF)
-  static constexpr int FB = FP64 ? 576 : 640;  // near-field entries left to the per-vertex table
   static constexpr int KG = FP64 ? 22 : 12;  // moments of a geometric box ((2/9)^KG)
 };
 
@@ -156,7 +164,7 @@ template <typename T> __device__ __forceinline__ int box_of(T c, T s, const BoxT
   if (!tb.on) return -1;
   const T x = c - tb.umax;
   if (x >= tb.x0) {
-    int b = (int)(__log2f((float)(x / tb.x0)) * 3.1062837f);  // log base 1.25
+    int b = (int)(__log2f((float)quot(x, tb.x0)) * 3.1062837f);  // log base 1.25 (a first guess)
     b = b < 0 ? 0 : (b > kBoxG - 1 ? kBoxG - 1 : b);
     while (b > 0 && x < tb.lowG[b]) --b;
     while (b < kBoxG - 1 && x >= tb.lowG[b + 1]) ++b;
@@ -167,7 +175,7 @@ template <typename T> __device__ __forceinline__ int box_of(T c, T s, const BoxT
 #pragma unroll 1
   for (int l = 0; l < kBoxL; ++l) {
     if (s <= T(0.5) * w) {
-      const T jf = floor(c / w);
+      const T jf = floor(quot(c, w));
       return jf < (T)box_J(l) ? off + (int)jf : -1;
     }
     off += box_J(l);
@@ -282,22 +290,22 @@ __device__ __forceinline__ void near_add(int ent, T re, const T x[4], const T f[
 
 // evaluates one piece's near-field list, one entry per lane and round, by the shared
 // divided-difference table (all branches alike).  Entries it leaves (three clustered knots,
-// three zero knots) are appended to the drain's fallback list as (queue slot << 10 | entry),
-// evaluated later for all pieces of the drain together.  Entries of one round are distinct, so
-// each round adds to distinct slots.
+// three zero knots) are appended, knots and all, to the warp's fallback buffer in global memory
+// (the caller keeps room for n entries).  Entries of one round are distinct, so each round adds
+// to distinct slots.
 template <bool FP64, typename T>
 __device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D0l, const T f[4], T vr,
-                                          const T *s_w, const T *s_wl, const short *list, int n, int slot,
-                                          int *fb, int &nfb, T *sR, T *cR, T *sI, T *cI, const T *rs) {
+                                          const T *s_w, const T *s_wl, const short *list, int n,
+                                          FbEnt<T> *fb, int &nfb, T *sR, T *cR, T *sI, T *cI, const T *rs) {
   const int lane = threadIdx.x & 31;
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
     bool left = false;
     int ent = 0;
+    T x[4];
+    bool neg = false;
     if (k < n) {
       ent = list[k];
-      T x[4];
-      bool neg;
       near_knots<FP64>(ent, d, e, D0h, D0l, s_w, s_wl, x, neg);
       // (a near entry has the frequency within two half-widths of the piece's midpoint, where
       // the moment series about the knot midpoint does not apply)
@@ -306,9 +314,20 @@ __device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D
       else left = true;
     }
     const unsigned bal = __ballot_sync(kFull, left);
-    if (left) fb[nfb + __popc(bal & ((1u << lane) - 1u))] = (slot << 10) | ent;
-    nfb += __popc(bal);
-    __syncwarp();
+    if (bal) {  // warp-uniform
+      if (left) {
+        FbEnt<T> &o = fb[nfb + __popc(bal & ((1u << lane) - 1u))];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          o.x[i] = x[i];
+          o.f[i] = f[i];
+        }
+        o.v = vr;
+        o.code = ((ent >> 1) << 2) | ((ent & 1) << 1) | (neg ? 1 : 0);
+      }
+      nfb += __popc(bal);
+      __syncwarp();
+    }
   }
 }
 
@@ -321,8 +340,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
               unsigned long long *__restrict__ counters) {
   using T = typename std::conditional<FP64, double, float>::type;
   using S = DynShape<FP64>;
-  constexpr int W = S::warps, KM = S::KM, KF = S::KF, KG = S::KG, DC = S::DC, kFbCap = S::FB;
-  static_assert(kFbCap >= kNearCap + 32, "one piece's near list must fit the fallback list");
+  constexpr int W = S::warps, KM = S::KM, KF = S::KF, KG = S::KG, DC = S::DC;
   constexpr int QC = 64;  // queue of final tetrahedra that evaluate frequencies themselves
   constexpr int NS = box_slots<FP64>();
   constexpr int SKM = KM + 1, SKF = KF + 1;  // per-lane strides of the scratch (odd: no bank conflicts)
@@ -344,7 +362,6 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
   __shared__ short s_near[W][kNearCap];
-  __shared__ int s_fb[W][kFbCap];  // near-field entries the shared table leaves (slot << 10 | entry)
   __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
   extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
@@ -356,6 +373,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   const long long nbatch = (g.ntet + 31) / 32;
   const long long gwarp = (long long)blockIdx.x * W + wib, nwarps = (long long)gridDim.x * W;
   double *gpart = db.box_part + gwarp * NS;
+  FbEnt<T> *gfb = (FbEnt<T> *)db.fb + gwarp * kFbCap;
   for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
     s_w[iw] = (T)omega[iw];
     if constexpr (!FP64) s_wl[iw] = (float)(omega[iw] - (double)s_w[iw]);
@@ -397,49 +415,48 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   // one queued final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr,
   // own far-field moments am[0..K)) on the frequencies its box (b >= 0) leaves to it, or on
   // all of them (b < 0); lanes own frequencies
-  int nfb = 0;  // entries in the drain's fallback list
-  // the fallback list: per-vertex table, one entry per lane and round; results added one lane
-  // at a time in lane order (entries of one round may share a frequency)
-  auto fallback_drain = [&]() {
+  int nfb = 0;  // entries in the warp's fallback buffer
+  // the fallback buffer: per-vertex table, one entry per lane and round (full rounds: the
+  // buffer collects the entries of many pieces).  Lanes that share a frequency add one at a
+  // time in lane order (the buffer's order is fixed, so the sums are reproducible), the others
+  // at once.
+  auto fallback_flush = [&]() {
+    __syncwarp();
     for (int base = 0; base < nfb; base += 32) {
       const int k = base + lane;
       T re = T(0), im = T(0);
-      int iw = 0;
-      bool has_im = false;
+      int iw = -1 - lane;  // inactive lanes: keys of their own
       if (k < nfb) {
-        const int code = s_fb[wib][k], sl = code >> 10, ent = code & 1023;
-        T ee[4], ff[4], d[4], x[4];
-        const T D0h = s_qv[wib][sl][1], D0l = s_qv[wib][sl][2], vr = s_qv[wib][sl][0];
+        const FbEnt<T> &o = gfb[k];
+        T x[4], ff[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          ee[i] = s_qe[wib][sl][i];
-          ff[i] = s_qf[wib][sl][i];
-          d[i] = D0h + ee[i];
+          x[i] = o.x[i];
+          ff[i] = o.f[i];
         }
-        bool neg;
-        near_knots<FP64>(ent, d, ee, D0h, D0l, s_w, s_wl, x, neg);
+        const T vr = o.v;
+        const int code = o.code;
+        iw = code >> 2;
         re = vr * near_term<FP64>(x, ff, tau, nfp64);
-        iw = ent >> 1;
-        if ((ent & 1) == 0 && x[0] < T(0) && x[3] > T(0)) {
-          has_im = true;
+        if ((code & 2) == 0 && x[0] < T(0) && x[3] > T(0)) {
           im = vr * delta_sum_ol(x, ff) * T(3.141592653589793);
-          if (neg) im = -im;
+          if (code & 1) im = -im;
         }
       }
-      unsigned m = __ballot_sync(kFull, k < nfb);
-      while (m) {  // warp-uniform
-        const int src = __ffs(m) - 1;
-        m &= m - 1u;
-        if (lane == src) {
+      const unsigned grp = __match_any_sync(kFull, iw);
+      const int rank = __popc(grp & lt);
+      const int nr = __reduce_max_sync(kFull, iw >= 0 ? rank : 0);
+      for (int r = 0; r <= nr; ++r) {
+        if (iw >= 0 && rank == r) {
           kadd_t(sR[wib][iw], cR[wib][iw], re);
-          if (has_im) kadd_t(sI[wib][iw], cI[wib][iw], im);
+          if (im != T(0)) kadd_t(sI[wib][iw], cI[wib][iw], im);
         }
         __syncwarp();
       }
     }
     nfb = 0;
   };
-  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b, int slot) {
+  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b) {
     T d[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
@@ -456,19 +473,20 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
       T re = T(0);
       if (b < 0 || !box_far(Cb, Rb, b, om, 1)) {
-        const T rp = half / (c + om);
+        const T rp = quot(half, c + om);
         if (rp <= T(Num<T>::kappa_far)) re += far_eval_ol(am, K, c, -om, rp);
         else nearp |= 1u << itn;
       }
       if (b < 0 || !box_far(Cb, Rb, b, om, 0)) {
         const T dm = c - om;
-        const T rm = half / (dm < T(0) ? -dm : dm);
+        const T rm = quot(half, dm < T(0) ? -dm : dm);
         if (rm <= T(Num<T>::kappa_far)) re += far_eval_ol(am, K, c, om, rm);
         else nearm |= 1u << itn;
       }
       if (re != T(0)) kadd_t(sR[wib][iw], cR[wib][iw], vr * re);
     }
-    // near field: compact the (frequency, term) pairs of the warp into a list
+    // near field: compact the (frequency, term) pairs of the warp into a list, evaluated in
+    // full warps whenever it might overflow and after the last frequencies (one call site)
     int nlist = 0;
     const int nit = (hi - lo + 31) >> 5;
     for (int itn = 0; itn < nit; ++itn) {
@@ -479,20 +497,14 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         if (mine) s_near[wib][nlist + __popc(bal & lt)] = (short)((lo + itn * 32 + lane) * 2 + sgn);
         nlist += __popc(bal);
       }
-      if (nlist > kNearCap - 64) {  // flush a full list
+      if (nlist > kNearCap - 64 || (itn == nit - 1 && nlist > 0)) {
         __syncwarp();
-        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib],
-                        cR[wib], sI[wib], cI[wib], rs);
-        if (nfb > kFbCap - kNearCap) fallback_drain();
+        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, gfb, nfb, sR[wib], cR[wib],
+                        sI[wib], cI[wib], rs);
         nlist = 0;
         __syncwarp();
       }
     }
-    __syncwarp();
-    near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, slot, s_fb[wib], nfb, sR[wib], cR[wib],
-                    sI[wib], cI[wib], rs);
-    if (nfb > kFbCap - kNearCap) fallback_drain();
-    __syncwarp();
   };
   // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then each piece
   // on its frequencies with the whole warp
@@ -509,6 +521,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
     __syncwarp();
     for (int p = 0; p < n; ++p) {
+      if (nfb > kFbCap - 2 * kNWPass) fallback_flush();  // room for the piece's entries (warp-uniform)
       const int sl = (qh + p) % QC;
       T ee[4], ff[4];
 #pragma unroll
@@ -517,12 +530,12 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         ff[i] = s_qf[wib][sl][i];
       }
       eval_piece(ee, ff, s_qv[wib][sl][0], s_qv[wib][sl][1], s_qv[wib][sl][2], scr + p * SKM, s_pk[wib][p],
-                 s_qb[wib][sl], sl);
+                 s_qb[wib][sl]);
     }
-    fallback_drain();  // the ring slots of this round are still valid
     qh += n;
     __syncwarp();
   };
+  int dthr = DC;  // queued pieces that trigger a drain (1: drain them all; warp-uniform)
   // one carving step: at most one final tetrahedron per lane (has).  Its box and moments, the
   // box sums (one moment index per lane, pieces in lane order), and the queue for pieces that
   // evaluate frequencies themselves.
@@ -537,7 +550,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
       b = boxes ? box_of(c, half, s_tab) : -1;
       if (b >= 0) {
-        const T ri = T(1) / s_tab.R[b], base = (D0h - s_tab.C[b]) + D0l;
+        const T ri = rcp(s_tab.R[b]), base = (D0h - s_tab.C[b]) + D0l;
         T e[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) e[i] = (base + ee[i]) * ri;
@@ -570,7 +583,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
     qt += __popc(qm);
     __syncwarp();
-    while (qt - qh >= DC) drain(DC);
+    while (qt - qh >= dthr) drain(qt - qh < DC ? qt - qh : DC);
   };
   // item data of (tetrahedron l of the batch, bands m, n): a = e^m_k - eF, D = D0 + e (e_0 = 0)
   // and |M|^2 at the corners.  Mixed path: energies as FP32 hi + lo pairs, so that D0 (hi + lo)
@@ -616,7 +629,8 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   };
   // up to 32 items, one per lane: both carvings of Sec. II as warp-uniform loops over the
   // pieces of the first and second cut, one final tetrahedron per lane and step
-  auto carve_items = [&](bool has, int l, int m, int n) {
+  // (force: at least one step, so that piece() runs and drains the queue)
+  auto carve_items = [&](bool has, int l, int m, int n, bool force) {
     T a[4] = {T(0), T(0), T(0), T(0)}, e[4] = {T(0), T(0), T(0), T(0)}, f[4] = {T(0), T(0), T(0), T(0)};
     T D0h = T(0), D0l = T(0);
     if (has) load_item(l, m, n, a, e, f, D0h, D0l);
@@ -627,11 +641,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       const T bmin = fmin(fmin(a[0] + D0h + e[0], a[1] + D0h + e[1]), fmin(a[2] + D0h + e[2], a[3] + D0h + e[3]));
       whole = amax < T(0) && bmin > T(0);  // occupied at k and empty at k+q everywhere: no cut
     }
-    if (!__any_sync(kFull, has && !whole)) {
-      piece(whole, e, f, vol, D0h, D0l);
-      return;
-    }
-    // general case (whole items emit their one piece at the first step)
+    // whole items emit their one piece at the first step
     Vt<T> V[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) V[i] = Vt<T>{a[i], e[i], f[i]};
@@ -639,7 +649,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     Vt<T> P0[4];
     T r0 = T(0);
     const int n1 = cut ? cut_piece<0>(V, 0, P0, r0) : 0;
-    const int n1max = __reduce_max_sync(kFull, whole ? 1 : n1);
+    const int n1max = max(__reduce_max_sync(kFull, whole ? 1 : n1), force ? 1 : 0);
 #pragma unroll 1
     for (int i1 = 0; i1 < n1max; ++i1) {
       Vt<T> P[4];
@@ -657,7 +667,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         T rd;
         n2 = cut_piece<1>(P, 0, Qd, rd);
       }
-      const int n2max = __reduce_max_sync(kFull, (whole && i1 == 0) ? 1 : n2);
+      const int n2max = max(__reduce_max_sync(kFull, (whole && i1 == 0) ? 1 : n2), (force && i1 == 0) ? 1 : 0);
 #pragma unroll 1
       for (int i2 = 0; i2 < n2max; ++i2) {
         T ee[4], ff[4], vr = T(0);
@@ -742,17 +752,22 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         else if (nc >= 32) which = 1;
         else if (final && nf > 0) which = 0;
         else if (final && nc > 0) which = 1;
+        else if (final && qt > qh) which = 2;  // the batch's last queued pieces
         else break;
-        const int cntl = which ? nc : nf;
-        const int take = cntl < 32 ? cntl : 32;
-        int code = 0;
-        if (lane < take) code = s_list[wib][which][cntl - take + lane];
-        __syncwarp();
-        if (lane == 0) s_nl[wib][which] = cntl - take;
-        __syncwarp();
+        int take = 0, code = 0;
+        if (which < 2) {
+          const int cntl = which ? nc : nf;
+          take = cntl < 32 ? cntl : 32;
+          if (lane < take) code = s_list[wib][which][cntl - take + lane];
+          __syncwarp();
+          if (lane == 0) s_nl[wib][which] = cntl - take;
+          __syncwarp();
+        }
+        dthr = which == 2 ? 1 : DC;
         const unsigned u = (unsigned)code;
-        carve_items(lane < take, (int)(u >> 24), (int)((u >> 12) & 0xFFFu), (int)(u & 0xFFFu));
+        carve_items(lane < take, (int)(u >> 24), (int)((u >> 12) & 0xFFFu), (int)(u & 0xFFFu), which == 2);
       }
+      dthr = DC;
     };
     for (int base = 0;; base += 32) {  // warp-uniform; the pass after the last items drains
       const bool last = base >= total;
@@ -805,8 +820,8 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       drain_items(last);
       if (last) break;
     }
-    while (qt > qh) drain(qt - qh < DC ? qt - qh : DC);  // the batch's last queued pieces
-    qh = qt = 0;
+    qh = qt = 0;  // (the last pass of drain_items emptied the queue)
+    if (nfb > 0) fallback_flush();  // warp-uniform
     __syncwarp();
     for (int iw = lane; iw < nw; iw += 32) {
       db.partR[batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
@@ -904,6 +919,9 @@ template <bool FP64> size_t dyn_smem() {
 int dynamic_max_nw() { return kNWPass; }
 int dynamic_warps_per_cta(int fp64) { return fp64 ? DynShape<true>::warps : DynShape<false>::warps; }
 size_t dynamic_box_slots(int fp64) { return fp64 ? box_slots<true>() : box_slots<false>(); }
+size_t dynamic_fb_bytes(int fp64) {
+  return (size_t)kFbCap * (fp64 ? sizeof(FbEnt<double>) : sizeof(FbEnt<float>));
+}
 size_t dynamic_box_tab_bytes() {
   return sizeof(BoxTab<double>) > sizeof(BoxTab<float>) ? sizeof(BoxTab<double>) : sizeof(BoxTab<float>);
 }
@@ -923,7 +941,7 @@ cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const 
                            const float *Ekqlo) {
   if (nw > kNWPass || nw <= 0 || nblocks <= 0) return cudaErrorInvalidValue;
   if (!fp64 && (!Eklo || !Ekqlo)) return cudaErrorInvalidValue;
-  if (!db.box_tab || !db.box_part || !db.box_tot || !db.far) return cudaErrorInvalidValue;
+  if (!db.box_tab || !db.box_part || !db.box_tot || !db.far || !db.fb) return cudaErrorInvalidValue;
   if (fp64) {
     const int nwarps = nblocks * DynShape<true>::warps;
     k_box_setup<double><<<1, 256, 0, s>>>(omega, nw, (BoxTab<double> *)db.box_tab);

@@ -100,6 +100,8 @@ struct DynBufs {
   double *box_part;       // [warps of the launch][dynamic_box_slots(fp64)]
   double *box_tot;        // [dynamic_box_slots(fp64)]
   double *far;            // [nw]: Re contribution of the box multipoles per frequency
+  void *fb;               // [warps of the launch][dynamic_fb_bytes(fp64)]: near-field entries
+                          // left to the per-vertex table (scratch)
 };
 
 // dynamic weights for one q and nw <= dynamic_max_nw() frequencies: partR/partI per batch and
@@ -113,6 +115,7 @@ int dynamic_persistent_blocks(int fp64);
 int dynamic_warps_per_cta(int fp64);
 size_t dynamic_box_slots(int fp64);
 size_t dynamic_box_tab_bytes();
+size_t dynamic_fb_bytes(int fp64);
 cudaError_t dynamic_prepare();  // kernel attributes (shared memory); call outside stream capture
 
 // Gamma: intraband q -> 0 limit, tetrahedron DOS at eF: partial[nblocks]

@@ -52,12 +52,23 @@ template <> struct Num<float> {
 
 template <typename T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
-// Reciprocal and quotient of the weight kernels.  FP64: IEEE division.  FP32: the correctly
-// rounded reciprocal intrinsic (same result as 1/x, shorter sequence) and the fast quotient
-// (at most 2 ulp from a / b for the cut fractions, |b| < 2^126), far below the FP32 path's
-// 1e-6 target.
+// Reciprocal and quotient of the weight kernels.  FP64: IEEE division.  FP32: the hardware
+// reciprocal approximation refined by one Newton-Raphson step, r' = r + r (1 - x r), within
+// about 1 ulp of 1/x for normal x (0 and denormals are never divided by: ties and zero knots
+// take their own branches), and the fast quotient (at most 2 ulp from a / b for the cut
+// fractions, |b| < 2^126); both far below the FP32 path's 1e-6 target.  The correctly rounded
+// intrinsics carry slow paths for special operands that made the weight kernels' hot code
+// several times larger (instruction-cache misses).
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp(float x) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+#else
+  return __frcp_rn(x);
+#endif
+}
 __device__ __forceinline__ double quot(double a, double b) { return a / b; }
 __device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
 
@@ -325,7 +336,7 @@ template <typename T> __device__ __forceinline__ bool inv_sum_shared(const T x[4
     return true;
   }
   const T rho = T(kRhoShared);
-  const T si = T(1) / s;
+  const T si = rcp(s);
   T u[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) u[i] = x[i] * si;
@@ -364,11 +375,12 @@ template <typename T> __device__ __forceinline__ bool inv_sum_shared(const T x[4
       HL[p] = (G1[p] - gp[p]) * r;
       HR[p] = (gp[p + 1] - G1[p]) * r;
     } else {
-      const T a = u[p], y = d / a, Lp = L[p];
+      const T a = u[p], y = d * rcp(a), Lp = L[p];
       const T g2 = T(6) * a * Lp + T(5) * a, g3 = T(6) * Lp + T(11);
       // T_4 = a y^2 / 4; successive terms: T_{k+1} = -T_k (k-3) y / (k+1)
       T t = T(0.25) * a * y * y;
       T s0 = T(0), s1 = T(0);
+#pragma unroll 1
       for (int k = 4; k < 4 + Num<T>::kmax; ++k) {
         s0 += t;
         s1 += T(k - 1) * t;
@@ -503,8 +515,8 @@ template <typename T, int KMAX> __device__ int far_moments(const T d[4], const T
 
 // (1/(c - w)) sum_{k<K} a_k z^k with z = c/(c - w), truncated where rho^k < tol
 template <typename T> __device__ __forceinline__ T far_eval(const T *a, int K, T c, T w, T rho) {
-  const T den = c - w;
-  const T z = c / den;
+  const T den = c - w, rd = rcp(den);
+  const T z = c * rd;
   int kk = K;
   if (rho > T(0)) {
     const float need = __log2f((float)Num<T>::tol) / __log2f((float)rho);  // rho^need = tol
@@ -512,7 +524,7 @@ template <typename T> __device__ __forceinline__ T far_eval(const T *a, int K, T
   }
   T sum = T(0);
   for (int k = kk - 1; k >= 0; --k) sum = sum * z + a[k];
-  return sum / den;
+  return sum * rd;
 }
 
 // Normalised cubic B-spline density M(w; t0..t4) (integral 1) by the de Boor-Cox
