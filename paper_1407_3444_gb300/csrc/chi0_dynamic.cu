@@ -63,9 +63,10 @@ using grid::kFull;
 using grid::tet_corners;
 
 constexpr int kNWPass = 256;   // frequencies per dynamic pass
-constexpr int kNearCap = 512;  // near-field (frequency, term) entries listed per warp
-constexpr int kFbCap = 1024;   // near-field entries left to the per-vertex table, per warp
-static_assert(kFbCap >= 4 * kNWPass, "the fallback buffer keeps room for two pieces' entries");
+constexpr int kNearCap = 1024;  // near-field (piece, frequency, term) entries listed per warp
+constexpr int kFbCap = 4096;   // near-field entries left to the per-vertex table, per warp
+static_assert(kFbCap >= 4 * kNearCap, "the fallback buffer holds several near lists' leftovers");
+static_assert(kNearCap >= 4 * kNWPass, "the near list keeps room for two pieces' entries");
 
 // a near-field entry the shared table leaves: knots x (sorted), values f, weight v, and
 // code = frequency index << 2 | term << 1 | (w < 0)
@@ -272,65 +273,6 @@ __device__ __forceinline__ void near_knots(int ent, const T d[4], const T e[4], 
   }
 }
 
-// adds one near-field result: the two terms of a frequency may both be in one round, so they
-// are added one term at a time; the delta term where |w| lies inside the knot range
-template <typename T>
-__device__ __forceinline__ void near_add(int ent, T re, const T x[4], const T f[4], T vr, bool neg, T *sR, T *cR,
-                                         T *sI, T *cI, const T *rs) {
-  const int iw = ent >> 1, sgn = ent & 1;
-  for (int t2 = 0; t2 < 2; ++t2) {
-    if (t2 == sgn) kadd_t(sR[iw], cR[iw], vr * re);
-    __syncwarp(__activemask());
-  }
-  if (sgn == 0 && x[0] < T(0) && x[3] > T(0)) {
-    const T im = delta_sum_pre_ol(x, f, rs) * T(3.141592653589793);
-    kadd_t(sI[iw], cI[iw], neg ? -vr * im : vr * im);
-  }
-}
-
-// evaluates one piece's near-field list, one entry per lane and round, by the shared
-// divided-difference table (all branches alike).  Entries it leaves (three clustered knots,
-// three zero knots) are appended, knots and all, to the warp's fallback buffer in global memory
-// (the caller keeps room for n entries).  Entries of one round are distinct, so each round adds
-// to distinct slots.
-template <bool FP64, typename T>
-__device__ __forceinline__ void near_pass(const T d[4], const T e[4], T D0h, T D0l, const T f[4], T vr,
-                                          const T *s_w, const T *s_wl, const short *list, int n,
-                                          FbEnt<T> *fb, int &nfb, T *sR, T *cR, T *sI, T *cI, const T *rs) {
-  const int lane = threadIdx.x & 31;
-  for (int base = 0; base < n; base += 32) {
-    const int k = base + lane;
-    bool left = false;
-    int ent = 0;
-    T x[4];
-    bool neg = false;
-    if (k < n) {
-      ent = list[k];
-      near_knots<FP64>(ent, d, e, D0h, D0l, s_w, s_wl, x, neg);
-      // (a near entry has the frequency within two half-widths of the piece's midpoint, where
-      // the moment series about the knot midpoint does not apply)
-      T re;
-      if (inv_sum_shared_ol(x, f, re)) near_add(ent, re, x, f, vr, neg, sR, cR, sI, cI, rs);
-      else left = true;
-    }
-    const unsigned bal = __ballot_sync(kFull, left);
-    if (bal) {  // warp-uniform
-      if (left) {
-        FbEnt<T> &o = fb[nfb + __popc(bal & ((1u << lane) - 1u))];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          o.x[i] = x[i];
-          o.f[i] = f[i];
-        }
-        o.v = vr;
-        o.code = ((ent >> 1) << 2) | ((ent & 1) << 1) | (neg ? 1 : 0);
-      }
-      nfb += __popc(bal);
-      __syncwarp();
-    }
-  }
-}
-
 template <bool FP64>
 __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     k_dynamic(Grid g, Tet tet, const void *__restrict__ Ek, const void *__restrict__ Ekq, Q q,
@@ -361,7 +303,8 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   __shared__ T cR[W][kNWPass], cI[W][kNWPass];  // compensation terms
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
-  __shared__ short s_near[W][kNearCap];
+  // near-field entries of the drain's pieces: ring slot << 9 | 2 * frequency index + term
+  __shared__ unsigned short s_near[W][kNearCap];
   __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
   extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
@@ -374,6 +317,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   const long long gwarp = (long long)blockIdx.x * W + wib, nwarps = (long long)gridDim.x * W;
   double *gpart = db.box_part + gwarp * NS;
   FbEnt<T> *gfb = (FbEnt<T> *)db.fb + gwarp * kFbCap;
+#pragma unroll 1
   for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
     s_w[iw] = (T)omega[iw];
     if constexpr (!FP64) s_wl[iw] = (float)(omega[iw] - (double)s_w[iw]);
@@ -381,21 +325,26 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   {
     const BoxTab<T> *src = (const BoxTab<T> *)db.box_tab;
     const int nwords = (int)(sizeof(BoxTab<T>) / 4);
+#pragma unroll 1
     for (int i = threadIdx.x; i < nwords; i += blockDim.x) ((int *)&s_tab)[i] = ((const int *)src)[i];
   }
+#pragma unroll 1
   for (int i = lane; i < NS; i += 32) acc[i] = T(0);
   __syncthreads();
   // frequency ranges of the fine boxes: contiguous when |w| ascends along the grid (an
   // interval for the - term, a prefix for the + term); otherwise the whole grid, the
   // predicate deciding each frequency
   bool sorted = true;
+#pragma unroll 1
   for (int i = threadIdx.x; i + 1 < nw; i += blockDim.x) sorted = sorted && tabs(s_w[i]) <= tabs(s_w[i + 1]);
   sorted = __syncthreads_and(sorted) != 0;
+#pragma unroll 1
   for (int b = threadIdx.x; b < kBoxFine; b += blockDim.x) {
     int lo = 0, hi = nw;
     if (sorted) {
       lo = nw;
       hi = 0;
+#pragma unroll 1
       for (int i = 0; i < nw; ++i) {
         const T om = tabs(s_w[i]);
         if (!box_far(s_tab.C[b], s_tab.R[b], b, om, 0) || !box_far(s_tab.C[b], s_tab.R[b], b, om, 1)) {
@@ -422,6 +371,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   // at once.
   auto fallback_flush = [&]() {
     __syncwarp();
+#pragma unroll 1
     for (int base = 0; base < nfb; base += 32) {
       const int k = base + lane;
       T re = T(0), im = T(0);
@@ -446,6 +396,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       const unsigned grp = __match_any_sync(kFull, iw);
       const int rank = __popc(grp & lt);
       const int nr = __reduce_max_sync(kFull, iw >= 0 ? rank : 0);
+#pragma unroll 1
       for (int r = 0; r <= nr; ++r) {
         if (iw >= 0 && rank == r) {
           kadd_t(sR[wib][iw], cR[wib][iw], re);
@@ -456,19 +407,90 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
     nfb = 0;
   };
-  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b) {
+  int nnear = 0;  // entries in the drain's near list
+  // the drain's near list: the shared divided-difference table, one entry per lane and round
+  // (the entries of all queued pieces packed together); lanes that share a frequency add one
+  // at a time in lane order (the list's order is fixed, so the sums are reproducible).  Entries
+  // the table leaves (three clustered knots, three zero knots) go, knots and all, to the
+  // fallback buffer (the caller keeps room for the whole list).
+  auto near_drain = [&]() {
+#pragma unroll 1
+    for (int base = 0; base < nnear; base += 32) {
+      const int k = base + lane;
+      T re = T(0), im = T(0), x[4], ff[4], vr = T(0);
+      int iw = -1 - lane, ent = 0;  // inactive lanes: keys of their own
+      bool left = false, neg = false;
+      if (k < nnear) {
+        const int code = s_near[wib][k], sl = code >> 9;
+        ent = code & 511;
+        T ee[4], d[4];
+        const T D0h = s_qv[wib][sl][1], D0l = s_qv[wib][sl][2];
+        vr = s_qv[wib][sl][0];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ee[i] = s_qe[wib][sl][i];
+          ff[i] = s_qf[wib][sl][i];
+          d[i] = D0h + ee[i];
+        }
+        near_knots<FP64>(ent, d, ee, D0h, D0l, s_w, s_wl, x, neg);
+        // (a near entry has the frequency within two half-widths of the piece's midpoint,
+        // where the moment series about the knot midpoint does not apply)
+        T v;
+        if (inv_sum_shared_ol(x, ff, v)) {
+          iw = ent >> 1;
+          re = vr * v;
+          if ((ent & 1) == 0 && x[0] < T(0) && x[3] > T(0)) {
+            // reciprocal knot spans 01, 12, 23, 02, 13, 03 for the de Boor recursion (from the
+            // unshifted offsets: nonnegative terms, no cancellation)
+            const T rs[6] = {rcp(ee[1] - ee[0]), rcp(ee[2] - ee[1]), rcp(ee[3] - ee[2]),
+                             rcp(ee[2] - ee[0]), rcp(ee[3] - ee[1]), rcp(ee[3] - ee[0])};
+            im = vr * delta_sum_pre_ol(x, ff, rs) * T(3.141592653589793);
+            if (neg) im = -im;
+          }
+        } else {
+          left = true;
+        }
+      }
+      const unsigned grp = __match_any_sync(kFull, iw);
+      const int rank = __popc(grp & lt);
+      const int nr = __reduce_max_sync(kFull, iw >= 0 ? rank : 0);
+#pragma unroll 1
+      for (int r = 0; r <= nr; ++r) {
+        if (iw >= 0 && rank == r) {
+          kadd_t(sR[wib][iw], cR[wib][iw], re);
+          if (im != T(0)) kadd_t(sI[wib][iw], cI[wib][iw], im);
+        }
+        __syncwarp();
+      }
+      const unsigned bal = __ballot_sync(kFull, left);
+      if (bal) {  // warp-uniform
+        if (left) {
+          FbEnt<T> &o = gfb[nfb + __popc(bal & lt)];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            o.x[i] = x[i];
+            o.f[i] = ff[i];
+          }
+          o.v = vr;
+          o.code = ((ent >> 1) << 2) | ((ent & 1) << 1) | (neg ? 1 : 0);
+        }
+        nfb += __popc(bal);
+        __syncwarp();
+      }
+    }
+    nnear = 0;
+  };
+  auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b, int slot) {
     T d[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
     const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
     const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
     const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
-    // reciprocal knot spans 01, 12, 23, 02, 13, 03 (the same for every frequency; the delta term)
-    const T rs[6] = {rcp(ee[1] - ee[0]), rcp(ee[2] - ee[1]), rcp(ee[3] - ee[2]),
-                     rcp(ee[2] - ee[0]), rcp(ee[3] - ee[1]), rcp(ee[3] - ee[0])};
     // far field for both terms (Horner on the moments); near-field frequencies are
     // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
     unsigned nearm = 0u, nearp = 0u;
+#pragma unroll 1
     for (int iw = lo + lane, itn = 0; iw < hi; iw += 32, ++itn) {
       const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
       T re = T(0);
@@ -485,26 +507,20 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       }
       if (re != T(0)) kadd_t(sR[wib][iw], cR[wib][iw], vr * re);
     }
-    // near field: compact the (frequency, term) pairs of the warp into a list, evaluated in
-    // full warps whenever it might overflow and after the last frequencies (one call site)
-    int nlist = 0;
+    // near field: the (frequency, term) pairs go to the drain's near list (the caller keeps
+    // room for them)
     const int nit = (hi - lo + 31) >> 5;
+#pragma unroll 1
     for (int itn = 0; itn < nit; ++itn) {
 #pragma unroll
       for (int sgn = 0; sgn < 2; ++sgn) {
         const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
         const unsigned bal = __ballot_sync(kFull, mine);
-        if (mine) s_near[wib][nlist + __popc(bal & lt)] = (short)((lo + itn * 32 + lane) * 2 + sgn);
-        nlist += __popc(bal);
-      }
-      if (nlist > kNearCap - 64 || (itn == nit - 1 && nlist > 0)) {
-        __syncwarp();
-        near_pass<FP64>(d, ee, D0h, D0l, ff, vr, s_w, s_wl, s_near[wib], nlist, gfb, nfb, sR[wib], cR[wib],
-                        sI[wib], cI[wib], rs);
-        nlist = 0;
-        __syncwarp();
+        if (mine) s_near[wib][nnear + __popc(bal & lt)] = (unsigned short)((slot << 9) | ((lo + itn * 32 + lane) * 2 + sgn));
+        nnear += __popc(bal);
       }
     }
+    __syncwarp();
   };
   // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then each piece
   // on its frequencies with the whole warp
@@ -520,8 +536,15 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       s_pk[wib][lane] = far_moments_ol<T, KM>(d, ff, scr + lane * SKM);
     }
     __syncwarp();
-    for (int p = 0; p < n; ++p) {
-      if (nfb > kFbCap - 2 * kNWPass) fallback_flush();  // room for the piece's entries (warp-uniform)
+    // pieces one by one (p < n), the near list whenever it might not hold another piece's
+    // entries and after the last piece (p == n; one call site), with room for its leftovers
+#pragma unroll 1
+    for (int p = 0; p <= n; ++p) {
+      if (p == n ? nnear > 0 : nnear > kNearCap - 2 * kNWPass) {  // warp-uniform
+        if (nfb > kFbCap - kNearCap) fallback_flush();
+        near_drain();
+      }
+      if (p == n) break;
       const int sl = (qh + p) % QC;
       T ee[4], ff[4];
 #pragma unroll
@@ -530,7 +553,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         ff[i] = s_qf[wib][sl][i];
       }
       eval_piece(ee, ff, s_qv[wib][sl][0], s_qv[wib][sl][1], s_qv[wib][sl][2], scr + p * SKM, s_pk[wib][p],
-                 s_qb[wib][sl]);
+                 s_qb[wib][sl], sl);
     }
     qh += n;
     __syncwarp();
@@ -560,11 +583,13 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
     __syncwarp();
     unsigned mask = __ballot_sync(kFull, has && b >= 0);
+#pragma unroll 1
     while (mask) {  // warp-uniform
       const int p = __ffs(mask) - 1;
       mask &= mask - 1u;
       const int bp = __shfl_sync(kFull, b, p);
       const int K = bp < kBoxFine ? KF : KG, base = slot_base<FP64>(bp);
+#pragma unroll 1
       for (int k = lane; k < K; k += 32) acc[base + k] += scr[p * SKF + k];
     }
     const bool queue = has && b < kBoxFine;
@@ -702,6 +727,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   };
   bool first = true;  // this warp's first batch writes its box partials, later ones add to them
   for (long long batch = gwarp; batch < nbatch; batch += nwarps) {
+#pragma unroll 1
     for (int iw = lane; iw < nw; iw += 32) {
       sR[wib][iw] = T(0);
       sI[wib][iw] = T(0);
@@ -823,12 +849,14 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     qh = qt = 0;  // (the last pass of drain_items emptied the queue)
     if (nfb > 0) fallback_flush();  // warp-uniform
     __syncwarp();
+#pragma unroll 1
     for (int iw = lane; iw < nw; iw += 32) {
       db.partR[batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
       db.partI[batch * nw + iw] = (double)sI[wib][iw] + (double)cI[wib][iw];
     }
     // this batch's box sums into the warp's FP64 partials (a fixed order: bitwise reproducible)
     if (boxes) {
+#pragma unroll 1
       for (int i = lane; i < NS; i += 32) {
         const double v = (double)acc[i];
         gpart[i] = first ? v : gpart[i] + v;
@@ -839,6 +867,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     __syncwarp();
   }
   if (boxes && first)  // a warp without batches
+#pragma unroll 1
     for (int i = lane; i < NS; i += 32) gpart[i] = 0.0;
   if (counters) {
     unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64,
