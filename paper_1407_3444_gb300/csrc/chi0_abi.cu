@@ -51,7 +51,9 @@ struct chi0_plan {
   double *box_part_d = nullptr;               // per-warp box moments, their totals and the
   double *box_tot_d = nullptr;                // boxes' share of Re per frequency
   double *far_d = nullptr;
-  void *fb_d = nullptr;                       // dynamic weights: per-warp fallback entries
+  void *fb_d = nullptr;                       // dynamic weights: per-warp fallback entries,
+  unsigned long long *fx_d = nullptr;         // per-CTA fixed-point sums (FP32) and the
+  unsigned long long *ctr_d = nullptr;        // batch counter
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
   int static_grid = 0, dynamic_grid = 0;  // persistent CTAs of the weight kernels
@@ -150,6 +152,8 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->box_tot_d);
   cudaFree(p->far_d);
   cudaFree(p->fb_d);
+  cudaFree(p->fx_d);
+  cudaFree(p->ctr_d);
 }
 
 extern "C" void chi0_destroy(chi0_plan_t *p) {
@@ -303,6 +307,8 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     CK(p, cudaMalloc(&p->box_tot_d, sizeof(double) * dynamic_box_slots(fp64)));
     CK(p, cudaMalloc(&p->far_d, sizeof(double) * dynamic_max_nw()));
     CK(p, cudaMalloc(&p->fb_d, warps * dynamic_fb_bytes(fp64)));
+    CK(p, cudaMalloc(&p->fx_d, dynamic_fx_bytes(dynamic_max_ctas_per_sm(fp64) * device_sms())));
+    CK(p, cudaMalloc(&p->ctr_d, sizeof(unsigned long long)));
   }
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, p->stream));
   CK(p, cudaStreamSynchronize(p->stream));
@@ -489,16 +495,18 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
       const int maxw = dynamic_max_nw();
       for (int w0 = 0; w0 < nw; w0 += maxw) {
         const int nwc = nw - w0 < maxw ? nw - w0 : maxw;
-        DynBufs db{p->partR, p->partI, p->box_tab_d, p->box_part_d, p->box_tot_d, p->far_d, p->fb_d};
+        DynBufs db{p->partR, p->partI, p->box_tab_d, p->box_part_d, p->box_tot_d, p->far_d, p->fb_d, p->fx_d,
+                   p->ctr_d};
+        int rows = nb;
         tm.start(CHI0_K_DYNAMIC);
         CK(p, launch_dynamic(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
-                             om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s, Eklo, Ekqlo));
-        p->stats.kernels += 4;  // box table, weights, box sums, box evaluation
+                             om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s, Eklo, Ekqlo, &rows));
+        p->stats.kernels += fp64 ? 4 : 5;  // box table, weights, box sums, box evaluation (+ row sums)
         tm.stop();
         tm.start(CHI0_K_REDUCE);
-        CK(p, launch_reduce(p->partR, nb, nwc, scale, q.gamma ? p->dos_d : nullptr, ndos, om_d + w0,
+        CK(p, launch_reduce(p->partR, rows, nwc, scale, q.gamma ? p->dos_d : nullptr, ndos, om_d + w0,
                             outR + (size_t)iq * nw + w0, s, p->far_d));
-        CK(p, launch_reduce(p->partI, nb, nwc, scale, nullptr, 0, nullptr, outI + (size_t)iq * nw + w0, s));
+        CK(p, launch_reduce(p->partI, rows, nwc, scale, nullptr, 0, nullptr, outI + (size_t)iq * nw + w0, s));
         p->stats.kernels += 2;
         tm.stop();
       }

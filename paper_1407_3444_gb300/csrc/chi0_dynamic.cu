@@ -36,13 +36,18 @@
 // Work layout.  A warp takes a batch of 32 tetrahedra; the batch's (m, n) items are sorted
 // into whole-tetrahedron and cut lists and carved 32 at a time, one item per lane, in warp-
 // uniform steps that emit at most one final tetrahedron per lane.  Each piece finds its box
-// and moments in its lane; the moments go to per-warp sums in shared memory (one lane per
-// moment index, pieces in lane order: no atomics), added after every batch into per-warp FP64
-// partials in global memory.  Pieces that evaluate frequencies themselves (fine boxes, or no
-// box) go to a per-warp ring queue that the whole warp evaluates, lanes owning frequencies,
-// over the frequency range its box leaves to it.  Batches are assigned to warps statically
-// (batch = warp + k * warps), and every sum runs in a fixed order, so results are bitwise
-// reproducible for a given launch shape.
+// and moments in its lane (one lane per moment index adds them to the box sums).  Pieces that
+// evaluate frequencies themselves (fine boxes, or no box) go to a per-warp ring queue that the
+// whole warp drains 32 pieces at a time: own series with lanes owning frequencies, then the
+// near-field (piece, frequency, term) entries of all of them packed one per lane; entries the
+// shared divided-difference table leaves go to a per-warp fallback buffer in global memory,
+// evaluated in full rounds when it fills.
+// Sums.  FP32 kernel: per-CTA sums in 64-bit fixed point (units of 2^-44) in shared memory,
+// added with integer atomics and written once per CTA: integer sums are exact in any order, so
+// the warps take batches from a launch-wide counter (balanced loads) and the results are
+// bitwise reproducible for any launch shape.  FP64 kernel: per-warp compensated FP64 sums per
+// batch, batches assigned statically (batch = warp + k * warps), every sum in a fixed order:
+// bitwise reproducible for a given launch shape.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -63,6 +68,11 @@ using grid::kFull;
 using grid::tet_corners;
 
 constexpr int kNWPass = 256;   // frequencies per dynamic pass
+// FP32 kernel: sums in 64-bit fixed point, units of 2^-44 (exact and order-independent; every
+// per-CTA total stays far below 2^19, and one rounding of 2^-45 per term is far below the
+// FP32 terms' own error)
+constexpr float kFxScale = 17592186044416.0f;  // 2^44
+constexpr double kFxUnit = 1.0 / 17592186044416.0;
 constexpr int kNearCap = 1024;  // near-field (piece, frequency, term) entries listed per warp
 constexpr int kFbCap = 4096;   // near-field entries left to the per-vertex table, per warp
 static_assert(kFbCap >= 4 * kNearCap, "the fallback buffer holds several near lists' leftovers");
@@ -204,14 +214,32 @@ template <typename T> __device__ __noinline__ void box_moments_ol(const T e[4], 
   }
 }
 
+// the same moments added straight into fixed-point box sums dst[0..K) (shared-memory atomics)
+__device__ __noinline__ void box_moments_fx_ol(const float e[4], const float f[4], float v, unsigned long long *dst,
+                                               int K) {
+  float H[4] = {1.f, 1.f, 1.f, 1.f};
+  float P[4] = {1.f, 1.f, 1.f, 1.f};
+  atomicAdd(&dst[0], (unsigned long long)__float2ll_rn(v * 0.25f * (f[0] + f[1] + f[2] + f[3]) * kFxScale));
+#pragma unroll 1
+  for (int k = 1; k < K; ++k) {
+    H[0] = e[0] * H[0];
+#pragma unroll
+    for (int l = 1; l < 4; ++l) H[l] = H[l - 1] + e[l] * H[l];
+    float sj = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      P[jj] = H[3] + e[jj] * P[jj];
+      sj += f[jj] * P[jj];
+    }
+    atomicAdd(&dst[k], (unsigned long long)__float2ll_rn(v * tabs(series_coef<float>(k)) * sj * kFxScale));
+  }
+}
+
 // Out-of-line copies of the large per-piece helpers: the weight kernel calls each from a few
 // places, and inlined copies made its body overflow the instruction cache (ncu: 45% of the issue
 // stalls waiting for instructions).
 template <typename T, int KM>
 __device__ __noinline__ int far_moments_ol(const T d[4], const T f[4], T *a) { return far_moments<T, KM>(d, f, a); }
-template <typename T> __device__ __noinline__ T far_eval_ol(const T *a, int K, T c, T w, T rho) {
-  return far_eval(a, K, c, w, rho);
-}
 template <typename T> __device__ __noinline__ bool inv_sum_shared_ol(const T x[4], const T f[4], T &out) {
   return inv_sum_shared(x, f, out);
 }
@@ -274,7 +302,7 @@ __device__ __forceinline__ void near_knots(int ent, const T d[4], const T e[4], 
 }
 
 template <bool FP64>
-__global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
+__global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
     k_dynamic(Grid g, Tet tet, const void *__restrict__ Ek, const void *__restrict__ Ekq, Q q,
               const void *__restrict__ W2, int cma, float tau, const short *__restrict__ occ,
               const short *__restrict__ empq, const double *__restrict__ omega, int nw, DynBufs db,
@@ -299,18 +327,24 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   // ring queue: offsets e from D0 (sorted), values f, (weight, D0h, D0l), box
   __shared__ T s_qe[W][QC][4], s_qf[W][QC][4], s_qv[W][QC][3];
   __shared__ int s_qb[W][QC];
-  __shared__ T sR[W][kNWPass], sI[W][kNWPass];
-  __shared__ T cR[W][kNWPass], cI[W][kNWPass];  // compensation terms
+  // FP64 kernel: per-warp compensated sums of the batch (static batch order); FP32 kernel:
+  // per-CTA fixed-point sums of the whole launch (s_fx; batches in any order)
+  constexpr bool FX = !FP64;
+  constexpr int WA = FX ? 1 : W, NA = FX ? 1 : kNWPass;
+  __shared__ T sR[WA][NA], sI[WA][NA];
+  __shared__ T cR[WA][NA], cI[WA][NA];  // compensation terms
+  __shared__ unsigned long long s_fx[FX ? 2 : 1][FX ? kNWPass : 1];
   __shared__ T s_w[kNWPass];
   __shared__ T s_wl[FP64 ? 1 : kNWPass];  // FP32 path: w - (float)w
   // near-field entries of the drain's pieces: ring slot << 9 | 2 * frequency index + term
   __shared__ unsigned short s_near[W][kNearCap];
   __shared__ short s_rng[kBoxFine][2];  // frequencies a fine box leaves to its pieces: [lo, hi)
   __shared__ BoxTab<T> s_tab;
-  extern __shared__ __align__(16) unsigned char s_dyn[];  // per-warp box sums [W][NS]
+  extern __shared__ __align__(16) unsigned char s_dyn[];  // box sums: [W][NS] (FP64), [NS] fixed point
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   T *acc = (T *)s_dyn + (size_t)wib * NS;
+  unsigned long long *bfx = (unsigned long long *)s_dyn;
   T *scr = s_scr[wib];
   const int w = q.hi - q.lo;
   const long long nbatch = (g.ntet + 31) / 32;
@@ -328,8 +362,15 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
 #pragma unroll 1
     for (int i = threadIdx.x; i < nwords; i += blockDim.x) ((int *)&s_tab)[i] = ((const int *)src)[i];
   }
+  if constexpr (FX) {
 #pragma unroll 1
-  for (int i = lane; i < NS; i += 32) acc[i] = T(0);
+    for (int i = threadIdx.x; i < NS; i += blockDim.x) bfx[i] = 0ull;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < 2 * kNWPass; i += blockDim.x) s_fx[i / kNWPass][i % kNWPass] = 0ull;
+  } else {
+#pragma unroll 1
+    for (int i = lane; i < NS; i += 32) acc[i] = T(0);
+  }
   __syncthreads();
   // frequency ranges of the fine boxes: contiguous when |w| ascends along the grid (an
   // interval for the - term, a prefix for the + term); otherwise the whole grid, the
@@ -364,6 +405,38 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   // one queued final tetrahedron (sorted offsets ee from D0 = D0h + D0l, values ff, weight vr,
   // own far-field moments am[0..K)) on the frequencies its box (b >= 0) leaves to it, or on
   // all of them (b < 0); lanes own frequencies
+  // one term of Re / Im at frequency iw
+  auto add_re = [&](int iw, T v) {
+    if constexpr (FX) atomicAdd(&s_fx[0][iw], (unsigned long long)__float2ll_rn(v * kFxScale));
+    else kadd_t(sR[wib][iw], cR[wib][iw], v);
+  };
+  auto add_im = [&](int iw, T v) {
+    if constexpr (FX) atomicAdd(&s_fx[1][iw], (unsigned long long)__float2ll_rn(v * kFxScale));
+    else kadd_t(sI[wib][iw], cI[wib][iw], v);
+  };
+  // one round of per-lane results (iw < 0: nothing).  Fixed point: atomic adds (exact, any
+  // order).  FP64: lanes that share a frequency add one at a time in lane order (the lists are
+  // built in a fixed order, so the sums are reproducible), the others at once.
+  auto round_add = [&](int iw, T re, T im) {
+    if constexpr (FX) {
+      if (iw >= 0) {
+        add_re(iw, re);
+        if (im != T(0)) add_im(iw, im);
+      }
+    } else {
+      const unsigned grp = __match_any_sync(kFull, iw >= 0 ? iw : -1 - lane);
+      const int rank = __popc(grp & lt);
+      const int nr = __reduce_max_sync(kFull, iw >= 0 ? rank : 0);
+#pragma unroll 1
+      for (int r = 0; r <= nr; ++r) {
+        if (iw >= 0 && rank == r) {
+          add_re(iw, re);
+          if (im != T(0)) add_im(iw, im);
+        }
+        __syncwarp();
+      }
+    }
+  };
   int nfb = 0;  // entries in the warp's fallback buffer
   // the fallback buffer: per-vertex table, one entry per lane and round (full rounds: the
   // buffer collects the entries of many pieces).  Lanes that share a frequency add one at a
@@ -393,17 +466,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
           if (code & 1) im = -im;
         }
       }
-      const unsigned grp = __match_any_sync(kFull, iw);
-      const int rank = __popc(grp & lt);
-      const int nr = __reduce_max_sync(kFull, iw >= 0 ? rank : 0);
-#pragma unroll 1
-      for (int r = 0; r <= nr; ++r) {
-        if (iw >= 0 && rank == r) {
-          kadd_t(sR[wib][iw], cR[wib][iw], re);
-          if (im != T(0)) kadd_t(sI[wib][iw], cI[wib][iw], im);
-        }
-        __syncwarp();
-      }
+      round_add(iw, re, im);
     }
     nfb = 0;
   };
@@ -451,17 +514,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
           left = true;
         }
       }
-      const unsigned grp = __match_any_sync(kFull, iw);
-      const int rank = __popc(grp & lt);
-      const int nr = __reduce_max_sync(kFull, iw >= 0 ? rank : 0);
-#pragma unroll 1
-      for (int r = 0; r <= nr; ++r) {
-        if (iw >= 0 && rank == r) {
-          kadd_t(sR[wib][iw], cR[wib][iw], re);
-          if (im != T(0)) kadd_t(sI[wib][iw], cI[wib][iw], im);
-        }
-        __syncwarp();
-      }
+      round_add(iw, re, im);
       const unsigned bal = __ballot_sync(kFull, left);
       if (bal) {  // warp-uniform
         if (left) {
@@ -494,18 +547,17 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     for (int iw = lo + lane, itn = 0; iw < hi; iw += 32, ++itn) {
       const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
       T re = T(0);
-      if (b < 0 || !box_far(Cb, Rb, b, om, 1)) {
-        const T rp = quot(half, c + om);
-        if (rp <= T(Num<T>::kappa_far)) re += far_eval_ol(am, K, c, -om, rp);
-        else nearp |= 1u << itn;
+#pragma unroll 1
+      for (int t = 1; t >= 0; --t) {  // the + term (t = 1), then the - term
+        if (b < 0 || !box_far(Cb, Rb, b, om, t)) {
+          const T den = t ? c + om : c - om;
+          const T r = quot(half, den < T(0) ? -den : den);
+          if (r <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, t ? -om : om, r);
+          else if (t) nearp |= 1u << itn;
+          else nearm |= 1u << itn;
+        }
       }
-      if (b < 0 || !box_far(Cb, Rb, b, om, 0)) {
-        const T dm = c - om;
-        const T rm = quot(half, dm < T(0) ? -dm : dm);
-        if (rm <= T(Num<T>::kappa_far)) re += far_eval_ol(am, K, c, om, rm);
-        else nearm |= 1u << itn;
-      }
-      if (re != T(0)) kadd_t(sR[wib][iw], cR[wib][iw], vr * re);
+      if (re != T(0)) add_re(iw, vr * re);
     }
     // near field: the (frequency, term) pairs go to the drain's near list (the caller keeps
     // room for them)
@@ -577,20 +629,23 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
         T e[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) e[i] = (base + ee[i]) * ri;
-        box_moments_ol(e, ff, vr, scr + lane * SKF, b < kBoxFine ? KF : KG);
+        if constexpr (FX) box_moments_fx_ol(e, ff, vr, bfx + slot_base<FP64>(b), b < kBoxFine ? KF : KG);
+        else box_moments_ol(e, ff, vr, scr + lane * SKF, b < kBoxFine ? KF : KG);
         ++nboxed;
       }
     }
-    __syncwarp();
-    unsigned mask = __ballot_sync(kFull, has && b >= 0);
+    if constexpr (!FX) {  // FP64 box sums: one moment index per lane, pieces in lane order
+      __syncwarp();
+      unsigned mask = __ballot_sync(kFull, has && b >= 0);
 #pragma unroll 1
-    while (mask) {  // warp-uniform
-      const int p = __ffs(mask) - 1;
-      mask &= mask - 1u;
-      const int bp = __shfl_sync(kFull, b, p);
-      const int K = bp < kBoxFine ? KF : KG, base = slot_base<FP64>(bp);
+      while (mask) {  // warp-uniform
+        const int p = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const int bp = __shfl_sync(kFull, b, p);
+        const int K = bp < kBoxFine ? KF : KG, base = slot_base<FP64>(bp);
 #pragma unroll 1
-      for (int k = lane; k < K; k += 32) acc[base + k] += scr[p * SKF + k];
+        for (int k = lane; k < K; k += 32) acc[base + k] += scr[p * SKF + k];
+      }
     }
     const bool queue = has && b < kBoxFine;
     const unsigned qm = __ballot_sync(kFull, queue);
@@ -726,13 +781,28 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
     }
   };
   bool first = true;  // this warp's first batch writes its box partials, later ones add to them
-  for (long long batch = gwarp; batch < nbatch; batch += nwarps) {
+  // batches: FP64 kernel in a fixed order per warp (batch = warp + k x warps: its FP64 sums are
+  // reproducible); FP32 kernel from a launch-wide counter (its sums are exact integers, whatever
+  // the order), which balances the warps' loads
+  auto next_batch = [&](long long cur) -> long long {
+    if constexpr (FX) {
+      unsigned long long b = 0ull;
+      if (lane == 0) b = atomicAdd(db.ctr, 1ull);
+      return (long long)__shfl_sync(kFull, b, 0);
+    } else {
+      return cur < 0 ? gwarp : cur + nwarps;
+    }
+  };
 #pragma unroll 1
-    for (int iw = lane; iw < nw; iw += 32) {
-      sR[wib][iw] = T(0);
-      sI[wib][iw] = T(0);
-      cR[wib][iw] = T(0);
-      cI[wib][iw] = T(0);
+  for (long long batch = next_batch(-1); batch < nbatch; batch = next_batch(batch)) {
+    if constexpr (!FX) {
+#pragma unroll 1
+      for (int iw = lane; iw < nw; iw += 32) {
+        sR[wib][iw] = T(0);
+        sI[wib][iw] = T(0);
+        cR[wib][iw] = T(0);
+        cI[wib][iw] = T(0);
+      }
     }
     const long long t = batch * 32 + lane;
     int cnt = 0;
@@ -847,28 +917,42 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
       if (last) break;
     }
     qh = qt = 0;  // (the last pass of drain_items emptied the queue)
-    if (nfb > 0) fallback_flush();  // warp-uniform
-    __syncwarp();
+    if constexpr (!FX) {
+      if (nfb > 0) fallback_flush();  // warp-uniform
+      __syncwarp();
 #pragma unroll 1
-    for (int iw = lane; iw < nw; iw += 32) {
-      db.partR[batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
-      db.partI[batch * nw + iw] = (double)sI[wib][iw] + (double)cI[wib][iw];
-    }
-    // this batch's box sums into the warp's FP64 partials (a fixed order: bitwise reproducible)
-    if (boxes) {
+      for (int iw = lane; iw < nw; iw += 32) {
+        db.partR[batch * nw + iw] = (double)sR[wib][iw] + (double)cR[wib][iw];
+        db.partI[batch * nw + iw] = (double)sI[wib][iw] + (double)cI[wib][iw];
+      }
+      // this batch's box sums into the warp's FP64 partials (a fixed order: bitwise reproducible)
+      if (boxes) {
 #pragma unroll 1
-      for (int i = lane; i < NS; i += 32) {
-        const double v = (double)acc[i];
-        gpart[i] = first ? v : gpart[i] + v;
-        acc[i] = T(0);
+        for (int i = lane; i < NS; i += 32) {
+          const double v = (double)acc[i];
+          gpart[i] = first ? v : gpart[i] + v;
+          acc[i] = T(0);
+        }
       }
     }
     first = false;
     __syncwarp();
   }
-  if (boxes && first)  // a warp without batches
+  if constexpr (FX) {
+    // the warp's remaining fallback entries, then the CTA's fixed-point sums into its rows
+    if (nfb > 0) fallback_flush();  // warp-uniform
+    __syncthreads();
+    unsigned long long *row = db.fx + (size_t)blockIdx.x * 2 * kNWPass;
+    unsigned long long *brow = (unsigned long long *)db.box_part + (size_t)blockIdx.x * NS;
 #pragma unroll 1
-    for (int i = lane; i < NS; i += 32) gpart[i] = 0.0;
+    for (int i = threadIdx.x; i < 2 * kNWPass; i += blockDim.x) row[i] = s_fx[i / kNWPass][i % kNWPass];
+#pragma unroll 1
+    for (int i = threadIdx.x; i < NS; i += blockDim.x) brow[i] = bfx[i];
+  } else {
+    if (boxes && first)  // a warp without batches
+#pragma unroll 1
+      for (int i = lane; i < NS; i += 32) gpart[i] = 0.0;
+  }
   if (counters) {
     unsigned long long a = (unsigned long long)npieces, b = (unsigned long long)nfp64,
                        x = (unsigned long long)nboxed;
@@ -886,22 +970,42 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, 2)
   }
 }
 
-// box totals: slot i summed over the warps of the weight launch, in warp order
+// box totals: slot i summed over the rows of the weight launch (FP64 kernel: per-warp FP64
+// partials, in warp order; FP32 kernel: per-CTA fixed-point rows, summed exactly)
 template <bool FP64>
-__global__ void __launch_bounds__(256) k_box_sum(const double *__restrict__ part, int nwarps, double *__restrict__ tot) {
+__global__ void __launch_bounds__(256) k_box_sum(const double *__restrict__ part, int nrows, double *__restrict__ tot) {
   constexpr int NS = box_slots<FP64>();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NS) return;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int wv = 0;
-  for (; wv + 3 < nwarps; wv += 4) {
-    s0 += part[(size_t)wv * NS + i];
-    s1 += part[(size_t)(wv + 1) * NS + i];
-    s2 += part[(size_t)(wv + 2) * NS + i];
-    s3 += part[(size_t)(wv + 3) * NS + i];
+  if constexpr (FP64) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int wv = 0;
+    for (; wv + 3 < nrows; wv += 4) {
+      s0 += part[(size_t)wv * NS + i];
+      s1 += part[(size_t)(wv + 1) * NS + i];
+      s2 += part[(size_t)(wv + 2) * NS + i];
+      s3 += part[(size_t)(wv + 3) * NS + i];
+    }
+    for (; wv < nrows; ++wv) s0 += part[(size_t)wv * NS + i];
+    tot[i] = (s0 + s1) + (s2 + s3);
+  } else {
+    const unsigned long long *fx = (const unsigned long long *)part;
+    unsigned long long a = 0ull;
+    for (int r = 0; r < nrows; ++r) a += fx[(size_t)r * NS + i];
+    tot[i] = (double)(long long)a * kFxUnit;
   }
-  for (; wv < nwarps; ++wv) s0 += part[(size_t)wv * NS + i];
-  tot[i] = (s0 + s1) + (s2 + s3);
+}
+
+// FP32 kernel: Re and Im per frequency from the CTAs' fixed-point rows (exact sums) into row 0
+// of the partials
+__global__ void __launch_bounds__(256) k_fx_rows(const unsigned long long *__restrict__ fx, int nrows, int nw,
+                                                 double *__restrict__ partR, double *__restrict__ partI) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * nw) return;
+  const int term = i / nw, iw = i % nw;
+  unsigned long long a = 0ull;
+  for (int r = 0; r < nrows; ++r) a += fx[((size_t)r * 2 + term) * kNWPass + iw];
+  (term ? partI : partR)[iw] = (double)(long long)a * kFxUnit;
 }
 
 // far[iw]: the boxes' share of Re at frequency iw (FP64 evaluation of the multipoles); one
@@ -940,7 +1044,8 @@ __global__ void __launch_bounds__(128) k_box_eval(const double *__restrict__ ome
 }
 
 template <bool FP64> size_t dyn_smem() {
-  return (size_t)DynShape<FP64>::warps * box_slots<FP64>() * (FP64 ? sizeof(double) : sizeof(float));
+  return FP64 ? (size_t)DynShape<FP64>::warps * box_slots<FP64>() * sizeof(double)
+              : (size_t)box_slots<FP64>() * sizeof(unsigned long long);
 }
 
 }  // namespace
@@ -948,6 +1053,7 @@ template <bool FP64> size_t dyn_smem() {
 int dynamic_max_nw() { return kNWPass; }
 int dynamic_warps_per_cta(int fp64) { return fp64 ? DynShape<true>::warps : DynShape<false>::warps; }
 size_t dynamic_box_slots(int fp64) { return fp64 ? box_slots<true>() : box_slots<false>(); }
+size_t dynamic_fx_bytes(int nblocks) { return (size_t)nblocks * 2 * kNWPass * sizeof(unsigned long long); }
 size_t dynamic_fb_bytes(int fp64) {
   return (size_t)kFbCap * (fp64 ? sizeof(FbEnt<double>) : sizeof(FbEnt<float>));
 }
@@ -967,10 +1073,11 @@ cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const 
                            const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
                            const double *omega, int nw, const DynBufs &db, int nblocks,
                            unsigned long long *counters, cudaStream_t s, const float *Eklo,
-                           const float *Ekqlo) {
+                           const float *Ekqlo, int *rows) {
   if (nw > kNWPass || nw <= 0 || nblocks <= 0) return cudaErrorInvalidValue;
   if (!fp64 && (!Eklo || !Ekqlo)) return cudaErrorInvalidValue;
-  if (!db.box_tab || !db.box_part || !db.box_tot || !db.far || !db.fb) return cudaErrorInvalidValue;
+  if (!db.box_tab || !db.box_part || !db.box_tot || !db.far || !db.fb || !db.fx || !db.ctr)
+    return cudaErrorInvalidValue;
   if (fp64) {
     const int nwarps = nblocks * DynShape<true>::warps;
     k_box_setup<double><<<1, 256, 0, s>>>(omega, nw, (BoxTab<double> *)db.box_tab);
@@ -978,13 +1085,17 @@ cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const 
         g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db, Eklo, Ekqlo, counters);
     k_box_sum<true><<<(box_slots<true>() + 255) / 256, 256, 0, s>>>(db.box_part, nwarps, db.box_tot);
     k_box_eval<true><<<nw, 128, 0, s>>>(omega, db.box_tab, db.box_tot, db.far);
+    *rows = (int)((g.ntet + 31) / 32);
   } else {
-    const int nwarps = nblocks * DynShape<false>::warps;
+    cudaError_t e = cudaMemsetAsync(db.ctr, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     k_box_setup<float><<<1, 256, 0, s>>>(omega, nw, (BoxTab<float> *)db.box_tab);
     k_dynamic<false><<<nblocks, DynShape<false>::threads, dyn_smem<false>(), s>>>(
         g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db, Eklo, Ekqlo, counters);
-    k_box_sum<false><<<(box_slots<false>() + 255) / 256, 256, 0, s>>>(db.box_part, nwarps, db.box_tot);
+    k_box_sum<false><<<(box_slots<false>() + 255) / 256, 256, 0, s>>>(db.box_part, nblocks, db.box_tot);
     k_box_eval<false><<<nw, 128, 0, s>>>(omega, db.box_tab, db.box_tot, db.far);
+    k_fx_rows<<<(2 * nw + 255) / 256, 256, 0, s>>>(db.fx, nblocks, nw, db.partR, db.partI);
+    *rows = 1;
   }
   return cudaGetLastError();
 }

@@ -97,20 +97,23 @@ size_t static_piece_bytes(int fp64);
 struct DynBufs {
   double *partR, *partI;  // [nbatch][nw]
   void *box_tab;          // box centres and radii of the pass (dynamic_box_tab_bytes())
-  double *box_part;       // [warps of the launch][dynamic_box_slots(fp64)]
+  double *box_part;       // [warps of the launch][dynamic_box_slots(fp64)] (FP32 kernel: int64 per CTA)
   double *box_tot;        // [dynamic_box_slots(fp64)]
   double *far;            // [nw]: Re contribution of the box multipoles per frequency
   void *fb;               // [warps of the launch][dynamic_fb_bytes(fp64)]: near-field entries
                           // left to the per-vertex table (scratch)
+  unsigned long long *fx;   // FP32 kernel: [CTAs of the launch][2][dynamic_max_nw()] fixed-point sums
+  unsigned long long *ctr;  // FP32 kernel: batch counter (reset by the launch)
 };
 
-// dynamic weights for one q and nw <= dynamic_max_nw() frequencies: partR/partI per batch and
-// far[nw] (add far to the sum of partR)
+// dynamic weights for one q and nw <= dynamic_max_nw() frequencies: partR/partI in *rows rows
+// of nw (FP64: one per batch; FP32: one) and far[nw] (add far to the sum of partR)
 cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
                            const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
                            const double *omega, int nw, const DynBufs &db, int nblocks,
                            unsigned long long *counters, cudaStream_t s, const float *Eklo,
-                           const float *Ekqlo);
+                           const float *Ekqlo, int *rows);
+size_t dynamic_fx_bytes(int nblocks);
 int dynamic_persistent_blocks(int fp64);
 int dynamic_warps_per_cta(int fp64);
 size_t dynamic_box_slots(int fp64);

@@ -519,7 +519,7 @@ template <typename T> __device__ __forceinline__ T far_eval(const T *a, int K, T
   const T z = c * rd;
   int kk = K;
   if (rho > T(0)) {
-    const float need = __log2f((float)Num<T>::tol) / __log2f((float)rho);  // rho^need = tol
+    const float need = __fdividef(__log2f((float)Num<T>::tol), __log2f((float)rho));  // rho^need = tol
     kk = min(K, 2 + (int)need);
   }
   T sum = T(0);
