@@ -279,10 +279,12 @@ def arithmetic_peaks(chi0):
 FLOPS_PER_PIECE_MIXED = 202.6
 TRAFFIC_PER_PIECE_MIXED = 3.58
 # The same for the dynamic weight kernel per final tetrahedron over one pass of 256 frequencies
-# (ncu counters of k_dynamic on the 80-band model, 24^3 mesh, one q; the FP64 kernel's FP64
-# operations likewise).  None until counted on the current kernel.
-FLOPS_PER_PIECE_DYN32 = None
-FLOPS_PER_PIECE_DYN64 = None
+# (ncu instruction counters of k_dynamic on a seeded sample of 16384 tetrahedra of the 80-band
+# 72^3 mesh, one q: the full mesh's mix of pieces; the FP64 kernel's FP64 operations likewise).
+# DRAM bytes: not taken from the sample (its scattered tetrahedra defeat the caches that the
+# whole mesh uses), None until counted on the whole mesh.
+FLOPS_PER_PIECE_DYN32 = 2855.8
+FLOPS_PER_PIECE_DYN64 = 5846.8
 TRAFFIC_PER_PIECE_DYN32 = None
 
 
@@ -492,6 +494,7 @@ def run_ours(args):
         del host
 
     peaks, kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_pk = peaks_run.get("fp32_fma_tflops")
     fp64_pk = peaks_run.get("fp64_fma_tflops")
     if W.omega is None:
@@ -515,7 +518,7 @@ def run_ours(args):
             "frac": ach / fp32_pk if (ach is not None and fp32_pk) else None,
             "traffic": tpu * units if tpu else None, "kernel": kname, "kernel_ms": k_ms,
             "units_per_launch": units, "unit_name": uname, "flops_per_unit": fpu,
-            "final_tetrahedra_per_s_per_sm": units / (k_ms * 1e-3) / 152.0 if k_ms else None,
+            "final_tetrahedra_per_s_per_sm": units / (k_ms * 1e-3) / sms if k_ms else None,
             "peak_source": "measured FP32 FMA peak of this GPU (chi0_peak, this run)"}
     roof64 = None
     if dyn64_ms and pieces64:

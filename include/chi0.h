@@ -221,6 +221,20 @@ int chi0_plan(const chi0_kgrid_t *kgrid, const chi0_tetra_t *tetra, chi0_band_wi
  * opts.wait_budget; the results of the call are then undefined, the plan stays usable). */
 int chi0_static(chi0_plan_t *plan, const chi0_q_t *q, int nq, double *chi);
 
+/* Static chi0 as chi0_static, and its band-pair contributions (the two-dimensional histogram
+ * of Sec. III, Fig. 8: the part of chi0(q) from transitions m -> n):
+ *   pairs[off_q + (m - lo_q) * w_q + (n - lo_q)],  w_q = hi_q - lo_q,
+ * with the q blocks back to back (off_q = sum of w^2 over the q before it).  Occupied band m
+ * at k, empty band n at k+q (Eq. 1), the normalisation and sign of chi; at a q flagged
+ * Gamma the intraband pairs (m, m) carry the q -> 0 limit N(eF) of band m (Sec. III).  The
+ * pairs of a q add up to chi[iq].  Each pair is summed in 64-bit fixed point (units of
+ * 2^-50 before the normalisation: exact in any order, reproducible, one rounding of 2^-51
+ * per term).  pairs is a host or device pointer like chi (opts.outputs_on_device) with room
+ * for sum_q w_q^2 doubles; the call does not use graph capture.  Errors as chi0_static, plus
+ * CHI0_EINVAL for pairs NULL or a plan window wider than 1024 bands.  The paper's figure is
+ * a plot of these numbers; this entry point has no other counterpart in it. */
+int chi0_static_pairs(chi0_plan_t *plan, const chi0_q_t *q, int nq, double *chi, double *pairs);
+
 /* Dynamic chi0(q, w) (Eqs. 1-3) on nw frequencies: re[iq*nw + iw], im[iq*nw + iw].
  * Re is the principal value of Eq. 1; Im is Eq. 2 for w > 0, 0 at w = 0, and odd
  * (Eq. 3) for w < 0.  Errors as chi0_static, plus CHI0_EINVAL for nw <= 0. */
@@ -307,7 +321,7 @@ void chi0_destroy(chi0_plan_t *plan);
 const char *chi0_last_error(const chi0_plan_t *plan);
 
 /* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow
- * and chi0_stats_t.box_pieces. */
+ * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs. */
 int chi0_version(void);
 
 #ifdef __cplusplus

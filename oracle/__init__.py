@@ -62,6 +62,8 @@ def lib():
             L.oracle_tet_integrals.argtypes = [dp, dp, dp, ct.c_int, dp, dp, dp]
             L.oracle_chi0.restype = ct.c_int
             L.oracle_chi0.argtypes = [ct.POINTER(_Input), dp, dp]
+            L.oracle_chi0_pairs.restype = ct.c_int
+            L.oracle_chi0_pairs.argtypes = [ct.POINTER(_Input), dp]
             L.oracle_max_threads.restype = ct.c_int
             L.oracle_input_size.restype = ct.c_int
             assert L.oracle_input_size() == ct.sizeof(_Input), "oracle_input layout mismatch"
@@ -123,13 +125,8 @@ def tet_integrals(a, b, f=(1, 1, 1, 1), omega=None):
 
 
 # ---------------------------------------------------------------------- full chi0 for one q
-def chi0_q(W, q, omega=None, sign: int = 0, nthreads: int = 0, tet=None, tvol=None, window=None):
-    """chi0 at one q of workload W (see paper_1407_3444_gb300.workloads).
-
-    Returns the static value (float) when ``omega`` is None and W is static, else
-    (re[nw], im[nw]).  ``tet``/``tvol`` restrict the sum to a caller tetrahedron list."""
-    if omega is None:
-        omega = W.omega
+def _input(W, q, omega, sign, nthreads, tet, tvol, window):
+    """The oracle's input record for one q (and the arrays it points into)."""
     keep = []
     inp = _Input()
     inp.n[:] = list(W.n)
@@ -172,7 +169,18 @@ def chi0_q(W, q, omega=None, sign: int = 0, nthreads: int = 0, tet=None, tvol=No
         inp.omega = w.ctypes.data
     inp.sign = int(sign)
     inp.nthreads = int(nthreads)
-    nout = 1 if omega is None else w.size
+    return inp, keep, (int(lo), int(hi))
+
+
+def chi0_q(W, q, omega=None, sign: int = 0, nthreads: int = 0, tet=None, tvol=None, window=None):
+    """chi0 at one q of workload W (see paper_1407_3444_gb300.workloads).
+
+    Returns the static value (float) when ``omega`` is None and W is static, else
+    (re[nw], im[nw]).  ``tet``/``tvol`` restrict the sum to a caller tetrahedron list."""
+    if omega is None:
+        omega = W.omega
+    inp, keep, _ = _input(W, q, omega, sign, nthreads, tet, tvol, window)
+    nout = 1 if omega is None else len(omega)
     re = np.zeros(nout)
     im = np.zeros(nout)
     rc = lib().oracle_chi0(ct.byref(inp), _dp(re), _dp(im))
@@ -181,6 +189,18 @@ def chi0_q(W, q, omega=None, sign: int = 0, nthreads: int = 0, tet=None, tvol=No
     if omega is None:
         return float(re[0])
     return re, im
+
+
+def chi0_pairs_q(W, q, sign: int = 0, nthreads: int = 0, tet=None, tvol=None, window=None):
+    """Static chi0 at one q resolved by band pair: [w, w] array, entry (m - lo, n - lo) the
+    contribution of the transitions m -> n (Sec. III, Fig. 8); the entries add up to chi0_q."""
+    inp, keep, (lo, hi) = _input(W, q, None, sign, nthreads, tet, tvol, window)
+    w = hi - lo
+    out = np.zeros(w * w)
+    rc = lib().oracle_chi0_pairs(ct.byref(inp), _dp(out))
+    if rc != 0:
+        raise RuntimeError("oracle_chi0_pairs failed: %d" % rc)
+    return out.reshape(w, w)
 
 
 def chi0(W, omega=None, sign: int = 0, nthreads: int = 0, qs=None):

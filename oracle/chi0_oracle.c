@@ -552,6 +552,107 @@ int oracle_chi0(const oracle_input *in, double *re_out, double *im_out) {
   return 0;
 }
 
+/* Static chi0 resolved by band pair (Sec. III, Fig. 8: the contribution of the transitions
+ * m -> n): pairs[(m - lo) * w + (n - lo)], w = hi - lo, the same sum as oracle_chi0 at w = 0
+ * (same normalisation and sign) taken per (m, n); at Gamma the q -> 0 limit N(eF) of band m
+ * goes to the pair (m, m).  Returns 0 on success. */
+int oracle_chi0_pairs(const oracle_input *in, double *pairs) {
+  int N[3], w, nth = 1;
+  int64_t ntet, t;
+  double vol_builtin, sgn;
+  acc_t *P;
+  const double *Eq, *Cq;
+  if (!in || !pairs || in->nw != 0 || !in->E || in->nb <= 0 || in->lo < 0 || in->hi > in->nb ||
+      in->lo >= in->hi)
+    return -1;
+  if (!in->cma && !in->C) return -1;
+  if (!in->periodic && !in->Eq) return -1;
+  corner_dims(in, N);
+  w = in->hi - in->lo;
+  ntet = in->ntet > 0 ? in->ntet : 6LL * in->n[0] * in->n[1] * in->n[2];
+  vol_builtin = 1.0 / (6.0 * in->n[0] * in->n[1] * in->n[2]);
+  Eq = in->Eq ? in->Eq : in->E;
+  Cq = in->Eq ? in->Cq : in->C;
+  if (!in->cma && !Cq) return -1;
+#ifdef _OPENMP
+  nth = in->nthreads > 0 ? in->nthreads : omp_get_max_threads();
+#endif
+  P = (acc_t *)calloc((size_t)nth * w * w, sizeof(acc_t));
+  if (!P) return -2;
+
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nth)
+  for (t = 0; t < ntet; ++t) {
+    int tid = 0, i, m, n;
+    int64_t c[4], cq[4];
+    double vol;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    if (in->ntet > 0) {
+      for (i = 0; i < 4; ++i) c[i] = in->tet[4 * t + i];
+      vol = in->tvol[t];
+    } else {
+      builtin_tet(in, N, t, c);
+      vol = vol_builtin;
+    }
+    for (i = 0; i < 4; ++i) cq[i] = in->Eq ? c[i] : shifted(in, N, c[i]);
+    for (m = in->lo; m < in->hi; ++m) {
+      double a[4], amin = 1e300;
+      for (i = 0; i < 4; ++i) {
+        a[i] = in->E[c[i] * in->nb + m] - in->ef;
+        if (a[i] < amin) amin = a[i];
+      }
+      if (!(amin < 0.0)) continue;
+      for (n = in->lo; n < in->hi; ++n) {
+        double b[4], f[4], bmax = -1e300;
+        acc_t one = {0, 0}, none = {0, 0};
+        if (in->gamma && n == m) continue;
+        for (i = 0; i < 4; ++i) {
+          b[i] = Eq[cq[i] * in->nb + n] - in->ef;
+          if (b[i] > bmax) bmax = b[i];
+        }
+        if (!(bmax > 0.0)) continue;
+        for (i = 0; i < 4; ++i) f[i] = in->cma ? 1.0 : msq(in, c[i], cq[i], in->C, Cq, m, n);
+        tet_pair(a, b, f, vol, 0, NULL, &one, &none);
+        acc_add(&P[((size_t)tid * w + (m - in->lo)) * w + (n - in->lo)], acc_val(&one));
+      }
+    }
+  }
+
+  sgn = in->sign ? -1.0 : 1.0;
+  {
+    int k, th;
+    for (k = 0; k < w * w; ++k) {
+      acc_t R = {0, 0};
+      for (th = 0; th < nth; ++th) acc_add(&R, acc_val(&P[(size_t)th * w * w + k]));
+      pairs[k] = sgn * 2.0 * acc_val(&R);
+    }
+  }
+  if (in->gamma) {
+    int m;
+    for (m = in->lo; m < in->hi; ++m) {
+      acc_t G = {0, 0};
+      for (t = 0; t < ntet; ++t) {
+        int64_t c[4];
+        double vol, a[4];
+        int i;
+        if (in->ntet > 0) {
+          for (i = 0; i < 4; ++i) c[i] = in->tet[4 * t + i];
+          vol = in->tvol[t];
+        } else {
+          builtin_tet(in, N, t, c);
+          vol = vol_builtin;
+        }
+        for (i = 0; i < 4; ++i) a[i] = in->E[c[i] * in->nb + m] - in->ef;
+        acc_add(&G, vol * oracle_tet_dos(a));
+      }
+      pairs[(m - in->lo) * (w + 1)] += sgn * 2.0 * acc_val(&G);
+    }
+  }
+  free(P);
+  return 0;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -92,7 +92,8 @@ _lib = None
 
 # every entry point declared in include/chi0.h (checked by the ABI test)
 EXPORTS = ["chi0_opts_default", "chi0_plan", "chi0_static", "chi0_dynamic", "chi0_plan_stats",
-           "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune", "chi0_peak"]
+           "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune", "chi0_peak",
+           "chi0_static_pairs"]
 CHI0_PEAK_FP32_FMA, CHI0_PEAK_FP64_FMA, CHI0_PEAK_TF32_MMA, CHI0_PEAK_BF16_MMA = 0, 1, 2, 3
 CHI0_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -111,6 +112,8 @@ def lib():
         L.chi0_plan.restype = ct.c_int
         L.chi0_static.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p]
         L.chi0_static.restype = ct.c_int
+        L.chi0_static_pairs.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_void_p]
+        L.chi0_static_pairs.restype = ct.c_int
         L.chi0_dynamic.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_int,
                                    ct.c_void_p, ct.c_void_p]
         L.chi0_dynamic.restype = ct.c_int
@@ -158,6 +161,10 @@ def chi0_plan(kgrid: chi0_kgrid_t, tetra: Optional[chi0_tetra_t], window: chi0_b
 
 def chi0_static(plan, q, nq: int, chi_ptr: int) -> None:
     _check(lib().chi0_static(plan, q, nq, chi_ptr), plan)
+
+
+def chi0_static_pairs(plan, q, nq: int, chi_ptr: int, pairs_ptr: int) -> None:
+    _check(lib().chi0_static_pairs(plan, q, nq, chi_ptr, pairs_ptr), plan)
 
 
 def chi0_dynamic(plan, q, nq: int, omega_ptr: int, nw: int, re_ptr: int, im_ptr: int) -> None:
@@ -334,6 +341,7 @@ class Plan:
             tt = chi0_tetra_t(corners.shape[0], corners.ctypes.data, vols.ctypes.data)
         lo, hi = window if window is not None else W.window
         self.h = chi0_plan(kg, tt, chi0_band_window_t(lo, hi), o)
+        self.window = (lo, hi)
         if qs is None:
             self.qarr = self.make_q(W.qs, staged.q)
         else:
@@ -369,6 +377,31 @@ class Plan:
         o = np.empty(nq)
         chi0_static(self.h, qarr, nq, o.ctypes.data)
         return o
+
+    def static_pairs(self, qarr=None):
+        """Static chi0 and its band-pair contributions: (chi[nq], [w_q x w_q array per q])."""
+        qarr = self.qarr if qarr is None else qarr
+        nq = len(qarr)
+        ws = []
+        for i in range(nq):
+            lo, hi = (qarr[i].win.lo, qarr[i].win.hi) if qarr[i].win.lo >= 0 else self.window
+            ws.append(hi - lo)
+        npairs = sum(w * w for w in ws)
+        if self.device:
+            t = self.torch
+            o = t.empty(nq, dtype=t.float64, device="cuda")
+            pr = t.empty(npairs, dtype=t.float64, device="cuda")
+            chi0_static_pairs(self.h, qarr, nq, o.data_ptr(), pr.data_ptr())
+            o, pr = o.cpu().numpy(), pr.cpu().numpy()
+        else:
+            o = np.empty(nq)
+            pr = np.empty(npairs)
+            chi0_static_pairs(self.h, qarr, nq, o.ctypes.data, pr.ctypes.data)
+        blocks, off = [], 0
+        for w in ws:
+            blocks.append(pr[off:off + w * w].reshape(w, w))
+            off += w * w
+        return o, blocks
 
     def dynamic(self, omega, qarr=None, out=None):
         qarr = self.qarr if qarr is None else qarr

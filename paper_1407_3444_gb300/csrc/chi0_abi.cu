@@ -54,6 +54,10 @@ struct chi0_plan {
   void *fb_d = nullptr;                       // dynamic weights: per-warp fallback entries,
   unsigned long long *fx_d = nullptr;         // per-CTA fixed-point sums (FP32) and the
   unsigned long long *ctr_d = nullptr;        // batch counter
+  unsigned long long *pairs_fx_d = nullptr;   // band-pair output: fixed-point totals of one q,
+  size_t pairs_fx_cap = 0;                    // and the FP64 results of the call (host outputs)
+  double *pairs_out_d = nullptr;
+  size_t pairs_out_cap = 0;
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
   int static_grid = 0, dynamic_grid = 0;  // persistent CTAs of the weight kernels
@@ -110,7 +114,7 @@ extern "C" void chi0_opts_default(chi0_opts_t *o) {
   o->wait_budget = 0;
 }
 
-extern "C" int chi0_version(void) { return 101; }
+extern "C" int chi0_version(void) { return 102; }
 
 extern "C" const char *chi0_last_error(const chi0_plan_t *p) { return p ? p->err : g_plan_err; }
 
@@ -154,6 +158,8 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->fb_d);
   cudaFree(p->fx_d);
   cudaFree(p->ctr_d);
+  cudaFree(p->pairs_fx_d);
+  cudaFree(p->pairs_out_d);
 }
 
 extern "C" void chi0_destroy(chi0_plan_t *p) {
@@ -436,16 +442,20 @@ int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q) {
 // Every launch and device-side copy of one call, in stream order (the part a CUDA graph
 // captures): counters, then per q the overlap, DOS, band bounds, weights and reductions.
 static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *om_d, int nw, bool dyn,
-                        double *outR, double *outI, Timer &tm, bool tc) {
+                        double *outR, double *outI, Timer &tm, bool tc, double *outP = nullptr) {
   const chi0_opts_t &op = p->opts;
   const int fp64 = op.precision == CHI0_PREC_FP64;
   const double scale = op.sign == CHI0_SIGN_PAPER ? -2.0 : 2.0;
   cudaStream_t s = p->stream;
   CK(p, cudaMemsetAsync(p->counters_d, 0, sizeof(unsigned long long) * 4, s));
+  size_t poff = 0;  // band-pair output: offset of this q's w x w block
   for (int iq = 0; iq < nq; ++iq) {
     Q q;
     int rc = prepare_q(p, qs[iq], q);
     if (rc) return rc;
+    const int wq = q.hi - q.lo;
+    unsigned long long *pfx = outP ? p->pairs_fx_d : nullptr;
+    if (pfx) CK(p, cudaMemsetAsync(pfx, 0, sizeof(unsigned long long) * wq * wq, s));
     if (!op.cma) {
       tm.start(CHI0_K_OVERLAP);
       if (tc)
@@ -460,7 +470,7 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
     const int ndos = static_blocks();
     if (q.gamma) {
       tm.start(CHI0_K_DOS);
-      CK(p, launch_dos(p->g, p->tet, p->E_d, q.lo, q.hi, p->dos_d, ndos, s));
+      CK(p, launch_dos(p->g, p->tet, p->E_d, q.lo, q.hi, p->dos_d, ndos, s, pfx));
       p->stats.kernels += 1;
       tm.stop();
     }
@@ -481,7 +491,7 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
       if (!fp64) Ekqlo = p->Eq32_d + ncb;
     }
     if (!dyn) {
-      StaticBufs sb{p->tq_d, p->tq_n_d, p->partR, p->next_d, static_tab_cap()};
+      StaticBufs sb{p->tq_d, p->tq_n_d, p->partR, p->next_d, static_tab_cap(), pfx};
       tm.start(CHI0_K_STATIC);
       CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq, sb,
                           p->static_grid, p->counters_d, s, p->static_variant));
@@ -490,6 +500,11 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
       tm.start(CHI0_K_REDUCE);
       CK(p, launch_reduce(p->partR, 2 * nb, 1, scale, q.gamma ? p->dos_d : nullptr, ndos, nullptr, outR + iq, s));
       p->stats.kernels += 1;
+      if (pfx) {
+        CK(p, launch_pairs_out(pfx, wq * wq, scale, outP + poff, s));
+        p->stats.kernels += 1;
+        poff += (size_t)wq * wq;
+      }
       tm.stop();
     } else {
       const int maxw = dynamic_max_nw();
@@ -544,7 +559,7 @@ static void drop_graph(chi0_plan_t *p) {
 }
 
 static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, int nw, double *re,
-               double *im) {
+               double *im, double *pairs = nullptr) {
   if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
   if (nq <= 0 || !qs) return fail(p, CHI0_EINVAL, "nq = %d or q NULL", nq);
   const bool dyn = omega != nullptr;
@@ -582,7 +597,26 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     }
   }
   const bool tc = op.overlap != CHI0_OVL_FP32 && !op.cma && !fp64;
-  if (op.graph) {
+  // band-pair output: fixed-point scratch for the widest window, and room for every q's block
+  double *outP = nullptr;
+  size_t npairs = 0;
+  if (pairs) {
+    const int wp = p->win.hi - p->win.lo;
+    int rc = ensure(p, (void **)&p->pairs_fx_d, &p->pairs_fx_cap, sizeof(unsigned long long) * wp * wp);
+    if (rc) return rc;
+    for (int iq = 0; iq < nq; ++iq) {
+      const int lo = qs[iq].win.lo < 0 ? p->win.lo : qs[iq].win.lo, hi = qs[iq].win.lo < 0 ? p->win.hi : qs[iq].win.hi;
+      npairs += (size_t)(hi - lo) * (hi - lo);
+    }
+    if (op.outputs_on_device) {
+      outP = pairs;
+    } else {
+      rc = ensure(p, (void **)&p->pairs_out_d, &p->pairs_out_cap, sizeof(double) * npairs);
+      if (rc) return rc;
+      outP = p->pairs_out_d;
+    }
+  }
+  if (op.graph && !pairs) {
     // replay the captured sequence when the call matches the one captured, else capture anew
     std::vector<unsigned char> key = call_key(qs, nq, om_d, nw, dyn, outR, outI);
     if (!p->gexec || key != p->gkey) {
@@ -627,7 +661,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     tm.stop();
     p->stats.kernels += p->gkernels;
   } else {
-    const int rc = enqueue_call(p, qs, nq, om_d, nw, dyn, outR, outI, tm, tc);
+    const int rc = enqueue_call(p, qs, nq, om_d, nw, dyn, outR, outI, tm, tc, outP);
     if (rc) return rc;
   }
   if (tc) {  // the tensor-core overlap's bounded waits report through the error word
@@ -643,6 +677,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
   if (!op.outputs_on_device) {
     CK(p, cudaMemcpyAsync(re, outR, sizeof(double) * nq * nwo, cudaMemcpyDeviceToHost, s));
     if (dyn) CK(p, cudaMemcpyAsync(im, outI, sizeof(double) * nq * nw, cudaMemcpyDeviceToHost, s));
+    if (pairs) CK(p, cudaMemcpyAsync(pairs, outP, sizeof(double) * npairs, cudaMemcpyDeviceToHost, s));
   }
   if (op.profile || !op.outputs_on_device) CK(p, cudaStreamSynchronize(s));
   CK(p, cudaGetLastError());
@@ -661,6 +696,12 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
 
 extern "C" int chi0_static(chi0_plan_t *p, const chi0_q_t *q, int nq, double *chi) {
   return run(p, q, nq, nullptr, 0, chi, nullptr);
+}
+
+extern "C" int chi0_static_pairs(chi0_plan_t *p, const chi0_q_t *q, int nq, double *chi, double *pairs) {
+  if (!pairs) return fail(p, CHI0_EINVAL, "pairs is NULL");
+  if (p && p->win.hi - p->win.lo > 1024) return fail(p, CHI0_EINVAL, "band-pair output: window wider than 1024");
+  return run(p, q, nq, nullptr, 0, chi, nullptr, pairs);
 }
 
 extern "C" int chi0_dynamic(chi0_plan_t *p, const chi0_q_t *q, int nq, const double *omega, int nw, double *re,

@@ -76,6 +76,7 @@ struct StaticBufs {
   double *partial; // [2 * nbatch]: series part, queued part
   int *next;       // batch counter
   int tcap;        // queue entries per batch (at most static_tab_cap())
+  unsigned long long *pairs = nullptr;  // band-pair output: [w][w] fixed-point totals (or none)
 };
 
 // static weights for one q: partial[2 * nbatch] (sum them for chi0); Ek/Ekq are the absolute
@@ -123,7 +124,9 @@ cudaError_t dynamic_prepare();  // kernel attributes (shared memory); call outsi
 
 // Gamma: intraband q -> 0 limit, tetrahedron DOS at eF: partial[nblocks]
 cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,
-                       int nblocks, cudaStream_t s);
+                       int nblocks, cudaStream_t s, unsigned long long *pairs = nullptr);
+// band-pair output: out[i] = scale * pairs[i] in FP64 (pairs: fixed-point totals of the static kernels)
+cudaError_t launch_pairs_out(const unsigned long long *pairs, int n, double scale, double *out, cudaStream_t s);
 
 // out[k] = scale * (sum_b partial[b*nw + k] (+ sum dos where omega == 0) (+ extra[k]))
 cudaError_t launch_reduce(const double *partial, int nblocks, int nw, double scale, const double *dos,

@@ -31,8 +31,14 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kSMs = 152;
-constexpr int kStaticBlocks = kSMs * 8;
+constexpr int kSMs = 152;                 // default when the device cannot be queried
+constexpr int kStaticBlocks = kSMs * 8;   // fixed grid of the DOS kernel (its partials)
+// band-pair output: 64-bit fixed point in units of 2^-50 (|pair totals| < 2^13; one rounding
+// of 2^-51 per term)
+constexpr double kPairScale = 1125899906842624.0;  // 2^50
+__device__ __forceinline__ void pair_add(unsigned long long *pairs, int idx, double v) {
+  atomicAdd(&pairs[idx], (unsigned long long)__double2ll_rn(v * kPairScale));
+}
 using grid::kFull;
 using grid::div_small;
 using grid::tet_corners;
@@ -172,7 +178,7 @@ constexpr int kTabCap = 64;  // queued final tetrahedra per batch (plans; Static
 
 template <typename T> struct Piece {
   T d[4], f[4], w;
-  int i64;  // 1: evaluate in FP64 (near-degenerate knots), -1: FP32
+  int code;  // bit 0: evaluate in FP64 (near-degenerate knots); bits 1..: band pair (m - lo) w + (n - lo)
 };
 
 // compensated (Neumaier) accumulator in the kernel's precision
@@ -265,11 +271,13 @@ __global__ void __launch_bounds__(NT, MINB)
     const int total = __shfl_sync(kFull, pre, 31);
     __syncwarp();
     // final tetrahedron -> series on the spot, or the batch's queue region
-    auto emit = [&](T r, T d[4], T ff[4], T vol2) {
+    auto emit = [&](T r, T d[4], T ff[4], T vol2, int pidx) {
       sort4(d, ff);
       ++npieces;
       if (series_ok(d, T(Num<T>::kappa))) {
-        acc.add(vol2 * r * series_sum(d, ff));
+        const T v = vol2 * r * series_sum(d, ff);
+        acc.add(v);
+        if (sb.pairs) pair_add(sb.pairs, pidx, (double)v);
         return;
       }
       Piece<T> pc;
@@ -283,14 +291,16 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
       for (int i = 0; i < 4; ++i) pc.f[i] = ff[i];
       pc.w = vol2 * r;
-      pc.i64 = fp ? 1 : -1;
+      pc.code = (pidx << 1) | fp;
       const int slot = atomicAdd(&s_qn[wib], 1);
       if (slot < sb.tcap) {
         nfp64 += fp;
         tq[(long long)batch * sb.tcap + slot] = pc;
       } else {
         ++nover;
-        acc_q += piece_eval<FP64>(pc, tau, nfp64);
+        const double v = piece_eval<FP64>(pc, tau, nfp64);
+        acc_q += v;
+        if (sb.pairs) pair_add(sb.pairs, pidx, v);
       }
     };
     // corner data of item (tetrahedron l of the batch, bands m, n)
@@ -340,7 +350,8 @@ __global__ void __launch_bounds__(NT, MINB)
           load(l, m, n, a, b);
           load_f(l, m, n, f);
           const T vol2 = s_vol[wib][l];
-          carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) { emit(r, d, ff, vol2); });
+          const int pidx = (m - q.lo) * w + (n - q.lo);
+          carve2<T>(a, b, f, [&](T r, T d[4], T ff[4]) { emit(r, d, ff, vol2, pidx); });
         }
       }
     };
@@ -429,20 +440,24 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
     unsigned any64 = 0u;
     for (int slot = lane; slot < n; slot += 32) {
       const Piece<T> pc = tq[b * sb.tcap + slot];
+      double v = 0.0;
       if constexpr (FP64) {
-        acc += pc.w * inv_sum_fast(pc.d, pc.f);
-      } else if (pc.i64 >= 0) {
+        v = pc.w * inv_sum_fast(pc.d, pc.f);
+      } else if (pc.code & 1) {
         any64 = 1u;  // near-degenerate knots: the FP64 table, below
+        continue;
       } else {
-        acc += (double)(pc.w * inv_sum_long(pc.d, pc.f));
+        v = (double)(pc.w * inv_sum_long(pc.d, pc.f));
       }
+      acc += v;
+      if (sb.pairs) pair_add(sb.pairs, pc.code >> 1, v);
     }
     if constexpr (!FP64) {
       // FP64 entries (rare): four lanes, one vertex j each, to cut the FP64 latency
       if (__any_sync(kFull, any64)) {
         for (int slot = 0; slot < n; ++slot) {
           const Piece<T> pc = tq[b * sb.tcap + slot];
-          if (pc.i64 < 0) continue;
+          if (!(pc.code & 1)) continue;
           double t = 0.0;
           if (lane < 4) {
             double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
@@ -450,7 +465,10 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
           }
           t += __shfl_xor_sync(kFull, t, 1);
           t += __shfl_xor_sync(kFull, t, 2);
-          if (lane == 0) acc += (double)pc.w * t;
+          if (lane == 0) {
+            acc += (double)pc.w * t;
+            if (sb.pairs) pair_add(sb.pairs, pc.code >> 1, (double)pc.w * t);
+          }
         }
       }
     }
@@ -461,7 +479,8 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
 
 // ---------------------------------------------------------------- Gamma DOS term
 __global__ void __launch_bounds__(kThreads) k_dos(Grid g, Tet tet, const double *__restrict__ E, int lo,
-                                                   int hi, double *__restrict__ partial) {
+                                                   int hi, double *__restrict__ partial,
+                                                   unsigned long long *__restrict__ pairs) {
   const int w = hi - lo;
   const long long total = g.ntet * (long long)w;
   Q q0{};
@@ -474,10 +493,19 @@ __global__ void __launch_bounds__(kThreads) k_dos(Grid g, Tet tet, const double 
     long long c[4], cq[4];
     double vol;
     tet_corners(g, tet, q0, t, c, cq, vol);
-    acc += vol * dos4(E[c[0] * g.nb + band] - g.ef, E[c[1] * g.nb + band] - g.ef,
-                      E[c[2] * g.nb + band] - g.ef, E[c[3] * g.nb + band] - g.ef);
+    const double v = vol * dos4(E[c[0] * g.nb + band] - g.ef, E[c[1] * g.nb + band] - g.ef,
+                                E[c[2] * g.nb + band] - g.ef, E[c[3] * g.nb + band] - g.ef);
+    acc += v;
+    if (pairs && v != 0.0) pair_add(pairs, (band - lo) * (w + 1), v);  // the intraband pair (m, m)
   }
   block_sum_store(acc, &partial[blockIdx.x]);
+}
+
+// band-pair output: fixed-point totals to FP64, times the normalisation and sign
+__global__ void __launch_bounds__(kThreads) k_pairs_out(const unsigned long long *__restrict__ pairs, int n,
+                                                         double scale, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = scale * ((double)(long long)pairs[i] / kPairScale);
 }
 
 // ---------------------------------------------------------------- reduction
@@ -526,7 +554,7 @@ __global__ void __launch_bounds__(kThreads) k_c128_to_c64(const double2 *__restr
 }
 
 cudaError_t launch_c128_to_c64(const void *in, void *out, long long n, cudaStream_t s) {
-  k_c128_to_c64<<<kSMs * 8, kThreads, 0, s>>>((const double2 *)in, (float2 *)out, n);
+  k_c128_to_c64<<<device_sms() * 8, kThreads, 0, s>>>((const double2 *)in, (float2 *)out, n);
   return cudaGetLastError();
 }
 
@@ -535,14 +563,14 @@ cudaError_t launch_overlap(const Grid &g, const double *, const void *C, int dty
   const int w = q.hi - q.lo;
   const long long total = g.nc * (long long)w * w;
   long long nb = (total + kThreads - 1) / kThreads;
-  const int blocks = (int)(nb < kSMs * 16 ? nb : kSMs * 16);
+  const int blocks = (int)(nb < device_sms() * 16 ? nb : device_sms() * 16);
   if (blocks <= 0) return cudaSuccess;
   const bool small = (long long)g.norb * w <= kOvlSmall && !fp64;
   if (small) {
     // k side in complex64 (the plan's copy when the inputs are complex128)
     const float2 *Ck = (const float2 *)(C32 ? C32 : C);
     long long nbw = (g.nc + kWarps - 1) / kWarps;
-    const int bw = (int)(nbw < kSMs * 8 ? nbw : kSMs * 8);
+    const int bw = (int)(nbw < device_sms() * 8 ? nbw : device_sms() * 8);
     if (q.Cq && dtype == DT_C128)
       k_overlap_small<float2, double2, float><<<bw, kThreads, 0, s>>>(g, Ck, (const double2 *)q.Cq, 1, q,
                                                                       (float *)W2);
@@ -568,7 +596,7 @@ cudaError_t launch_overlap(const Grid &g, const double *, const void *C, int dty
 cudaError_t launch_bands(const double *E, long long nc, int nb, double ef, short *occ, short *emp, float *E32,
                          cudaStream_t s, float *E32lo) {
   long long nb_ = (nc + kThreads - 1) / kThreads;
-  const int blocks = (int)(nb_ < kSMs * 8 ? nb_ : kSMs * 8);
+  const int blocks = (int)(nb_ < device_sms() * 8 ? nb_ : device_sms() * 8);
   k_bands<<<blocks, kThreads, 0, s>>>(E, nc, nb, ef, occ, emp, E32, E32lo);
   return cudaGetLastError();
 }
@@ -615,15 +643,20 @@ cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const v
     k_static<false, 256, 2><<<nblocks, 256, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, sb, counters);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   long long tb = (nbatch * 32 + kThreads - 1) / kThreads;
-  const int tblocks = (int)(tb < kSMs * 16 ? tb : kSMs * 16);
+  const int tblocks = (int)(tb < device_sms() * 16 ? tb : device_sms() * 16);
   if (fp64) k_static_tab<true><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
   else k_static_tab<false><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dos(const Grid &g, const Tet &tet, const double *E, int lo, int hi, double *partial,
-                       int nblocks, cudaStream_t s) {
-  k_dos<<<nblocks, kThreads, 0, s>>>(g, tet, E, lo, hi, partial);
+                       int nblocks, cudaStream_t s, unsigned long long *pairs) {
+  k_dos<<<nblocks, kThreads, 0, s>>>(g, tet, E, lo, hi, partial, pairs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_out(const unsigned long long *pairs, int n, double scale, double *out, cudaStream_t s) {
+  k_pairs_out<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(pairs, n, scale, out);
   return cudaGetLastError();
 }
 

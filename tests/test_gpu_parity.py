@@ -100,6 +100,35 @@ def test_static_per_q_windows(C, O, prec):
     assert nerr(got[:, None], ref[:, None]) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_static_band_pairs(C, O, prec):
+    """Band-pair resolved static chi0 (chi0_static_pairs) against the oracle's pair sums: a
+    general on-grid q, Gamma (the intraband pairs carry their band's DOS) and per-q windows of
+    different widths (blocks back to back); each pair within the form's
+    tolerance of the largest pair of its q, and the pairs of a q add up to its chi0."""
+    W = wl.tiny_tb(n=8, norb=6, nq=0, seed=wl.SEED_BASE + 45)
+    qs = [wl.QPoint(shift=(1, 3, 2)), wl.QPoint(shift=(0, 0, 0), gamma=True),
+          wl.QPoint(shift=(2, 0, 5), window=(1, 5)), wl.QPoint(shift=(4, 4, 4), window=(2, 4))]
+    W.qs = qs
+    P = C.Plan(W, precision=prec, device=True)
+    chi, blocks = P.static_pairs()
+    P.close()
+    tot_ref = O.chi0(W)
+    assert nerr(chi[:, None], tot_ref[:, None]) < TOL[prec]
+    for iq, q in enumerate(qs):
+        ref = O.chi0_pairs_q(W, q)
+        got = blocks[iq]
+        assert got.shape == ref.shape
+        assert np.max(np.abs(got - ref)) <= TOL[prec] * np.max(np.abs(ref)), (iq, got, ref)
+        assert abs(got.sum() - chi[iq]) <= 1e-12 * abs(chi[iq]) + 1e-14, (iq, got.sum(), chi[iq])
+    # host outputs give the same numbers, bitwise (fixed-point sums)
+    Ph = C.Plan(W, precision=prec, device=False)
+    chi_h, blocks_h = Ph.static_pairs()
+    Ph.close()
+    for a, b in zip(blocks, blocks_h):
+        assert np.array_equal(a, b)
+
+
 def test_static_host_inputs_and_c64(C, O):
     W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 43, cdtype=np.complex64)
     ref = O.chi0(W)  # the oracle promotes the same complex64 values

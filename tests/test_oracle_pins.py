@@ -527,3 +527,54 @@ def test_chi_periodic_in_q(oracle_mod):
         a = oracle_mod.chi0_q(W, q0)
         b = oracle_mod.chi0_q(W, qG)
         assert abs(a - b) < 1e-10 * abs(a), (cma, a, b)
+
+
+def test_pairs_flat_bands_closed_form(oracle_mod):
+    """Band-pair resolved static chi0 (Sec. III, Fig. 8) on three flat bands -1, +1, +2 (eF = 0)
+    with eigenvectors U at k and V at k+q: only the pairs (0, 1) and (0, 2) carry weight,
+    2 f01 2/2 and 2 f02 2/3 with f = |U^H V|^2 (M_mn = <m,k|n,k+q>, Eq. 1); the transposed
+    entries (1, 0), (2, 0) are 0 (band 1 and 2 are empty at k), which a transposed operand or
+    a swapped m/n in the accumulation index would break."""
+    rng = np.random.default_rng(22)
+    n = 3
+    Nc = n ** 3
+
+    def unitary():
+        Z = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        Q, _ = np.linalg.qr(Z)
+        return Q
+
+    U, V = unitary(), unitary()
+    E = np.tile([-1.0, 1.0, 2.0], (Nc, 1))
+    W = wl.Workload("flat", (n, n, n), True, 3, 3, E, np.tile(U, (Nc, 1, 1)), 0.0, (0, 3), False,
+                    [wl.QPoint(Eq=E.copy(), Cq=np.tile(V, (Nc, 1, 1)))])
+    f = np.abs(U.conj().T @ V) ** 2
+    P = oracle_mod.chi0_pairs_q(W, W.qs[0])
+    ref = np.zeros((3, 3))
+    ref[0, 1] = 2.0 * f[0, 1] * 2 / 2
+    ref[0, 2] = 2.0 * f[0, 2] * 2 / 3
+    assert np.allclose(P, ref, rtol=1e-13, atol=1e-15)
+    assert abs(oracle_mod.chi0_pairs_q(W, W.qs[0], sign=1)[0, 2] + ref[0, 2]) < 1e-14
+
+
+def test_pairs_add_up_to_chi0(oracle_mod):
+    """The band-pair contributions of a q add up to its static chi0, at a general q and at
+    Gamma (where the intraband pairs carry the density of states of their band, Sec. III)."""
+    m = wl.random_model(4, wl.SEED_BASE + 41, spread=4.0)
+    n = 4
+    E, C = m.eig_grid((n, n, n))
+    ef = wl.fermi_level(E, 2.0)
+    qs = [wl.QPoint(shift=(1, 2, 0), frac=(0.25, 0.5, 0.0)),
+          wl.QPoint(shift=(0, 0, 0), gamma=True, frac=(0.0, 0.0, 0.0))]
+    W = wl.Workload("tiny", (n, n, n), True, 4, 4, E, C, ef, (0, 4), False, qs)
+    for q in qs:
+        P = oracle_mod.chi0_pairs_q(W, q)
+        tot = oracle_mod.chi0_q(W, q)
+        assert P.shape == (4, 4)
+        assert abs(P.sum() - tot) <= 1e-12 * abs(tot), (P.sum(), tot)
+    # at Gamma every diagonal entry is the DOS of its band (intraband transitions have no
+    # region of their own there), which equals the oracle's DOS of that band alone
+    Pg = oracle_mod.chi0_pairs_q(W, qs[1])
+    for b in range(4):
+        dos_b = oracle_mod.chi0_q(W, qs[1], window=(b, b + 1))
+        assert abs(Pg[b, b] - dos_b) <= 1e-12 * max(1.0, abs(dos_b)), (b, Pg[b, b], dos_b)
