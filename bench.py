@@ -72,6 +72,9 @@ def parse():
                     help="large: the step on a seeded sample of TETS of the mesh's tetrahedra (the full mesh's mix "
                          "of final tetrahedra at a fraction of its size, for profiler counters); nominal evals "
                          "scale by TETS / ntet")
+    ap.add_argument("--no-kk", action="store_true",
+                    help="dynamic workloads: skip the Kramers-Kronig route's timing (Im alone on a grid over the "
+                         "whole spectrum, Re by the transform), reported beside the direct principal value")
     ap.add_argument("--profile-out", default="")
     return ap.parse_args()
 
@@ -461,6 +464,37 @@ def run_ours(args):
                                                                     else chi0.CHI0_K_STATIC]))
         Pd.close()
 
+    # the Kramers-Kronig route (Im alone on a uniform grid of the step's spacing that covers the
+    # spectrum, Re by the transform), timed after the step's timed region, against the direct form
+    kk = None
+    if W.omega is not None and not args.no_kk and len(W.omega) > 1:
+        du = float(W.omega[1] - W.omega[0])
+        uniform = np.allclose(np.diff(W.omega), du, rtol=1e-9, atol=0) and W.omega[0] == 0.0
+        if uniform:
+            lo_w, hi_w = W.window
+            span = float(W.E[:, hi_w - 1].max() - W.E[:, lo_w].min())
+            nkk = int(np.ceil(span / du)) + 2
+            wmax = (nkk - 1) * du
+            Pm.dynamic_kk(wmax, nkk)
+            torch.cuda.synchronize()
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            rk, ik = Pm.dynamic_kk(wmax, nkk)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            kms = k0.elapsed_time(k1) / len(W.qs)
+            nwo = len(W.omega)
+            rk = rk.cpu().numpy()[:, :nwo]
+            ik = ik.cpu().numpy()[:, :nwo]
+            mre, mim = mixed
+            kk = {"ms_per_q": kms, "direct_ms_per_q": ms / len(W.qs), "nkk": nkk, "wmax": wmax,
+                  "passes": -(-nkk // chi0.DYNAMIC_MAX_NW),
+                  "speedup_vs_direct": (ms / len(W.qs)) / kms,
+                  "re_vs_direct": rel_err(rk, mre), "im_vs_direct": rel_err(ik, mim),
+                  "note": "Im on u_j = j dw up to the largest band-pair energy of the window (the step's "
+                          "spacing), Re by the transform of the piecewise-linear Im; the step's q"}
+
     # the GPU forms on the oracle's tetrahedron sample (large run): same q, same frequencies
     gpu_on_sample = None
     if tets is not None and cpu is not None:
@@ -477,20 +511,25 @@ def run_ours(args):
     e2e = None
     if args.e2e_steps > 0:
         host = chi0.HostInputs(W, pinned=True)
-        t_e2e = []
+        t_e2e, t_parts = [], []
         for s in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             Ph = chi0.Plan(W, precision="mixed", device=False, staged=host, overlap=ovl, tetra=sub)
+            ta = time.perf_counter()
             out_h = run_step(Ph, W)
+            tb = time.perf_counter()
             Ph.close()
             t1 = time.perf_counter()
             if s > 0:
                 t_e2e.append(t1 - t0)
+                t_parts.append((ta - t0, tb - ta, t1 - tb))
         T = sum(t_e2e) / len(t_e2e)
+        parts = [sum(x[i] for x in t_parts) / len(t_parts) * 1e3 for i in range(3)]
         e2e = {"value": nominal / T, "unit": "evals/s", "h2d_bytes_per_step": host.nbytes(),
                "d2h_bytes_per_step": int(sum(o.nbytes for o in out_h) if isinstance(out_h, tuple) else out_h.nbytes),
-               "ms_per_step": T * 1e3, "rel_diff_vs_device": rel_err(out_h, mixed)}
+               "ms_per_step": T * 1e3, "rel_diff_vs_device": rel_err(out_h, mixed),
+               "ms_plan_call_destroy": parts}
         del host
 
     peaks, kind = measured_peaks()
@@ -581,7 +620,7 @@ def run_ours(args):
                               "mixed_speedup": ms64 / ms} if ms64 else None),
                 "error": {"mixed_vs_fp64_gpu_max_rel": err_mixed, "vs_oracle": err_oracle},
                 "roofline": roof, "roofline_fp64": roof64, "roofline_overlap": ovl_roof,
-                "stage_ms_per_q": stages, "peaks_run": peaks_run,
+                "stage_ms_per_q": stages, "peaks_run": peaks_run, "kk_route": kk,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "tuned": tuned,
                 "nonzero": {"value": nonzero_rate, "unit": "(final tetrahedron, w) evaluations/s"},
                 "counters_per_step": counters_step, "counters": counters, "clocks": ck, "peaks_source": kind}

@@ -241,6 +241,22 @@ int chi0_static_pairs(chi0_plan_t *plan, const chi0_q_t *q, int nq, double *chi,
 int chi0_dynamic(chi0_plan_t *plan, const chi0_q_t *q, int nq, const double *omega, int nw,
                  double *re, double *im);
 
+/* Dynamic chi0 by the Kramers-Kronig route (Sec. II: Re obtained from Im, the usual way;
+ * Eq. 1's principal value is what chi0_dynamic evaluates instead).  On the uniform grid
+ * u_j = j wmax / (nkk - 1), j < nkk:
+ *   im[iq*nkk + j]: Im chi0 (Eq. 2, the delta term alone: no logarithms, no principal value),
+ *   re[iq*nkk + j]: (1/pi) PV int_0^wmax Im(u) [1/(u - u_j) + 1/(u + u_j)] du with Im taken
+ *                   piecewise linear between the nodes and 0 from wmax on (exact for that
+ *                   interpolant; at a Gamma q the intraband limit N(eF) is added at u = 0 as
+ *                   chi0_dynamic adds it at w = 0).
+ * The grid must cover the support of Im (wmax above the largest e_n(k+q) - e_m(k) of the
+ * window): Sec. IV notes that the transform fails when it does not.  The error of Re against
+ * the principal value falls with the grid spacing (second order where Im is smooth on the
+ * grid's scale).  Im takes ceil(nkk / 256) passes of the weight kernel.  Errors as
+ * chi0_dynamic, plus CHI0_EINVAL for wmax <= 0 or nkk < 2; the call does not use graph
+ * capture.  re, im: host or device like chi0_dynamic's outputs. */
+int chi0_dynamic_kk(chi0_plan_t *plan, const chi0_q_t *q, int nq, double wmax, int nkk, double *re, double *im);
+
 /* Autotuner.  Times the call (static when omega == NULL, else dynamic on nw frequencies)
  * once per candidate launch shape, with CUDA events on the plan's stream, and keeps the
  * fastest shape in the plan for its later calls.  Candidates, tuned one after the other:
@@ -321,7 +337,7 @@ void chi0_destroy(chi0_plan_t *plan);
 const char *chi0_last_error(const chi0_plan_t *plan);
 
 /* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow
- * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs. */
+ * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs; 103 adds chi0_dynamic_kk. */
 int chi0_version(void);
 
 #ifdef __cplusplus

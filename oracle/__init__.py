@@ -7,6 +7,7 @@ library never loads it and shares no code with it.
 from __future__ import annotations
 
 import ctypes as ct
+import math
 import os
 import subprocess
 import threading
@@ -201,6 +202,35 @@ def chi0_pairs_q(W, q, sign: int = 0, nthreads: int = 0, tet=None, tvol=None, wi
     if rc != 0:
         raise RuntimeError("oracle_chi0_pairs failed: %d" % rc)
     return out.reshape(w, w)
+
+
+def kk_re_from_im(u, im, w):
+    """Re(w) = (1/pi) PV int_0^inf Im(u) [1/(u - w) + 1/(u + w)] du for Im given on the
+    ascending nodes u (u[0] = 0, Im(u[0]) = 0), linear between them and 0 past the last node
+    (taken to fall to 0 over one more spacing of the last interval).  Segment by segment: on
+    [a, b] with Im = alpha + beta u,  int (alpha + beta u)/(u - c) du
+    = beta (b - a) + (alpha + beta c) ln|(b - c)/(a - c)|  (principal value if c in (a, b);
+    the logarithms of adjacent segments at a node c = a or b cancel and are dropped)."""
+    u = np.asarray(u, dtype=np.float64)
+    im = np.asarray(im, dtype=np.float64)
+    uu = np.append(u, u[-1] + (u[-1] - u[-2]))
+    yy = np.append(im, 0.0)
+    out = np.zeros(len(w))
+    for i, wv in enumerate(np.asarray(w, dtype=np.float64)):
+        tot = 0.0
+        for c in (wv, -wv):
+            for j in range(len(uu) - 1):
+                a, b = uu[j], uu[j + 1]
+                ya, yb = yy[j], yy[j + 1]
+                beta = (yb - ya) / (b - a)
+                alpha = ya - beta * a
+                lb = math.log(abs(b - c)) if b != c else 0.0
+                la = math.log(abs(a - c)) if a != c else 0.0
+                # at a node the singular parts of the two segments cancel: drop log|0|, keep
+                # the finite remainder (the value there times the log of the other end)
+                tot += beta * (b - a) + (alpha + beta * c) * (lb - la)
+        out[i] = tot / math.pi
+    return out
 
 
 def chi0(W, omega=None, sign: int = 0, nthreads: int = 0, qs=None):

@@ -93,7 +93,7 @@ _lib = None
 # every entry point declared in include/chi0.h (checked by the ABI test)
 EXPORTS = ["chi0_opts_default", "chi0_plan", "chi0_static", "chi0_dynamic", "chi0_plan_stats",
            "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune", "chi0_peak",
-           "chi0_static_pairs"]
+           "chi0_static_pairs", "chi0_dynamic_kk"]
 CHI0_PEAK_FP32_FMA, CHI0_PEAK_FP64_FMA, CHI0_PEAK_TF32_MMA, CHI0_PEAK_BF16_MMA = 0, 1, 2, 3
 CHI0_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -114,6 +114,9 @@ def lib():
         L.chi0_static.restype = ct.c_int
         L.chi0_static_pairs.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_void_p]
         L.chi0_static_pairs.restype = ct.c_int
+        L.chi0_dynamic_kk.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_double, ct.c_int,
+                                      ct.c_void_p, ct.c_void_p]
+        L.chi0_dynamic_kk.restype = ct.c_int
         L.chi0_dynamic.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_int,
                                    ct.c_void_p, ct.c_void_p]
         L.chi0_dynamic.restype = ct.c_int
@@ -165,6 +168,10 @@ def chi0_static(plan, q, nq: int, chi_ptr: int) -> None:
 
 def chi0_static_pairs(plan, q, nq: int, chi_ptr: int, pairs_ptr: int) -> None:
     _check(lib().chi0_static_pairs(plan, q, nq, chi_ptr, pairs_ptr), plan)
+
+
+def chi0_dynamic_kk(plan, q, nq: int, wmax: float, nkk: int, re_ptr: int, im_ptr: int) -> None:
+    _check(lib().chi0_dynamic_kk(plan, q, nq, wmax, nkk, re_ptr, im_ptr), plan)
 
 
 def chi0_dynamic(plan, q, nq: int, omega_ptr: int, nw: int, re_ptr: int, im_ptr: int) -> None:
@@ -402,6 +409,21 @@ class Plan:
             blocks.append(pr[off:off + w * w].reshape(w, w))
             off += w * w
         return o, blocks
+
+    def dynamic_kk(self, wmax: float, nkk: int, qarr=None):
+        """Kramers-Kronig route: (re, im) [nq, nkk] on u_j = j wmax / (nkk - 1)."""
+        qarr = self.qarr if qarr is None else qarr
+        nq = len(qarr)
+        if self.device:
+            t = self.torch
+            re = t.empty(nq * nkk, dtype=t.float64, device="cuda")
+            im = t.empty(nq * nkk, dtype=t.float64, device="cuda")
+            chi0_dynamic_kk(self.h, qarr, nq, float(wmax), int(nkk), re.data_ptr(), im.data_ptr())
+            return re.view(nq, nkk), im.view(nq, nkk)
+        re = np.empty((nq, nkk))
+        im = np.empty((nq, nkk))
+        chi0_dynamic_kk(self.h, qarr, nq, float(wmax), int(nkk), re.ctypes.data, im.ctypes.data)
+        return re, im
 
     def dynamic(self, omega, qarr=None, out=None):
         qarr = self.qarr if qarr is None else qarr

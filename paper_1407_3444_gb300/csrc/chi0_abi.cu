@@ -60,6 +60,8 @@ struct chi0_plan {
   size_t pairs_out_cap = 0;
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
+  int *tq_off_d = nullptr;                    // compacted queue: offsets and values
+  double *tq_val_d = nullptr;
   int static_grid = 0, dynamic_grid = 0;  // persistent CTAs of the weight kernels
   int static_variant = 0;                  // block shape of the static weight kernel
   int tc_gcap = 0;                         // corners per tensor-core round (0: most that fit)
@@ -114,7 +116,7 @@ extern "C" void chi0_opts_default(chi0_opts_t *o) {
   o->wait_budget = 0;
 }
 
-extern "C" int chi0_version(void) { return 102; }
+extern "C" int chi0_version(void) { return 103; }
 
 extern "C" const char *chi0_last_error(const chi0_plan_t *p) { return p ? p->err : g_plan_err; }
 
@@ -151,6 +153,8 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->err_d);
   cudaFree(p->tq_d);
   cudaFree(p->tq_n_d);
+  cudaFree(p->tq_off_d);
+  cudaFree(p->tq_val_d);
   cudaFree(p->box_tab_d);
   cudaFree(p->box_part_d);
   cudaFree(p->box_tot_d);
@@ -284,6 +288,8 @@ static int build_plan(chi0_plan_t *p, const chi0_kgrid_t *kg, const chi0_tetra_t
     const int fp64 = op.precision == CHI0_PREC_FP64;
     CK(p, cudaMalloc(&p->tq_d, static_piece_bytes(fp64) * (size_t)nbatch * static_tab_cap()));
     CK(p, cudaMalloc(&p->tq_n_d, sizeof(int) * (size_t)nbatch));
+    CK(p, cudaMalloc(&p->tq_off_d, sizeof(int) * (size_t)(nbatch + 1)));
+    CK(p, cudaMalloc(&p->tq_val_d, sizeof(double) * (size_t)nbatch * static_tab_cap()));
   }
   if (op.precision == CHI0_PREC_MIXED) {
     CK(p, cudaMalloc(&p->E32_d, 2 * sizeof(float) * (size_t)g.nc * g.nb));
@@ -442,7 +448,8 @@ int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q) {
 // Every launch and device-side copy of one call, in stream order (the part a CUDA graph
 // captures): counters, then per q the overlap, DOS, band bounds, weights and reductions.
 static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *om_d, int nw, bool dyn,
-                        double *outR, double *outI, Timer &tm, bool tc, double *outP = nullptr) {
+                        double *outR, double *outI, Timer &tm, bool tc, double *outP = nullptr,
+                        double kk_du = 0.0) {
   const chi0_opts_t &op = p->opts;
   const int fp64 = op.precision == CHI0_PREC_FP64;
   const double scale = op.sign == CHI0_SIGN_PAPER ? -2.0 : 2.0;
@@ -491,11 +498,14 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
       if (!fp64) Ekqlo = p->Eq32_d + ncb;
     }
     if (!dyn) {
-      StaticBufs sb{p->tq_d, p->tq_n_d, p->partR, p->next_d, static_tab_cap(), pfx};
+      // (the compacted queue indexes its pieces in 32 bits)
+      const bool compact = (long long)nb * static_tab_cap() < (1LL << 31);
+      StaticBufs sb{p->tq_d, p->tq_n_d, p->partR, p->next_d, static_tab_cap(), pfx,
+                    compact ? p->tq_off_d : nullptr, compact ? p->tq_val_d : nullptr};
       tm.start(CHI0_K_STATIC);
       CK(p, launch_static(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq, sb,
                           p->static_grid, p->counters_d, s, p->static_variant));
-      p->stats.kernels += 2;
+      p->stats.kernels += compact ? 4 : 2;
       tm.stop();
       tm.start(CHI0_K_REDUCE);
       CK(p, launch_reduce(p->partR, 2 * nb, 1, scale, q.gamma ? p->dos_d : nullptr, ndos, nullptr, outR + iq, s));
@@ -505,6 +515,30 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
         p->stats.kernels += 1;
         poff += (size_t)wq * wq;
       }
+      tm.stop();
+    } else if (kk_du > 0.0) {
+      // Kramers-Kronig route: Im alone on the uniform grid (passes of at most maxw nodes), then
+      // Re from Im over the whole grid
+      const int maxw = dynamic_max_nw();
+      for (int w0 = 0; w0 < nw; w0 += maxw) {
+        const int nwc = nw - w0 < maxw ? nw - w0 : maxw;
+        DynBufs db{p->partR, p->partI, p->box_tab_d, p->box_part_d, p->box_tot_d, p->far_d, p->fb_d, p->fx_d,
+                   p->ctr_d};
+        int rows = nb;
+        tm.start(CHI0_K_DYNAMIC);
+        CK(p, launch_dynamic_im(p->g, p->tet, Ek, Ekq, q, p->W2_d, op.cma, fp64, (float)op.tau, p->occ_d, empq,
+                                om_d + w0, nwc, db, p->dynamic_grid, p->counters_d, s, Eklo, Ekqlo, &rows));
+        p->stats.kernels += fp64 ? 1 : 2;
+        tm.stop();
+        tm.start(CHI0_K_REDUCE);
+        CK(p, launch_reduce(p->partI, rows, nwc, scale, nullptr, 0, nullptr, outI + (size_t)iq * nw + w0, s));
+        p->stats.kernels += 1;
+        tm.stop();
+      }
+      tm.start(CHI0_K_REDUCE);
+      CK(p, launch_kk(outI + (size_t)iq * nw, nw, kk_du, scale, q.gamma ? p->dos_d : nullptr, ndos,
+                      outR + (size_t)iq * nw, s));
+      p->stats.kernels += 1;
       tm.stop();
     } else {
       const int maxw = dynamic_max_nw();
@@ -559,7 +593,7 @@ static void drop_graph(chi0_plan_t *p) {
 }
 
 static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, int nw, double *re,
-               double *im, double *pairs = nullptr) {
+               double *im, double *pairs = nullptr, double kk_du = 0.0) {
   if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
   if (nq <= 0 || !qs) return fail(p, CHI0_EINVAL, "nq = %d or q NULL", nq);
   const bool dyn = omega != nullptr;
@@ -587,7 +621,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     outI = dyn ? p->out_d + (size_t)nq * nw : nullptr;
   }
   if (dyn) {
-    if (op.inputs_on_device) {
+    if (op.inputs_on_device || kk_du > 0.0) {  // (the Kramers-Kronig grid is already on the device)
       om_d = omega;
     } else {
       int rc = ensure(p, (void **)&p->omega_d, &p->omega_cap, sizeof(double) * nw);
@@ -616,7 +650,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
       outP = p->pairs_out_d;
     }
   }
-  if (op.graph && !pairs) {
+  if (op.graph && !pairs && !(kk_du > 0.0)) {
     // replay the captured sequence when the call matches the one captured, else capture anew
     std::vector<unsigned char> key = call_key(qs, nq, om_d, nw, dyn, outR, outI);
     if (!p->gexec || key != p->gkey) {
@@ -661,7 +695,7 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
     tm.stop();
     p->stats.kernels += p->gkernels;
   } else {
-    const int rc = enqueue_call(p, qs, nq, om_d, nw, dyn, outR, outI, tm, tc, outP);
+    const int rc = enqueue_call(p, qs, nq, om_d, nw, dyn, outR, outI, tm, tc, outP, kk_du);
     if (rc) return rc;
   }
   if (tc) {  // the tensor-core overlap's bounded waits report through the error word
@@ -702,6 +736,20 @@ extern "C" int chi0_static_pairs(chi0_plan_t *p, const chi0_q_t *q, int nq, doub
   if (!pairs) return fail(p, CHI0_EINVAL, "pairs is NULL");
   if (p && p->win.hi - p->win.lo > 1024) return fail(p, CHI0_EINVAL, "band-pair output: window wider than 1024");
   return run(p, q, nq, nullptr, 0, chi, nullptr, pairs);
+}
+
+extern "C" int chi0_dynamic_kk(chi0_plan_t *p, const chi0_q_t *q, int nq, double wmax, int nkk, double *re,
+                               double *im) {
+  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
+  if (!(wmax > 0.0) || !(wmax < 1e300) || nkk < 2) return fail(p, CHI0_EINVAL, "wmax = %g, nkk = %d", wmax, nkk);
+  const double du = wmax / (nkk - 1);
+  std::vector<double> grid((size_t)nkk);
+  for (int j = 0; j < nkk; ++j) grid[(size_t)j] = j * du;
+  int rc = ensure(p, (void **)&p->omega_d, &p->omega_cap, sizeof(double) * nkk);
+  if (rc) return rc;
+  CK(p, cudaMemcpyAsync(p->omega_d, grid.data(), sizeof(double) * nkk, cudaMemcpyHostToDevice, p->stream));
+  CK(p, cudaStreamSynchronize(p->stream));  // (the host grid goes out of scope)
+  return run(p, q, nq, p->omega_d, nkk, re, im, nullptr, du);
 }
 
 extern "C" int chi0_dynamic(chi0_plan_t *p, const chi0_q_t *q, int nq, const double *omega, int nw, double *re,

@@ -219,7 +219,9 @@ __device__ __noinline__ void box_moments_fx_ol(const float e[4], const float f[4
                                                int K) {
   float H[4] = {1.f, 1.f, 1.f, 1.f};
   float P[4] = {1.f, 1.f, 1.f, 1.f};
-  atomicAdd(&dst[0], (unsigned long long)__float2ll_rn(v * 0.25f * (f[0] + f[1] + f[2] + f[3]) * kFxScale));
+  // (terms that round to 0 in fixed point are skipped: high moments of small pieces)
+  long long t0 = __float2ll_rn(v * 0.25f * (f[0] + f[1] + f[2] + f[3]) * kFxScale);
+  if (t0) atomicAdd(&dst[0], (unsigned long long)t0);
 #pragma unroll 1
   for (int k = 1; k < K; ++k) {
     H[0] = e[0] * H[0];
@@ -231,7 +233,8 @@ __device__ __noinline__ void box_moments_fx_ol(const float e[4], const float f[4
       P[jj] = H[3] + e[jj] * P[jj];
       sj += f[jj] * P[jj];
     }
-    atomicAdd(&dst[k], (unsigned long long)__float2ll_rn(v * tabs(series_coef<float>(k)) * sj * kFxScale));
+    const long long t = __float2ll_rn(v * tabs(series_coef<float>(k)) * sj * kFxScale);
+    if (t) atomicAdd(&dst[k], (unsigned long long)t);
   }
 }
 
@@ -301,7 +304,9 @@ __device__ __forceinline__ void near_knots(int ent, const T d[4], const T e[4], 
   }
 }
 
-template <bool FP64>
+// IMO: Im only (the delta term of Eq. 2 on an ascending grid of w >= 0; no principal value,
+// no boxes) for the Kramers-Kronig route to Re
+template <bool FP64, bool IMO = false>
 __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
     k_dynamic(Grid g, Tet tet, const void *__restrict__ Ek, const void *__restrict__ Ekq, Q q,
               const void *__restrict__ W2, int cma, float tau, const short *__restrict__ occ,
@@ -357,19 +362,25 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
     if constexpr (!FP64) s_wl[iw] = (float)(omega[iw] - (double)s_w[iw]);
   }
   {
-    const BoxTab<T> *src = (const BoxTab<T> *)db.box_tab;
-    const int nwords = (int)(sizeof(BoxTab<T>) / 4);
+    if constexpr (IMO) {
+      if (threadIdx.x == 0) s_tab.on = 0;  // every piece evaluates its own frequencies
+    } else {
+      const BoxTab<T> *src = (const BoxTab<T> *)db.box_tab;
+      const int nwords = (int)(sizeof(BoxTab<T>) / 4);
 #pragma unroll 1
-    for (int i = threadIdx.x; i < nwords; i += blockDim.x) ((int *)&s_tab)[i] = ((const int *)src)[i];
+      for (int i = threadIdx.x; i < nwords; i += blockDim.x) ((int *)&s_tab)[i] = ((const int *)src)[i];
+    }
   }
   if constexpr (FX) {
+    if constexpr (!IMO) {
 #pragma unroll 1
-    for (int i = threadIdx.x; i < NS; i += blockDim.x) bfx[i] = 0ull;
+      for (int i = threadIdx.x; i < NS; i += blockDim.x) bfx[i] = 0ull;
+    }
 #pragma unroll 1
     for (int i = threadIdx.x; i < 2 * kNWPass; i += blockDim.x) s_fx[i / kNWPass][i % kNWPass] = 0ull;
   } else {
 #pragma unroll 1
-    for (int i = lane; i < NS; i += 32) acc[i] = T(0);
+    for (int i = lane; i < (IMO ? 0 : NS); i += 32) acc[i] = T(0);
   }
   __syncthreads();
   // frequency ranges of the fine boxes: contiguous when |w| ascends along the grid (an
@@ -380,7 +391,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
   for (int i = threadIdx.x; i + 1 < nw; i += blockDim.x) sorted = sorted && tabs(s_w[i]) <= tabs(s_w[i + 1]);
   sorted = __syncthreads_and(sorted) != 0;
 #pragma unroll 1
-  for (int b = threadIdx.x; b < kBoxFine; b += blockDim.x) {
+  for (int b = threadIdx.x; b < (IMO ? 0 : kBoxFine); b += blockDim.x) {
     int lo = 0, hi = nw;
     if (sorted) {
       lo = nw;
@@ -407,12 +418,20 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
   // all of them (b < 0); lanes own frequencies
   // one term of Re / Im at frequency iw
   auto add_re = [&](int iw, T v) {
-    if constexpr (FX) atomicAdd(&s_fx[0][iw], (unsigned long long)__float2ll_rn(v * kFxScale));
-    else kadd_t(sR[wib][iw], cR[wib][iw], v);
+    if constexpr (FX) {
+      const long long t = __float2ll_rn(v * kFxScale);
+      if (t) atomicAdd(&s_fx[0][iw], (unsigned long long)t);
+    } else {
+      kadd_t(sR[wib][iw], cR[wib][iw], v);
+    }
   };
   auto add_im = [&](int iw, T v) {
-    if constexpr (FX) atomicAdd(&s_fx[1][iw], (unsigned long long)__float2ll_rn(v * kFxScale));
-    else kadd_t(sI[wib][iw], cI[wib][iw], v);
+    if constexpr (FX) {
+      const long long t = __float2ll_rn(v * kFxScale);
+      if (t) atomicAdd(&s_fx[1][iw], (unsigned long long)t);
+    } else {
+      kadd_t(sI[wib][iw], cI[wib][iw], v);
+    }
   };
   // one round of per-lane results (iw < 0: nothing).  Fixed point: atomic adds (exact, any
   // order).  FP64: lanes that share a frequency add one at a time in lane order (the lists are
@@ -420,7 +439,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
   auto round_add = [&](int iw, T re, T im) {
     if constexpr (FX) {
       if (iw >= 0) {
-        add_re(iw, re);
+        if (re != T(0)) add_re(iw, re);
         if (im != T(0)) add_im(iw, im);
       }
     } else {
@@ -499,7 +518,14 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
         // (a near entry has the frequency within two half-widths of the piece's midpoint,
         // where the moment series about the knot midpoint does not apply)
         T v;
-        if (inv_sum_shared_ol(x, ff, v)) {
+        if (IMO) {  // the delta term alone
+          if (x[0] < T(0) && x[3] > T(0)) {
+            iw = ent >> 1;
+            const T rs[6] = {rcp(ee[1] - ee[0]), rcp(ee[2] - ee[1]), rcp(ee[3] - ee[2]),
+                             rcp(ee[2] - ee[0]), rcp(ee[3] - ee[1]), rcp(ee[3] - ee[0])};
+            im = vr * delta_sum_pre_ol(x, ff, rs) * T(3.141592653589793);
+          }
+        } else if (inv_sum_shared_ol(x, ff, v)) {
           iw = ent >> 1;
           re = vr * v;
           if ((ent & 1) == 0 && x[0] < T(0) && x[3] > T(0)) {
@@ -534,50 +560,75 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
     nnear = 0;
   };
   auto eval_piece = [&](const T ee[4], const T ff[4], T vr, T D0h, T D0l, const T *am, int K, int b, int slot) {
-    T d[4];
+    if constexpr (IMO) {
+      // the grid frequencies inside the knot range (ascending grid: one index range, widened
+      // by one on each side; the delta term's own test decides each entry)
+      const T lo_d = D0h + ee[0], hi_d = D0h + ee[3];
+      int a = 0, z = nw;  // first index with w > lo_d
+#pragma unroll 1
+      while (a < z) {
+        const int mid = (a + z) >> 1;
+        if (s_w[mid] > lo_d) z = mid;
+        else a = mid + 1;
+      }
+      int c = a, e = nw;  // first index with w >= hi_d
+#pragma unroll 1
+      while (c < e) {
+        const int mid = (c + e) >> 1;
+        if (s_w[mid] >= hi_d) e = mid;
+        else c = mid + 1;
+      }
+      const int lo = a > 0 ? a - 1 : 0, hi = c < nw ? c + 1 : nw;
+#pragma unroll 1
+      for (int iw = lo + lane; iw < hi; iw += 32) s_near[wib][nnear + iw - lo] = (unsigned short)((slot << 9) | (iw * 2));
+      nnear += hi - lo;
+      __syncwarp();
+    } else {
+      T d[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
-    const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
-    const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
-    const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
-    // far field for both terms (Horner on the moments); near-field frequencies are
-    // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
-    unsigned nearm = 0u, nearp = 0u;
+      for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
+      const T c = D0h + (ee[0] + ee[3]) * T(0.5), half = (ee[3] - ee[0]) * T(0.5);
+      const T Cb = b >= 0 ? s_tab.C[b] : T(0), Rb = b >= 0 ? s_tab.R[b] : T(0);
+      const int lo = b >= 0 ? s_rng[b][0] : 0, hi = b >= 0 ? s_rng[b][1] : nw;
+      // far field for both terms (Horner on the moments); near-field frequencies are
+      // recorded per lane (bit it of nearm / nearp) and evaluated below in full warps
+      unsigned nearm = 0u, nearp = 0u;
 #pragma unroll 1
-    for (int iw = lo + lane, itn = 0; iw < hi; iw += 32, ++itn) {
-      const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
-      T re = T(0);
+      for (int iw = lo + lane, itn = 0; iw < hi; iw += 32, ++itn) {
+        const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
+        T re = T(0);
 #pragma unroll 1
-      for (int t = 1; t >= 0; --t) {  // the + term (t = 1), then the - term
-        if (b < 0 || !box_far(Cb, Rb, b, om, t)) {
-          const T den = t ? c + om : c - om;
-          const T r = quot(half, den < T(0) ? -den : den);
-          if (r <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, t ? -om : om, r);
-          else if (t) nearp |= 1u << itn;
-          else nearm |= 1u << itn;
+        for (int t = 1; t >= 0; --t) {  // the + term (t = 1), then the - term
+          if (b < 0 || !box_far(Cb, Rb, b, om, t)) {
+            const T den = t ? c + om : c - om;
+            const T r = quot(half, den < T(0) ? -den : den);
+            if (r <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, t ? -om : om, r);
+            else if (t) nearp |= 1u << itn;
+            else nearm |= 1u << itn;
+          }
+        }
+        if (re != T(0)) add_re(iw, vr * re);
+      }
+      // near field: the (frequency, term) pairs go to the drain's near list (the caller keeps
+      // room for them)
+      const int nit = (hi - lo + 31) >> 5;
+#pragma unroll 1
+      for (int itn = 0; itn < nit; ++itn) {
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
+          const unsigned bal = __ballot_sync(kFull, mine);
+          if (mine) s_near[wib][nnear + __popc(bal & lt)] = (unsigned short)((slot << 9) | ((lo + itn * 32 + lane) * 2 + sgn));
+          nnear += __popc(bal);
         }
       }
-      if (re != T(0)) add_re(iw, vr * re);
+      __syncwarp();
     }
-    // near field: the (frequency, term) pairs go to the drain's near list (the caller keeps
-    // room for them)
-    const int nit = (hi - lo + 31) >> 5;
-#pragma unroll 1
-    for (int itn = 0; itn < nit; ++itn) {
-#pragma unroll
-      for (int sgn = 0; sgn < 2; ++sgn) {
-        const bool mine = ((sgn ? nearp : nearm) >> itn) & 1u;
-        const unsigned bal = __ballot_sync(kFull, mine);
-        if (mine) s_near[wib][nnear + __popc(bal & lt)] = (unsigned short)((slot << 9) | ((lo + itn * 32 + lane) * 2 + sgn));
-        nnear += __popc(bal);
-      }
-    }
-    __syncwarp();
   };
   // evaluates n <= DC queued pieces: own far-field moments one piece per lane, then each piece
   // on its frequencies with the whole warp
   auto drain = [&](int n) {
-    if (lane < n) {
+    if (!IMO && lane < n) {
       const int sl = (qh + lane) % QC;
       T d[4], ff[4];
 #pragma unroll
@@ -647,7 +698,9 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
         for (int k = lane; k < K; k += 32) acc[base + k] += scr[p * SKF + k];
       }
     }
-    const bool queue = has && b < kBoxFine;
+    // (Im only: pieces whose knot range meets the pass's frequencies)
+    const bool queue = has && b < kBoxFine &&
+                       (!IMO || (D0h + ee[3] > s_w[0] && D0h + ee[0] < s_w[nw - 1]));
     const unsigned qm = __ballot_sync(kFull, queue);
     if (queue) {
       const int sl = (qt + __popc(qm & lt)) % QC;
@@ -946,8 +999,10 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
     unsigned long long *brow = (unsigned long long *)db.box_part + (size_t)blockIdx.x * NS;
 #pragma unroll 1
     for (int i = threadIdx.x; i < 2 * kNWPass; i += blockDim.x) row[i] = s_fx[i / kNWPass][i % kNWPass];
+    if constexpr (!IMO) {
 #pragma unroll 1
-    for (int i = threadIdx.x; i < NS; i += blockDim.x) brow[i] = bfx[i];
+      for (int i = threadIdx.x; i < NS; i += blockDim.x) brow[i] = bfx[i];
+    }
   } else {
     if (boxes && first)  // a warp without batches
 #pragma unroll 1
@@ -1094,6 +1149,30 @@ cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const 
         g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq, omega, nw, db, Eklo, Ekqlo, counters);
     k_box_sum<false><<<(box_slots<false>() + 255) / 256, 256, 0, s>>>(db.box_part, nblocks, db.box_tot);
     k_box_eval<false><<<nw, 128, 0, s>>>(omega, db.box_tab, db.box_tot, db.far);
+    k_fx_rows<<<(2 * nw + 255) / 256, 256, 0, s>>>(db.fx, nblocks, nw, db.partR, db.partI);
+    *rows = 1;
+  }
+  return cudaGetLastError();
+}
+
+// Im only (the Kramers-Kronig route): the delta term on an ascending grid of w >= 0
+cudaError_t launch_dynamic_im(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
+                              const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
+                              const double *omega, int nw, const DynBufs &db, int nblocks,
+                              unsigned long long *counters, cudaStream_t s, const float *Eklo,
+                              const float *Ekqlo, int *rows) {
+  if (nw > kNWPass || nw <= 0 || nblocks <= 0) return cudaErrorInvalidValue;
+  if (!fp64 && (!Eklo || !Ekqlo)) return cudaErrorInvalidValue;
+  if (!db.fb || !db.fx || !db.ctr) return cudaErrorInvalidValue;
+  if (fp64) {
+    k_dynamic<true, true><<<nblocks, DynShape<true>::threads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq,
+                                                                       omega, nw, db, Eklo, Ekqlo, counters);
+    *rows = (int)((g.ntet + 31) / 32);
+  } else {
+    cudaError_t e = cudaMemsetAsync(db.ctr, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_dynamic<false, true><<<nblocks, DynShape<false>::threads, 0, s>>>(g, tet, Ek, Ekq, q, W2, cma, tau, occ, empq,
+                                                                         omega, nw, db, Eklo, Ekqlo, counters);
     k_fx_rows<<<(2 * nw + 255) / 256, 256, 0, s>>>(db.fx, nblocks, nw, db.partR, db.partI);
     *rows = 1;
   }

@@ -77,6 +77,8 @@ struct StaticBufs {
   int *next;       // batch counter
   int tcap;        // queue entries per batch (at most static_tab_cap())
   unsigned long long *pairs = nullptr;  // band-pair output: [w][w] fixed-point totals (or none)
+  int *off = nullptr;      // compacted queue: [nbatch + 1] offsets and [nbatch * tcap] values
+  double *vals = nullptr;  // (both null: one warp per batch walks its queue)
 };
 
 // static weights for one q: partial[2 * nbatch] (sum them for chi0); Ek/Ekq are the absolute
@@ -115,6 +117,16 @@ cudaError_t launch_dynamic(const Grid &g, const Tet &tet, const void *Ek, const 
                            unsigned long long *counters, cudaStream_t s, const float *Eklo,
                            const float *Ekqlo, int *rows);
 size_t dynamic_fx_bytes(int nblocks);
+// Im only, for the Kramers-Kronig route: partI in *rows rows of nw (omega ascending, >= 0)
+cudaError_t launch_dynamic_im(const Grid &g, const Tet &tet, const void *Ek, const void *Ekq, const Q &q,
+                              const void *W2, int cma, int fp64, float tau, const short *occ, const short *empq,
+                              const double *omega, int nw, const DynBufs &db, int nblocks,
+                              unsigned long long *counters, cudaStream_t s, const float *Eklo,
+                              const float *Ekqlo, int *rows);
+// Re from Im (Kramers-Kronig, chi0_kk.cu): im[0..m) on u_j = j du (im[0] = 0, im = 0 from u_m on),
+// re[i] at u_i, i < m, plus scale * (sum of dos[0..ndos)) at u = 0 when dos != NULL
+cudaError_t launch_kk(const double *im, int m, double du, double scale, const double *dos, int ndos, double *re,
+                      cudaStream_t s);
 int dynamic_persistent_blocks(int fp64);
 int dynamic_warps_per_cta(int fp64);
 size_t dynamic_box_slots(int fp64);

@@ -477,6 +477,71 @@ __global__ void __launch_bounds__(kThreads) k_static_tab(long long nbatch, Stati
   }
 }
 
+// The queued pieces compacted over all batches (one piece per thread instead of one batch per
+// warp: a batch holds ~12 of its 64 slots, so the per-batch walk ran 6.6 of 32 lanes):
+// exclusive scan of the per-batch counts, evaluation into vals[i], and a per-batch sum of
+// vals over the batch's segment in a fixed order (results independent of the schedule).
+__global__ void __launch_bounds__(1024) k_tab_scan(const int *__restrict__ n, long long nbatch,
+                                                    int *__restrict__ off) {
+  __shared__ long long part[1024];
+  const long long per = (nbatch + 1023) / 1024;
+  const long long b0 = threadIdx.x * per, b1 = b0 + per < nbatch ? b0 + per : nbatch;
+  long long sum = 0;
+  for (long long b = b0; b < b1; ++b) sum += n[b];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the thread sums
+    const long long v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  long long run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (long long b = b0; b < b1; ++b) {
+    off[b] = (int)run;
+    run += n[b];
+  }
+  if (threadIdx.x == 1023) off[nbatch] = (int)part[1023];
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_tab_eval(long long nbatch, StaticBufs sb) {
+  using T = typename std::conditional<FP64, double, float>::type;
+  const Piece<T> *tq = (const Piece<T> *)sb.tq;
+  const int total = sb.off[nbatch];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    long long lo = 0, hi = nbatch;  // batch: largest b with off[b] <= i
+    while (hi - lo > 1) {
+      const long long mid = (lo + hi) >> 1;
+      if (sb.off[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    const Piece<T> pc = tq[lo * sb.tcap + (i - sb.off[lo])];
+    double v;
+    if constexpr (FP64) {
+      v = pc.w * inv_sum_fast(pc.d, pc.f);
+    } else if (pc.code & 1) {  // near-degenerate knots: the FP64 table
+      double xd[4] = {pc.d[0], pc.d[1], pc.d[2], pc.d[3]}, fd[4] = {pc.f[0], pc.f[1], pc.f[2], pc.f[3]};
+      v = (double)pc.w * inv_sum_table(xd, fd);
+    } else {
+      v = (double)(pc.w * inv_sum_long(pc.d, pc.f));
+    }
+    sb.vals[i] = v;
+    if (sb.pairs) pair_add(sb.pairs, pc.code >> 1, v);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_tab_sum(long long nbatch, StaticBufs sb) {
+  const int lane = threadIdx.x & 31;
+  for (long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbatch;
+       b += ((long long)gridDim.x * blockDim.x) >> 5) {
+    double acc = 0.0;
+    for (int i = sb.off[b] + lane; i < sb.off[b + 1]; i += 32) acc += sb.vals[i];
+    const double v = warp_sum(acc);
+    if (lane == 0) sb.partial[nbatch + b] = v;
+  }
+}
+
 // ---------------------------------------------------------------- Gamma DOS term
 __global__ void __launch_bounds__(kThreads) k_dos(Grid g, Tet tet, const double *__restrict__ E, int lo,
                                                    int hi, double *__restrict__ partial,
@@ -644,8 +709,16 @@ cudaError_t launch_static(const Grid &g, const Tet &tet, const void *Ek, const v
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   long long tb = (nbatch * 32 + kThreads - 1) / kThreads;
   const int tblocks = (int)(tb < device_sms() * 16 ? tb : device_sms() * 16);
-  if (fp64) k_static_tab<true><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
-  else k_static_tab<false><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
+  if (sb.off && sb.vals) {  // compacted queue
+    k_tab_scan<<<1, 1024, 0, s>>>(sb.tq_n, nbatch, sb.off);
+    if (fp64) k_tab_eval<true><<<device_sms() * 8, kThreads, 0, s>>>(nbatch, sb);
+    else k_tab_eval<false><<<device_sms() * 8, kThreads, 0, s>>>(nbatch, sb);
+    k_tab_sum<<<tblocks, kThreads, 0, s>>>(nbatch, sb);
+  } else if (fp64) {
+    k_static_tab<true><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
+  } else {
+    k_static_tab<false><<<tblocks, kThreads, 0, s>>>(nbatch, sb);
+  }
   return cudaGetLastError();
 }
 

@@ -129,6 +129,30 @@ def test_static_band_pairs(C, O, prec):
         assert np.array_equal(a, b)
 
 
+def test_sweep_drivers(C, O):
+    """The Sec. III comparison drivers: band windows around E_F, CMA against exact |M|^2 (and
+    the CMA curve shifted to 0 at the first q), and the band-pair histogram, each against the
+    oracle with the same window or matrix elements (FP64, 1e-12)."""
+    import dataclasses
+    from paper_1407_3444_gb300 import sweeps
+    W = wl.tiny_tb(n=6, norb=6, nq=0, seed=wl.SEED_BASE + 47)
+    W.qs = [wl.QPoint(shift=(0, 0, 1)), wl.QPoint(shift=(1, 2, 0)), wl.QPoint(shift=(3, 3, 3))]
+    tr = sweeps.band_truncation(W, W.qs, [2, 4, 6], precision="fp64")
+    nocc = int(np.round(np.mean(np.sum(W.E < W.ef, axis=1))))
+    for w, got in tr.items():
+        lo = min(max(nocc - w // 2, 0), W.nb - w)
+        ref = np.array([O.chi0_q(W, q, window=(lo, lo + w)) for q in W.qs])
+        assert nerr(got[:, None], ref[:, None]) < 1e-12, (w, got, ref)
+    exact, cma, shifted = sweeps.cma_vs_exact(W, W.qs, precision="fp64")
+    Wc = dataclasses.replace(W, cma=True)
+    assert nerr(exact[:, None], O.chi0(W)[:, None]) < 1e-12
+    assert nerr(cma[:, None], O.chi0(Wc)[:, None]) < 1e-12
+    assert shifted[0] == 0.0 and np.allclose(shifted, cma - cma[0], rtol=0, atol=0)
+    chi, pairs = sweeps.pair_contributions(W, W.qs[1], precision="fp64")
+    assert abs(pairs.sum() - chi) <= 1e-12 * abs(chi)
+    assert np.max(np.abs(pairs - O.chi0_pairs_q(W, W.qs[1]))) <= 1e-12 * np.max(np.abs(pairs))
+
+
 def test_static_host_inputs_and_c64(C, O):
     W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 43, cdtype=np.complex64)
     ref = O.chi0(W)  # the oracle promotes the same complex64 values
@@ -225,6 +249,33 @@ def test_dynamic_many_frequencies_and_gamma(C, O):
     # there, so Im is compared on the scale of the whole (q, w) table
     ref_i = np.array(ref_i)
     assert np.max(np.abs(gi - ref_i)) < 1e-12 * np.max(np.abs(ref_i))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dynamic_kk_route(C, O, prec):
+    """Kramers-Kronig route (chi0_dynamic_kk): Im alone on a uniform grid that covers the
+    spectrum (two passes: 300 nodes), against the oracle's Im at every node; Re against the
+    oracle's transform of the oracle's Im (the device transform, independent code); and Re
+    against the principal value of Eq. 1 within the grid's interpolation error."""
+    W = wl.tiny_tb(n=8, norb=4, nq=0, seed=wl.SEED_BASE + 46)
+    W.qs = [wl.QPoint(shift=(1, 2, 3)), wl.QPoint(shift=(0, 0, 0), gamma=True)]
+    emax = float(W.E.max() - W.E.min()) + 0.5
+    nkk = 300
+    u = np.linspace(0.0, emax, nkk)
+    P = C.Plan(W, precision=prec, device=True)
+    re, im = P.dynamic_kk(emax, nkk)
+    P.close()
+    re, im = re.cpu().numpy(), im.cpu().numpy()
+    ref_re, ref_im = O.chi0(W, omega=u)
+    assert nerr(im[:1], ref_im[:1]) < TOL[prec], nerr(im[:1], ref_im[:1])
+    # at Gamma this model has no interband weight below emax: Im is 0 up to rounding (~1e-31),
+    # so the check there is absolute, against the size of Re
+    assert np.max(np.abs(im[1] - ref_im[1])) < TOL[prec] * np.max(np.abs(ref_re[1]))
+    kk = O.kk_re_from_im(u, ref_im[0], u)
+    assert nerr(re[0], kk) < (1e-10 if prec == "fp64" else 1e-6), nerr(re[0], kk)
+    # the route itself: second-order interpolation error of Im on this grid (oracle pin:
+    # 1.8e-3 -> 2.5e-5 over four halvings on a 4^3 two-band model)
+    assert nerr(re, ref_re) < 1e-2, nerr(re, ref_re)
 
 
 def test_dynamic_free_electron_open_grid(C, O):

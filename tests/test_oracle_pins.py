@@ -578,3 +578,57 @@ def test_pairs_add_up_to_chi0(oracle_mod):
     for b in range(4):
         dos_b = oracle_mod.chi0_q(W, qs[1], window=(b, b + 1))
         assert abs(Pg[b, b] - dos_b) <= 1e-12 * max(1.0, abs(dos_b)), (b, Pg[b, b], dos_b)
+
+
+def test_kk_transform_matches_cauchy_quadrature(oracle_mod):
+    """The Kramers-Kronig transform of a piecewise-linear Im (Re(w) = (1/pi) PV int_0^inf Im(u)
+    [1/(u - w) + 1/(u + w)] du) against scipy's Cauchy-weight quadrature of the same
+    interpolant, at nodes (where adjacent segments' singular parts cancel), between nodes, at
+    w = 0 and past the last node."""
+    integrate = pytest.importorskip("scipy.integrate")
+    rng = np.random.default_rng(9)
+    u = np.concatenate([[0.0], np.sort(rng.uniform(0.05, 2.0, 14))])
+    im = np.concatenate([[0.0], rng.uniform(-0.3, 1.0, 14)])
+    uu = np.append(u, u[-1] + (u[-1] - u[-2]))
+    yy = np.append(im, 0.0)
+
+    def interp(x):
+        return np.interp(x, uu, yy)
+
+    ws = np.array([0.0, u[3], 0.5 * (u[5] + u[6]), u[-1], uu[-1] + 0.3, 0.77])
+    got = oracle_mod.kk_re_from_im(u, im, ws)
+    for wv, g in zip(ws, got):
+        tot = 0.0
+        for j in range(len(uu) - 1):
+            a, b = uu[j], uu[j + 1]
+            for c in (wv, -wv):
+                if a < c < b:
+                    v, _ = integrate.quad(interp, a, b, weight="cauchy", wvar=c, epsabs=1e-13, epsrel=1e-12)
+                elif c == a or c == b:
+                    # split off the node: PV over the pair of adjacent segments is taken by the
+                    # symmetric limit; integrate (Im(u) - Im(c)) / (u - c) regularly plus Im(c) log
+                    f = lambda x, c=c: (interp(x) - interp(c)) / (x - c) if x != c else 0.0
+                    v, _ = integrate.quad(f, a, b, epsabs=1e-13, epsrel=1e-12, limit=200)
+                    v += interp(c) * (math.log(abs(b - c)) if b != c else 0.0) - interp(c) * (math.log(abs(a - c)) if a != c else 0.0)
+                else:
+                    v, _ = integrate.quad(lambda x, c=c: interp(x) / (x - c), a, b, epsabs=1e-13, epsrel=1e-12)
+                tot += v
+        ref = tot / math.pi
+        assert abs(g - ref) <= 1e-9 * max(1.0, abs(ref)), (wv, g, ref)
+
+
+def test_kk_route_converges_to_principal_value(oracle_mod):
+    """Sec. II's usual route: Re from Im by Kramers-Kronig on a grid that covers Im's whole
+    support approaches the principal value of Eq. 1 as the grid is refined (two-band model)."""
+    W = wl.tiny_tb(n=4, norb=2, nq=1, filling=1.0)
+    q = W.qs[0]
+    emax = float(W.E.max() - W.E.min()) + 0.5
+    ws = np.array([0.3, 0.9, 1.7])
+    re_pv, _ = oracle_mod.chi0_q(W, q, omega=ws)
+    errs = []
+    for m in (129, 513):
+        u = np.linspace(0.0, emax, m)
+        _, im = oracle_mod.chi0_q(W, q, omega=u)
+        re_kk = oracle_mod.kk_re_from_im(u, im, ws)
+        errs.append(np.max(np.abs(re_kk - re_pv)) / np.max(np.abs(re_pv)))
+    assert errs[1] < 0.5 * errs[0] and errs[1] < 2e-2, errs
