@@ -33,8 +33,13 @@ struct chi0_plan {
   size_t out_cap = 0;
   double *omega_d = nullptr;
   size_t omega_cap = 0;
-  double *Eq_stage = nullptr;
-  void *Cq_stage = nullptr;
+  double *Eq_stage = nullptr;                 // explicit k+q data from the host: two staging
+  void *Cq_stage = nullptr;                   // buffers, filled on a copy stream while the
+  double *Eq_stage2 = nullptr;                // previous q computes
+  void *Cq_stage2 = nullptr;
+  cudaStream_t copy_s = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  int stage_slot = 0;
   unsigned long long *counters_d = nullptr;
   short *occ_d = nullptr, *emp_d = nullptr, *occq_d = nullptr, *empq_d = nullptr;
   float *E32_d = nullptr, *Eq32_d = nullptr;  // energies - eF in FP32 (mixed precision): hi, then lo
@@ -141,6 +146,13 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->omega_d);
   cudaFree(p->Eq_stage);
   cudaFree(p->Cq_stage);
+  cudaFree(p->Eq_stage2);
+  cudaFree(p->Cq_stage2);
+  for (int i = 0; i < 2; ++i) {
+    if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
+    if (p->ev_free[i]) cudaEventDestroy(p->ev_free[i]);
+  }
+  if (p->copy_s) cudaStreamDestroy(p->copy_s);
   cudaFree(p->counters_d);
   cudaFree(p->occ_d);
   cudaFree(p->emp_d);
@@ -402,7 +414,8 @@ int validate_q(chi0_plan_t *p, const chi0_q_t &qd) {
   return CHI0_OK;
 }
 
-int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q) {
+int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q, int *slot_used) {
+  *slot_used = -1;
   const Grid &g = p->g;
   q.lo = qd.win.lo < 0 ? p->win.lo : qd.win.lo;
   q.hi = qd.win.lo < 0 ? p->win.hi : qd.win.hi;
@@ -418,16 +431,34 @@ int prepare_q(chi0_plan_t *p, const chi0_q_t &qd, Q &q) {
       q.Eq = qd.e_kq;
       q.Cq = qd.c_kq;
     } else {
+      // staging buffer `slot` (alternating): its copy waits until the q that used it last
+      // is done, runs on the copy stream, and the compute stream waits for the copy, so the
+      // copy of one q overlaps the kernels of the one before
+      const int slot = p->stage_slot;
+      p->stage_slot ^= 1;
+      if (!p->copy_s) {
+        CK(p, cudaStreamCreateWithFlags(&p->copy_s, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+          CK(p, cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming));
+          CK(p, cudaEventCreateWithFlags(&p->ev_free[i], cudaEventDisableTiming));
+        }
+      }
+      double *&Eb = slot ? p->Eq_stage2 : p->Eq_stage;
+      void *&Cb = slot ? p->Cq_stage2 : p->Cq_stage;
       const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;
-      if (!p->Eq_stage) CK(p, cudaMalloc(&p->Eq_stage, eb));
-      CK(p, cudaMemcpyAsync(p->Eq_stage, qd.e_kq, eb, cudaMemcpyHostToDevice, p->stream));
-      q.Eq = p->Eq_stage;
+      if (!Eb) CK(p, cudaMalloc(&Eb, eb));
+      CK(p, cudaStreamWaitEvent(p->copy_s, p->ev_free[slot], 0));
+      CK(p, cudaMemcpyAsync(Eb, qd.e_kq, eb, cudaMemcpyHostToDevice, p->copy_s));
+      q.Eq = Eb;
       if (!p->opts.cma) {
         const size_t cb = cplx_size(p->dtype) * (size_t)g.nc * g.norb * g.nb;
-        if (!p->Cq_stage) CK(p, cudaMalloc(&p->Cq_stage, cb));
-        CK(p, cudaMemcpyAsync(p->Cq_stage, qd.c_kq, cb, cudaMemcpyHostToDevice, p->stream));
-        q.Cq = p->Cq_stage;
+        if (!Cb) CK(p, cudaMalloc(&Cb, cb));
+        CK(p, cudaMemcpyAsync(Cb, qd.c_kq, cb, cudaMemcpyHostToDevice, p->copy_s));
+        q.Cq = Cb;
       }
+      CK(p, cudaEventRecord(p->ev_copied[slot], p->copy_s));
+      CK(p, cudaStreamWaitEvent(p->stream, p->ev_copied[slot], 0));
+      *slot_used = slot;
     }
   } else {
     if (!g.periodic) return fail(p, CHI0_EINVAL, "on-grid q shift needs a periodic grid");
@@ -458,7 +489,8 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
   size_t poff = 0;  // band-pair output: offset of this q's w x w block
   for (int iq = 0; iq < nq; ++iq) {
     Q q;
-    int rc = prepare_q(p, qs[iq], q);
+    int slot = -1;
+    int rc = prepare_q(p, qs[iq], q, &slot);
     if (rc) return rc;
     const int wq = q.hi - q.lo;
     unsigned long long *pfx = outP ? p->pairs_fx_d : nullptr;
@@ -560,6 +592,7 @@ static int enqueue_call(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double
         tm.stop();
       }
     }
+    if (slot >= 0) CK(p, cudaEventRecord(p->ev_free[slot], s));  // its staging buffer is free again
   }
   return CHI0_OK;
 }

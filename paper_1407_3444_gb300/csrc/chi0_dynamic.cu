@@ -238,17 +238,13 @@ __device__ __noinline__ void box_moments_fx_ol(const float e[4], const float f[4
   }
 }
 
-// Out-of-line copies of the large per-piece helpers: the weight kernel calls each from a few
-// places, and inlined copies made its body overflow the instruction cache (ncu: 45% of the issue
-// stalls waiting for instructions).
+// Out-of-line copies of per-piece helpers outside the hot near-field loop (the own moments of a
+// drain; the fallback's delta term): inlined copies made the kernel's body overflow the
+// instruction cache (ncu: 45% of the issue stalls waiting for instructions).  The near drain's
+// divided-difference table and de Boor recursion have one call site each and are inlined there
+// (8% faster than calling them).
 template <typename T, int KM>
 __device__ __noinline__ int far_moments_ol(const T d[4], const T f[4], T *a) { return far_moments<T, KM>(d, f, a); }
-template <typename T> __device__ __noinline__ bool inv_sum_shared_ol(const T x[4], const T f[4], T &out) {
-  return inv_sum_shared(x, f, out);
-}
-template <typename T> __device__ __noinline__ T delta_sum_pre_ol(const T x[4], const T f[4], const T *rs) {
-  return delta_sum_pre(x, f, rs);
-}
 template <typename T> __device__ __noinline__ T delta_sum_ol(const T d[4], const T f[4]) { return delta_sum(d, f, T(0)); }
 
 // does box b stand in for term (0: 1/(D - u), 1: 1/(D + u)) at frequency u = om?  Fine boxes
@@ -518,14 +514,14 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
         // (a near entry has the frequency within two half-widths of the piece's midpoint,
         // where the moment series about the knot midpoint does not apply)
         T v;
-        if (IMO) {  // the delta term alone
+        if constexpr (IMO) {  // the delta term alone
           if (x[0] < T(0) && x[3] > T(0)) {
             iw = ent >> 1;
             const T rs[6] = {rcp(ee[1] - ee[0]), rcp(ee[2] - ee[1]), rcp(ee[3] - ee[2]),
                              rcp(ee[2] - ee[0]), rcp(ee[3] - ee[1]), rcp(ee[3] - ee[0])};
-            im = vr * delta_sum_pre_ol(x, ff, rs) * T(3.141592653589793);
+            im = vr * delta_sum_pre(x, ff, rs) * T(3.141592653589793);
           }
-        } else if (inv_sum_shared_ol(x, ff, v)) {
+        } else if (inv_sum_shared(x, ff, v)) {
           iw = ent >> 1;
           re = vr * v;
           if ((ent & 1) == 0 && x[0] < T(0) && x[3] > T(0)) {
@@ -533,7 +529,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
             // unshifted offsets: nonnegative terms, no cancellation)
             const T rs[6] = {rcp(ee[1] - ee[0]), rcp(ee[2] - ee[1]), rcp(ee[3] - ee[2]),
                              rcp(ee[2] - ee[0]), rcp(ee[3] - ee[1]), rcp(ee[3] - ee[0])};
-            im = vr * delta_sum_pre_ol(x, ff, rs) * T(3.141592653589793);
+            im = vr * delta_sum_pre(x, ff, rs) * T(3.141592653589793);
             if (neg) im = -im;
           }
         } else {

@@ -36,6 +36,7 @@ template <typename T> struct Num;
 template <> struct Num<double> {
   static __device__ __forceinline__ double lg(double x) { return log(x); }
   static constexpr double tol = 1e-17;
+  static constexpr float log2_tol = -56.4727f;  // log2(tol)
   static constexpr double kappa = 0.25;  // series branch: (x3 - x0) <= kappa (x3 + x0)
   static constexpr double kappa_long = 0.25;
   static constexpr double kappa_far = 0.5;  // far-field expansion of the dynamic PV terms
@@ -44,6 +45,7 @@ template <> struct Num<double> {
 template <> struct Num<float> {
   static __device__ __forceinline__ float lg(float x) { return logf(x); }
   static constexpr float tol = 2e-8f;
+  static constexpr float log2_tol = -25.5754f;  // log2(tol)
   static constexpr float kappa = 0.5f;       // series branch inside the carving loop
   static constexpr float kappa_long = 0.7f;  // series branch of queued pieces (evaluated together)
   static constexpr float kappa_far = 0.5f;   // far-field expansion of the dynamic PV terms
@@ -513,18 +515,25 @@ template <typename T, int KMAX> __device__ int far_moments(const T d[4], const T
   return k;
 }
 
-// (1/(c - w)) sum_{k<K} a_k z^k with z = c/(c - w), truncated where rho^k < tol
+// (1/(c - w)) sum_{k<K} a_k z^k with z = c/(c - w), truncated where rho^k < tol.  The
+// polynomial is split into its even and odd parts, E(z^2) + z O(z^2), two independent Horner
+// chains of half the length (the weight kernels are bound by dependent latency).
 template <typename T> __device__ __forceinline__ T far_eval(const T *a, int K, T c, T w, T rho) {
   const T den = c - w, rd = rcp(den);
-  const T z = c * rd;
+  const T z = c * rd, z2 = z * z;
   int kk = K;
   if (rho > T(0)) {
-    const float need = __fdividef(__log2f((float)Num<T>::tol), __log2f((float)rho));  // rho^need = tol
+    const float need = __fdividef(Num<T>::log2_tol, __log2f((float)rho));  // rho^need = tol
     kk = min(K, 2 + (int)need);
   }
-  T sum = T(0);
-  for (int k = kk - 1; k >= 0; --k) sum = sum * z + a[k];
-  return sum * rd;
+  T e = T(0), o = T(0);
+  int k = kk - 1;
+  if (k >= 0 && (k & 1) == 0) e = a[k--];  // the top index odd from here on
+  for (; k >= 1; k -= 2) {
+    o = o * z2 + a[k];
+    e = e * z2 + a[k - 1];
+  }
+  return (e + z * o) * rd;
 }
 
 // Normalised cubic B-spline density M(w; t0..t4) (integral 1) by the de Boor-Cox
