@@ -215,7 +215,7 @@ template <typename T> __device__ __noinline__ void box_moments_ol(const T e[4], 
 }
 
 // the same moments added straight into fixed-point box sums dst[0..K) (shared-memory atomics)
-__device__ __noinline__ void box_moments_fx_ol(const float e[4], const float f[4], float v, unsigned long long *dst,
+__device__ __forceinline__ void box_moments_fx(const float e[4], const float f[4], float v, unsigned long long *dst,
                                                int K) {
   float H[4] = {1.f, 1.f, 1.f, 1.f};
   float P[4] = {1.f, 1.f, 1.f, 1.f};
@@ -238,13 +238,11 @@ __device__ __noinline__ void box_moments_fx_ol(const float e[4], const float f[4
   }
 }
 
-// Out-of-line copies of per-piece helpers outside the hot near-field loop (the own moments of a
-// drain; the fallback's delta term): inlined copies made the kernel's body overflow the
-// instruction cache (ncu: 45% of the issue stalls waiting for instructions).  The near drain's
-// divided-difference table and de Boor recursion have one call site each and are inlined there
-// (8% faster than calling them).
-template <typename T, int KM>
-__device__ __noinline__ int far_moments_ol(const T d[4], const T f[4], T *a) { return far_moments<T, KM>(d, f, a); }
+// Out-of-line copy of the fallback's delta term: inlined copies of the helpers at several call
+// sites made the kernel's body overflow the instruction cache (ncu: 45% of the issue stalls
+// waiting for instructions).  Helpers with one call site (the near drain's divided-difference
+// table and de Boor recursion, the own and the box moments) are inlined there: 8% and 3%
+// faster than calling them.
 template <typename T> __device__ __noinline__ T delta_sum_ol(const T d[4], const T f[4]) { return delta_sum(d, f, T(0)); }
 
 // does box b stand in for term (0: 1/(D - u), 1: 1/(D + u)) at frequency u = om?  Fine boxes
@@ -632,7 +630,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
         d[i] = s_qv[wib][sl][1] + s_qe[wib][sl][i];
         ff[i] = s_qf[wib][sl][i];
       }
-      s_pk[wib][lane] = far_moments_ol<T, KM>(d, ff, scr + lane * SKM);
+      s_pk[wib][lane] = far_moments<T, KM>(d, ff, scr + lane * SKM);
     }
     __syncwarp();
     // pieces one by one (p < n), the near list whenever it might not hold another piece's
@@ -676,7 +674,7 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
         T e[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) e[i] = (base + ee[i]) * ri;
-        if constexpr (FX) box_moments_fx_ol(e, ff, vr, bfx + slot_base<FP64>(b), b < kBoxFine ? KF : KG);
+        if constexpr (FX) box_moments_fx(e, ff, vr, bfx + slot_base<FP64>(b), b < kBoxFine ? KF : KG);
         else box_moments_ol(e, ff, vr, scr + lane * SKF, b < kBoxFine ? KF : KG);
         ++nboxed;
       }
