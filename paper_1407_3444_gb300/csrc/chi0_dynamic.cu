@@ -245,6 +245,39 @@ __device__ __forceinline__ void box_moments_fx(const float e[4], const float f[4
 // faster than calling them.
 template <typename T> __device__ __noinline__ T delta_sum_ol(const T d[4], const T f[4]) { return delta_sum(d, f, T(0)); }
 
+// own-series terms for convergence ratio rho (rho^kk <= tol), at most K
+template <typename T> __device__ __forceinline__ int own_terms(int K, T rho) {
+  if (!(rho > T(0))) return K > 0 ? 1 : 0;
+  const float need = __fdividef(Num<T>::log2_tol, __log2f((float)rho));
+  const int kk = 2 + (int)need;
+  return kk < K ? kk : K;
+}
+
+// (1/(c - w)) sum_{k<kk} a_k z^k, z = c/(c - w), as two half-length Horner chains (even and
+// odd powers); FP32 coefficients read in aligned pairs
+template <typename T> __device__ __forceinline__ T far_eval_k(const T *a, int kk, T c, T w) {
+  const T den = c - w, rd = rcp(den);
+  const T z = c * rd, z2 = z * z;
+  T e = T(0), o = T(0);
+  int k = kk - 1;
+  if (k >= 0 && (k & 1) == 0) e = a[k--];
+#pragma unroll 2
+  for (; k >= 1; k -= 2) {
+    T lo_, hi_;
+    if constexpr (sizeof(T) == 4) {
+      const float2 pr = *reinterpret_cast<const float2 *>(a + k - 1);
+      lo_ = pr.x;
+      hi_ = pr.y;
+    } else {
+      lo_ = a[k - 1];
+      hi_ = a[k];
+    }
+    o = o * z2 + hi_;
+    e = e * z2 + lo_;
+  }
+  return (e + z * o) * rd;
+}
+
 // does box b stand in for term (0: 1/(D - u), 1: 1/(D + u)) at frequency u = om?  Fine boxes
 // only near themselves; geometric boxes always.  Same expression in both kernels.
 template <typename T> __device__ __forceinline__ bool box_far(T C, T R, int b, T om, int term) {
@@ -262,10 +295,21 @@ __device__ __noinline__ typename std::conditional<FP64, double, float>::type nea
     const typename std::conditional<FP64, double, float>::type *f, float tau, int &nfp64) {
   using T = typename std::conditional<FP64, double, float>::type;
   T xx[4] = {x[0], x[1], x[2], x[3]};
+  // (the entries that reach this function are the ones the shared table left: the per-vertex
+  // table directly, after the series branches)
   if constexpr (FP64) {
-    return inv_sum(xx, f);
+    if (series_ok(xx, T(Num<T>::kappa))) return series_sum(xx, f);
+    return inv_sum_table(xx, f);
   } else {
-    return inv_sum_mixed(xx, f, tau, &nfp64);
+    if (series_ok(xx, Num<float>::kappa)) return series_sum(xx, f);
+    float y[4];
+    if (!mixed_knots(y, xx, tau)) {
+      if (series_ok(y, Num<float>::kappa_long)) return series_sum(y, f);
+      return inv_sum_table(y, f);
+    }
+    ++nfp64;
+    double yd[4] = {y[0], y[1], y[2], y[3]}, fd[4] = {f[0], f[1], f[2], f[3]};
+    return (float)inv_sum_table(yd, fd);
   }
 }
 
@@ -312,7 +356,9 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
   constexpr int W = S::warps, KM = S::KM, KF = S::KF, KG = S::KG, DC = S::DC;
   constexpr int QC = 64;  // queue of final tetrahedra that evaluate frequencies themselves
   constexpr int NS = box_slots<FP64>();
-  constexpr int SKM = KM + 1, SKF = KF + 1;  // per-lane strides of the scratch (odd: no bank conflicts)
+  // per-piece strides of the scratch: odd (conflict-free lane-parallel writes), except the FP32
+  // own moments, even so that the own series reads them in aligned pairs (2-way write conflicts)
+  constexpr int SKM = FP64 ? KM + 1 : KM + 2, SKF = KF + 1;
   constexpr int KU = DC * SKM > 32 * SKF ? DC * SKM : 32 * SKF;  // per-warp scratch (T elements)
   static_assert(QC >= DC + 32, "one carving step adds at most 32 queued pieces");
   __shared__ int s_c[W][32][4], s_cq[W][32][4];
@@ -593,13 +639,18 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
         T re = T(0);
 #pragma unroll 1
         for (int t = 1; t >= 0; --t) {  // the + term (t = 1), then the - term
+          int kk = 0;  // own-series terms this lane needs for this term (0: none)
           if (b < 0 || !box_far(Cb, Rb, b, om, t)) {
             const T den = t ? c + om : c - om;
             const T r = quot(half, den < T(0) ? -den : den);
-            if (r <= T(Num<T>::kappa_far)) re += far_eval(am, K, c, t ? -om : om, r);
+            if (r <= T(Num<T>::kappa_far)) kk = own_terms<T>(K, r);
             else if (t) nearp |= 1u << itn;
             else nearm |= 1u << itn;
           }
+          // one trip count for the lanes of the warp (extra terms only add what lies below the
+          // truncation tolerance): a convergent loop
+          const int km = __reduce_max_sync(__activemask(), kk);
+          if (kk > 0) re += far_eval_k(am, km, c, t ? -om : om);
         }
         if (re != T(0)) add_re(iw, vr * re);
       }
