@@ -257,6 +257,23 @@ int chi0_dynamic(chi0_plan_t *plan, const chi0_q_t *q, int nq, const double *ome
  * capture.  re, im: host or device like chi0_dynamic's outputs. */
 int chi0_dynamic_kk(chi0_plan_t *plan, const chi0_q_t *q, int nq, double wmax, int nkk, double *re, double *im);
 
+/* Energies and eigenvectors at k+q for an off-grid q by linear interpolation from the plan's
+ * mesh (Sec. II: the data at k+q are approximated by linear interpolation, energies and
+ * matrix elements on equal footing).  For every corner k of the periodic mesh, k+q (qfrac in
+ * units of the reciprocal lattice vectors) lies in one tetrahedron {000, e_p0, e_p0 + e_p1, 111}
+ * of one cube (p: the axis order sorting the cube-local coordinates t descending); with the
+ * barycentric weights (1 - t_p0, t_p0 - t_p1, t_p1 - t_p2, t_p2) every energy is the weighted
+ * sum of the four corner values of its band, and every eigenvector the weighted sum of the four
+ * corner vectors of its band after each is turned onto the phase of the first (times
+ * conj(<v_0|v_i>) / |<v_0|v_i>|), normalised.  Outputs in the plan's layouts: e_kq [Nk][nbands]
+ * (absolute energies, FP64), c_kq [Nk][norb][nbands] in the plan's eigenvector type (NULL, or
+ * a CMA plan: energies only); device pointers when the plan takes device inputs, else host
+ * pointers.  They are the explicit k+q data of a chi0_q_t (e_kq, c_kq) for chi0_static or
+ * chi0_dynamic.  An approximation: its error falls with the mesh spacing (exact for data linear
+ * in k).  Errors: CHI0_EINVAL (NULL plan, qfrac or e_kq, a non-periodic grid, |qfrac| >= 1e6),
+ * CHI0_ENOMEM, CHI0_ECUDA. */
+int chi0_interpolate_kq(chi0_plan_t *plan, const double *qfrac, double *e_kq, void *c_kq);
+
 /* Autotuner.  Times the call (static when omega == NULL, else dynamic on nw frequencies)
  * once per candidate launch shape, with CUDA events on the plan's stream, and keeps the
  * fastest shape in the plan for its later calls.  Candidates, tuned one after the other:
@@ -337,7 +354,7 @@ void chi0_destroy(chi0_plan_t *plan);
 const char *chi0_last_error(const chi0_plan_t *plan);
 
 /* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow
- * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs; 103 adds chi0_dynamic_kk. */
+ * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs; 103 adds chi0_dynamic_kk; 104 adds chi0_interpolate_kq. */
 int chi0_version(void);
 
 #ifdef __cplusplus

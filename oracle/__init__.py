@@ -233,6 +233,57 @@ def kk_re_from_im(u, im, w):
     return out
 
 
+def kq_interpolate(W, qfrac):
+    """Energies and eigenvectors at k+q for every corner k of W's periodic mesh by linear
+    interpolation from the mesh (Sec. II): k+q lies in one tetrahedron {000, e_p0, e_p0 + e_p1,
+    111} of one cube (p sorts the cube-local coordinates t descending); the barycentric weights
+    are (1 - t_p0, t_p0 - t_p1, t_p1 - t_p2, t_p2).  Energies: the weighted sum per band.
+    Eigenvectors: per band, the corner vectors turned onto the phase of the first corner's
+    (times conj(<v_0|v_i>) / |<v_0|v_i>|), summed with the weights and normalised.
+    Returns (Eq [Nc, nb], Cq [Nc, norb, nb] complex128, or None without eigenvectors)."""
+    n = np.array(W.n, dtype=np.int64)
+    assert W.periodic
+    nc = int(np.prod(n))
+    i0, i1, i2 = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    idx = np.stack([i0.ravel(), i1.ravel(), i2.ravel()], axis=1)          # corner c -> (i0, i1, i2)
+    x = idx + np.asarray(qfrac, dtype=np.float64)[None, :] * n[None, :]
+    fl = np.floor(x)
+    t = x - fl
+    base = np.mod(fl.astype(np.int64), n[None, :])
+    E = np.asarray(W.E, dtype=np.float64)
+    C = None if (W.cma or W.C is None) else np.asarray(W.C, dtype=np.complex128)
+    Eq = np.empty_like(E)
+    Cq = None if C is None else np.empty_like(C)
+    for c in range(nc):
+        tc = t[c]
+        # axis order: descending t, ties to the lower axis (a stable sort of -t)
+        order = sorted(range(3), key=lambda d: (-tc[d], d))
+        w = [1.0 - tc[order[0]], tc[order[0]] - tc[order[1]], tc[order[1]] - tc[order[2]], tc[order[2]]]
+        off = np.zeros(3, dtype=np.int64)
+        corners = []
+        for v in range(4):
+            if v >= 1:
+                off[order[v - 1]] = 1
+            j = np.mod(base[c] + off, n)
+            corners.append(int((j[0] * n[1] + j[1]) * n[2] + j[2]))
+        Eq[c] = sum(w[v] * E[corners[v]] for v in range(4))
+        if C is not None:
+            v0 = C[corners[0]]                                   # [norb, nb]
+            acc = np.zeros_like(v0)
+            for v in range(4):
+                vi = C[corners[v]]
+                if v == 0:
+                    ph = np.ones(vi.shape[1], dtype=np.complex128)
+                else:
+                    ov = np.sum(np.conj(v0) * vi, axis=0)        # <v_0|v_i> per band
+                    m = np.abs(ov)
+                    ph = np.where(m > 0, np.conj(ov) / np.where(m > 0, m, 1.0), 1.0)
+                acc += w[v] * vi * ph[None, :]
+            nrm = np.sqrt(np.sum(np.abs(acc) ** 2, axis=0))
+            Cq[c] = acc / np.where(nrm > 0, nrm, 1.0)[None, :]
+    return Eq, Cq
+
+
 def chi0(W, omega=None, sign: int = 0, nthreads: int = 0, qs=None):
     """chi0 for every q of W: static -> [nq]; dynamic -> (re [nq, nw], im [nq, nw])."""
     qs = W.qs if qs is None else qs

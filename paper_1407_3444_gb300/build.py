@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchi0.so")
-SOURCES = ["chi0_kernels.cu", "chi0_dynamic.cu", "chi0_kk.cu", "chi0_abi.cu", "chi0_noalloc.cu", "chi0_overlap_tc.cu",
+SOURCES = ["chi0_kernels.cu", "chi0_dynamic.cu", "chi0_kk.cu", "chi0_interp.cu", "chi0_abi.cu", "chi0_noalloc.cu", "chi0_overlap_tc.cu",
            "chi0_peaks.cu"]
 HEADERS = ["chi0_math.cuh", "chi0_internal.h", "chi0_grid.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -93,7 +93,7 @@ _lib = None
 # every entry point declared in include/chi0.h (checked by the ABI test)
 EXPORTS = ["chi0_opts_default", "chi0_plan", "chi0_static", "chi0_dynamic", "chi0_plan_stats",
            "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune", "chi0_peak",
-           "chi0_static_pairs", "chi0_dynamic_kk"]
+           "chi0_static_pairs", "chi0_dynamic_kk", "chi0_interpolate_kq"]
 CHI0_PEAK_FP32_FMA, CHI0_PEAK_FP64_FMA, CHI0_PEAK_TF32_MMA, CHI0_PEAK_BF16_MMA = 0, 1, 2, 3
 CHI0_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -117,6 +117,8 @@ def lib():
         L.chi0_dynamic_kk.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_double, ct.c_int,
                                       ct.c_void_p, ct.c_void_p]
         L.chi0_dynamic_kk.restype = ct.c_int
+        L.chi0_interpolate_kq.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double), ct.c_void_p, ct.c_void_p]
+        L.chi0_interpolate_kq.restype = ct.c_int
         L.chi0_dynamic.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_int,
                                    ct.c_void_p, ct.c_void_p]
         L.chi0_dynamic.restype = ct.c_int
@@ -168,6 +170,11 @@ def chi0_static(plan, q, nq: int, chi_ptr: int) -> None:
 
 def chi0_static_pairs(plan, q, nq: int, chi_ptr: int, pairs_ptr: int) -> None:
     _check(lib().chi0_static_pairs(plan, q, nq, chi_ptr, pairs_ptr), plan)
+
+
+def chi0_interpolate_kq(plan, qfrac, e_ptr: int, c_ptr: int) -> None:
+    q = (ct.c_double * 3)(*[float(x) for x in qfrac])
+    _check(lib().chi0_interpolate_kq(plan, q, e_ptr, c_ptr), plan)
 
 
 def chi0_dynamic_kk(plan, q, nq: int, wmax: float, nkk: int, re_ptr: int, im_ptr: int) -> None:
@@ -409,6 +416,31 @@ class Plan:
             blocks.append(pr[off:off + w * w].reshape(w, w))
             off += w * w
         return o, blocks
+
+    def interpolate_kq(self, qfrac):
+        """Energies [Nc, nb] and eigenvectors [Nc, norb, nb] at k+q by linear interpolation from
+        the mesh (numpy arrays; None for the vectors of a CMA plan)."""
+        W = self.W
+        nc = W.ncorner
+        E = np.empty((nc, W.nb))
+        Cq = None
+        if self.device:
+            t = self.torch
+            Ed = t.empty((nc, W.nb), dtype=t.float64, device="cuda")
+            Cd = None
+            if not self.cma:
+                Cd = t.empty((nc, W.norb, W.nb), dtype=t.complex64 if self.staged.evec_dtype == CHI0_C64
+                             else t.complex128, device="cuda")
+            chi0_interpolate_kq(self.h, qfrac, Ed.data_ptr(), Cd.data_ptr() if Cd is not None else None)
+            self.stream.synchronize()
+            E = Ed.cpu().numpy()
+            Cq = Cd.cpu().numpy() if Cd is not None else None
+        else:
+            if not self.cma:
+                Cq = np.empty((nc, W.norb, W.nb), dtype=np.complex64 if self.staged.evec_dtype == CHI0_C64
+                              else np.complex128)
+            chi0_interpolate_kq(self.h, qfrac, E.ctypes.data, Cq.ctypes.data if Cq is not None else None)
+        return E, Cq
 
     def dynamic_kk(self, wmax: float, nkk: int, qarr=None):
         """Kramers-Kronig route: (re, im) [nq, nkk] on u_j = j wmax / (nkk - 1)."""

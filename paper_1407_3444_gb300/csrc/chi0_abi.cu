@@ -63,6 +63,9 @@ struct chi0_plan {
   size_t pairs_fx_cap = 0;                    // and the FP64 results of the call (host outputs)
   double *pairs_out_d = nullptr;
   size_t pairs_out_cap = 0;
+  double *ikq_E_d = nullptr;                  // chi0_interpolate_kq with host outputs
+  void *ikq_C_d = nullptr;
+  size_t ikq_E_cap = 0, ikq_C_cap = 0;
   void *tq_d = nullptr;                       // queued final tetrahedra per batch
   int *tq_n_d = nullptr;
   int *tq_off_d = nullptr;                    // compacted queue: offsets and values
@@ -121,7 +124,7 @@ extern "C" void chi0_opts_default(chi0_opts_t *o) {
   o->wait_budget = 0;
 }
 
-extern "C" int chi0_version(void) { return 103; }
+extern "C" int chi0_version(void) { return 104; }
 
 extern "C" const char *chi0_last_error(const chi0_plan_t *p) { return p ? p->err : g_plan_err; }
 
@@ -176,6 +179,8 @@ static void release(chi0_plan_t *p) {
   cudaFree(p->ctr_d);
   cudaFree(p->pairs_fx_d);
   cudaFree(p->pairs_out_d);
+  cudaFree(p->ikq_E_d);
+  cudaFree(p->ikq_C_d);
 }
 
 extern "C" void chi0_destroy(chi0_plan_t *p) {
@@ -769,6 +774,39 @@ extern "C" int chi0_static_pairs(chi0_plan_t *p, const chi0_q_t *q, int nq, doub
   if (!pairs) return fail(p, CHI0_EINVAL, "pairs is NULL");
   if (p && p->win.hi - p->win.lo > 1024) return fail(p, CHI0_EINVAL, "band-pair output: window wider than 1024");
   return run(p, q, nq, nullptr, 0, chi, nullptr, pairs);
+}
+
+extern "C" int chi0_interpolate_kq(chi0_plan_t *p, const double *qfrac, double *e_kq, void *c_kq) {
+  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
+  if (!qfrac || !e_kq) return fail(p, CHI0_EINVAL, "qfrac or e_kq is NULL");
+  if (!p->g.periodic) return fail(p, CHI0_EINVAL, "k+q interpolation needs a periodic grid");
+  for (int d = 0; d < 3; ++d)
+    if (!(fabs(qfrac[d]) < 1e6)) return fail(p, CHI0_EINVAL, "qfrac[%d] = %g", d, qfrac[d]);
+  const Grid &g = p->g;
+  const bool vecs = c_kq && !p->opts.cma;
+  const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;
+  const size_t cb = vecs ? cplx_size(p->dtype) * (size_t)g.nc * g.norb * g.nb : 0;
+  double *Eo = e_kq;
+  void *Co = vecs ? c_kq : nullptr;
+  if (!p->opts.inputs_on_device) {  // host outputs: through device scratch
+    int rc = ensure(p, (void **)&p->ikq_E_d, &p->ikq_E_cap, eb);
+    if (rc) return rc;
+    Eo = p->ikq_E_d;
+    if (vecs) {
+      rc = ensure(p, &p->ikq_C_d, &p->ikq_C_cap, cb);
+      if (rc) return rc;
+      Co = p->ikq_C_d;
+    }
+  }
+  CK(p, launch_interp_kq(g, p->E_d, vecs ? p->C_d : nullptr, p->dtype == CHI0_C64, qfrac, Eo, Co, p->stream));
+  p->stats.kernels += 1;
+  if (!p->opts.inputs_on_device) {
+    CK(p, cudaMemcpyAsync(e_kq, Eo, eb, cudaMemcpyDeviceToHost, p->stream));
+    if (vecs) CK(p, cudaMemcpyAsync(c_kq, Co, cb, cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaStreamSynchronize(p->stream));
+  }
+  CK(p, cudaGetLastError());
+  return CHI0_OK;
 }
 
 extern "C" int chi0_dynamic_kk(chi0_plan_t *p, const chi0_q_t *q, int nq, double wmax, int nkk, double *re,

@@ -123,6 +123,11 @@ cudaError_t launch_dynamic_im(const Grid &g, const Tet &tet, const void *Ek, con
                               const double *omega, int nw, const DynBufs &db, int nblocks,
                               unsigned long long *counters, cudaStream_t s, const float *Eklo,
                               const float *Ekqlo, int *rows);
+// energies and eigenvectors at k+q (fractional q) by linear interpolation from the periodic
+// mesh (chi0_interp.cu): Eq [nc][nb], Cq [nc][norb][nb] (C == nullptr: energies only), c64:
+// complex64 vectors, else complex128
+cudaError_t launch_interp_kq(const Grid &g, const double *E, const void *C, int c64, const double q[3], double *Eq,
+                             void *Cq, cudaStream_t s);
 // Re from Im (Kramers-Kronig, chi0_kk.cu): im[0..m) on u_j = j du (im[0] = 0, im = 0 from u_m on),
 // re[i] at u_i, i < m, plus scale * (sum of dos[0..ndos)) at u = 0 when dos != NULL
 cudaError_t launch_kk(const double *im, int m, double du, double scale, const double *dos, int ndos, double *re,

@@ -153,6 +153,34 @@ def test_sweep_drivers(C, O):
     assert np.max(np.abs(pairs - O.chi0_pairs_q(W, W.qs[1]))) <= 1e-12 * np.max(np.abs(pairs))
 
 
+@pytest.mark.parametrize("cdt", ["c128", "c64"])
+def test_interpolated_kq(C, O, cdt):
+    """Off-grid q by linear interpolation of the mesh data (chi0_interpolate_kq, Sec. II)
+    against the oracle's interpolation, then chi0 on the interpolated k+q data (explicit q)
+    against the oracle on the same data; host and device outputs agree bitwise."""
+    cdtype = np.complex64 if cdt == "c64" else np.complex128
+    W = wl.tiny_tb(n=6, norb=4, nq=0, seed=wl.SEED_BASE + 54, cdtype=cdtype)
+    q = (0.173, 0.061, 0.29)
+    P = C.Plan(W, precision="fp64", device=True)
+    Eq, Cq = P.interpolate_kq(q)
+    P.close()
+    Ph = C.Plan(W, precision="fp64", device=False)
+    Eh, Ch = Ph.interpolate_kq(q)
+    Ph.close()
+    assert np.array_equal(Eq, Eh) and np.array_equal(Cq, Ch)
+    Eo, Co = O.kq_interpolate(W, q)
+    tol = 1e-12 if cdt == "c128" else 1e-6
+    assert np.max(np.abs(Eq - Eo)) <= 1e-12 * np.max(np.abs(Eo))
+    assert np.max(np.abs(Cq - Co)) <= tol, np.max(np.abs(Cq - Co))
+    Wq = wl.Workload(W.name, W.n, W.periodic, W.nb, W.norb, W.E, W.C, W.ef, W.window, False,
+                     [wl.QPoint(Eq=Eq, Cq=Cq.astype(W.C.dtype))])
+    got = run_static(C, Wq, "fp64")
+    Wo = wl.Workload(W.name, W.n, W.periodic, W.nb, W.norb, W.E, W.C.astype(np.complex128), W.ef, W.window, False,
+                     [wl.QPoint(Eq=Eq, Cq=Cq.astype(np.complex128))])
+    ref = O.chi0(Wo)
+    assert nerr(got[:, None], ref[:, None]) < (1e-12 if cdt == "c128" else 1e-6)
+
+
 def test_static_host_inputs_and_c64(C, O):
     W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 43, cdtype=np.complex64)
     ref = O.chi0(W)  # the oracle promotes the same complex64 values

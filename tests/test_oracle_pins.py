@@ -632,3 +632,52 @@ def test_kk_route_converges_to_principal_value(oracle_mod):
         re_kk = oracle_mod.kk_re_from_im(u, im, ws)
         errs.append(np.max(np.abs(re_kk - re_pv)) / np.max(np.abs(re_pv)))
     assert errs[1] < 0.5 * errs[0] and errs[1] < 2e-2, errs
+
+
+def test_kq_interpolation_on_grid_and_linear(oracle_mod):
+    """Linear interpolation of the data at k+q (Sec. II): an on-grid q returns the mesh data at
+    the shifted corner (eigenvectors up to their phase), and a k-linear quantity is reproduced
+    exactly wherever k+q stays inside the mesh's unwrapped part."""
+    W = wl.tiny_tb(n=5, norb=3, nq=0, seed=wl.SEED_BASE + 51)
+    n = 5
+    Eq, Cq = oracle_mod.kq_interpolate(W, (2 / n, 1 / n, 3 / n))
+    idx = np.array([(i, j, k) for i in range(n) for j in range(n) for k in range(n)])
+    sh = ((idx[:, 0] + 2) % n * n + (idx[:, 1] + 1) % n) * n + (idx[:, 2] + 3) % n
+    assert np.array_equal(Eq, W.E[sh])
+    ov = np.abs(np.sum(np.conj(W.C[sh]) * Cq, axis=1))       # |<v(k+q)|interpolated>| per band
+    assert np.allclose(ov, 1.0, atol=1e-12)
+    # k-linear energies: E = a . (i, j, k) + b per band; q small enough that no corner
+    # below the last plane wraps
+    a = np.array([0.3, -0.7, 1.1])
+    Wl = wl.Workload("lin", (n, n, n), True, 2, 2, np.stack([idx @ a, idx @ a + 2.0], axis=1), None, 0.5,
+                     (0, 2), True, [])
+    q = np.array([0.13, 0.05, 0.11])
+    El, _ = oracle_mod.kq_interpolate(Wl, q)
+    inner = np.all(idx < n - 1, axis=1)
+    ref = (idx + q[None, :] * n) @ a
+    assert np.allclose(El[inner, 0], ref[inner], rtol=0, atol=1e-12)
+
+
+def test_kq_interpolation_gauge_and_convergence(oracle_mod):
+    """|<m,k|n,k+q>|^2 from interpolated eigenvectors does not depend on the phases the mesh's
+    eigenvectors carry; interpolated energies converge to the exact ones at k+q at second order
+    in the mesh spacing (smooth bands of the seeded model)."""
+    rng = np.random.default_rng(4)
+    W = wl.tiny_tb(n=4, norb=3, nq=0, seed=wl.SEED_BASE + 52)
+    q = (0.173, 0.061, 0.29)
+    _, Cq = oracle_mod.kq_interpolate(W, q)
+    ph = np.exp(2j * np.pi * rng.uniform(size=(W.C.shape[0], 1, W.C.shape[2])))
+    Wp = wl.Workload(W.name, W.n, W.periodic, W.nb, W.norb, W.E, W.C * ph, W.ef, W.window, W.cma, [])
+    _, Cqp = oracle_mod.kq_interpolate(Wp, q)
+    M = np.abs(np.einsum("kom,kon->kmn", np.conj(W.C), Cq)) ** 2
+    Mp = np.abs(np.einsum("kom,kon->kmn", np.conj(Wp.C), Cqp)) ** 2
+    assert np.allclose(M, Mp, atol=1e-12)
+    m = wl.random_model(2, wl.SEED_BASE + 53, spread=2.0)
+    errs = []
+    for n in (8, 16):
+        E, C = m.eig_grid((n, n, n))
+        Wn = wl.Workload("s", (n, n, n), True, 2, 2, E, C, 0.0, (0, 2), False, [])
+        Eq, _ = oracle_mod.kq_interpolate(Wn, q)
+        Qx = wl.explicit_q(m, (n, n, n), np.array(q))
+        errs.append(np.max(np.abs(Eq - Qx.Eq)))
+    assert errs[1] < errs[0] / 3.0, errs
