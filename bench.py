@@ -286,8 +286,8 @@ TRAFFIC_PER_PIECE_MIXED = 3.58
 # 72^3 mesh, one q: the full mesh's mix of pieces; the FP64 kernel's FP64 operations likewise).
 # DRAM bytes: not taken from the sample (its scattered tetrahedra defeat the caches that the
 # whole mesh uses), None until counted on the whole mesh.
-FLOPS_PER_PIECE_DYN32 = 2855.8
-FLOPS_PER_PIECE_DYN64 = 5846.8
+FLOPS_PER_PIECE_DYN32 = 2987.4
+FLOPS_PER_PIECE_DYN64 = 6346.5
 TRAFFIC_PER_PIECE_DYN32 = None
 
 
