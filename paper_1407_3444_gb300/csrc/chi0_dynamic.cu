@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
   __shared__ T s_scr[W][KU];
   __shared__ int s_pk[W][DC];
   // ring queue: offsets e from D0 (sorted), values f, (weight, D0h, D0l), box
-  __shared__ T s_qe[W][QC][4], s_qf[W][QC][4], s_qv[W][QC][3];
+  __shared__ __align__(16) T s_qe[W][QC][4];
+  __shared__ __align__(16) T s_qf[W][QC][4];
+  __shared__ T s_qv[W][QC][3];
   __shared__ int s_qb[W][QC];
   // FP64 kernel: per-warp compensated sums of the batch (static batch order); FP32 kernel:
   // per-CTA fixed-point sums of the whole launch (s_fx; batches in any order)
@@ -548,12 +550,20 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
         T ee[4], d[4];
         const T D0h = s_qv[wib][sl][1], D0l = s_qv[wib][sl][2];
         vr = s_qv[wib][sl][0];
+        if constexpr (FP64) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          ee[i] = s_qe[wib][sl][i];
-          ff[i] = s_qf[wib][sl][i];
-          d[i] = D0h + ee[i];
+          for (int i = 0; i < 4; ++i) {
+            ee[i] = s_qe[wib][sl][i];
+            ff[i] = s_qf[wib][sl][i];
+          }
+        } else {  // one 16-byte load each
+          const float4 e4 = *reinterpret_cast<const float4 *>(&s_qe[wib][sl][0]);
+          const float4 f4 = *reinterpret_cast<const float4 *>(&s_qf[wib][sl][0]);
+          ee[0] = e4.x, ee[1] = e4.y, ee[2] = e4.z, ee[3] = e4.w;
+          ff[0] = f4.x, ff[1] = f4.y, ff[2] = f4.z, ff[3] = f4.w;
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = D0h + ee[i];
         near_knots<FP64>(ent, d, ee, D0h, D0l, s_w, s_wl, x, neg);
         // (a near entry has the frequency within two half-widths of the piece's midpoint,
         // where the moment series about the knot midpoint does not apply)
@@ -637,8 +647,10 @@ __global__ void __launch_bounds__(DynShape<FP64>::threads, FP64 ? 2 : 3)
       for (int iw = lo + lane, itn = 0; iw < hi; iw += 32, ++itn) {
         const T om = s_w[iw] < T(0) ? -s_w[iw] : s_w[iw];
         T re = T(0);
+        // (the + term is near only for boxes that reach below u = 0 + F R: most boxes skip it)
+        const int t_hi = (b >= 0 && !(Cb < Rb * T(DynShape<FP64>::NF))) ? 0 : 1;
 #pragma unroll 1
-        for (int t = 1; t >= 0; --t) {  // the + term (t = 1), then the - term
+        for (int t = t_hi; t >= 0; --t) {  // the + term (t = 1), then the - term
           int kk = 0;  // own-series terms this lane needs for this term (0: none)
           if (b < 0 || !box_far(Cb, Rb, b, om, t)) {
             const T den = t ? c + om : c - om;
