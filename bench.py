@@ -9,7 +9,9 @@ weights (FP32 with FP64 near-degenerate branches), reduction.  ``value`` is that
 with inputs resident in HBM; the all-FP64 GPU form is timed on the same inputs and reported
 beside it with the normwise error between the two; the FP64 CPU oracle is timed on a bounded,
 seeded sample of the builtin tetrahedra of the same q (``cpu_baseline``), and the GPU forms run
-on the same sample are compared with it (``error.vs_oracle``).
+on the same sample are compared with it (``error.vs_oracle``).  After the timed steps the
+Kramers-Kronig route (Im alone on a grid over the whole spectrum, Re by the transform) is
+timed on the same q and compared with the direct form (``kk_route``; ``--no-kk`` skips it).
 
 Other workloads (``--workload``): cr (Cr-like 9-band static, 48^3, 256 q), free (free-electron
 Lindhard), fese (FeSe-like dynamic, 512 w), sweep (40-band window sweep, static).
