@@ -512,26 +512,37 @@ def run_ours(args):
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
     if args.e2e_steps > 0:
+        # the plan is built in the untimed first step; every timed step hands it the step's
+        # eigen-data from pinned host memory (chi0_plan_update: the H2D copies), runs the
+        # step and reads the results back
         host = chi0.HostInputs(W, pinned=True)
         t_e2e, t_parts = [], []
+        Ph = None
+        plan_ms = None
         for s in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Ph = chi0.Plan(W, precision="mixed", device=False, staged=host, overlap=ovl, tetra=sub)
+            if Ph is None:
+                Ph = chi0.Plan(W, precision="mixed", device=False, staged=host, overlap=ovl, tetra=sub)
+                torch.cuda.synchronize()
+                plan_ms = (time.perf_counter() - t0) * 1e3
+            else:
+                Ph.update(host)
             ta = time.perf_counter()
             out_h = run_step(Ph, W)
-            tb = time.perf_counter()
-            Ph.close()
             t1 = time.perf_counter()
             if s > 0:
                 t_e2e.append(t1 - t0)
-                t_parts.append((ta - t0, tb - ta, t1 - tb))
+                t_parts.append((ta - t0, t1 - ta))
+        Ph.close()
         T = sum(t_e2e) / len(t_e2e)
-        parts = [sum(x[i] for x in t_parts) / len(t_parts) * 1e3 for i in range(3)]
+        parts = [sum(x[i] for x in t_parts) / len(t_parts) * 1e3 for i in range(2)]
         e2e = {"value": nominal / T, "unit": "evals/s", "h2d_bytes_per_step": host.nbytes(),
                "d2h_bytes_per_step": int(sum(o.nbytes for o in out_h) if isinstance(out_h, tuple) else out_h.nbytes),
                "ms_per_step": T * 1e3, "rel_diff_vs_device": rel_err(out_h, mixed),
-               "ms_plan_call_destroy": parts}
+               "ms_update_call": parts, "plan_ms_untimed": plan_ms,
+               "api": "chi0_plan (first, untimed step), then per step chi0_plan_update (host eigen-data) + "
+                      "chi0_dynamic/chi0_static (host results)"}
         del host
 
     peaks, kind = measured_peaks()

@@ -215,6 +215,16 @@ void chi0_opts_default(chi0_opts_t *opts);
 int chi0_plan(const chi0_kgrid_t *kgrid, const chi0_tetra_t *tetra, chi0_band_window_t window,
               const chi0_opts_t *opts, chi0_plan_t **out);
 
+/* New eigen-data for an existing plan: the same mesh, bands, orbitals, eigenvector type and
+ * Fermi level, new energies [Nk][nbands] (ascending per k) and eigenvectors [Nk][norb][nbands]
+ * (ignored with CMA).  Host inputs are checked and their copies into the plan's buffers
+ * enqueued on the plan's stream (the arrays must stay unchanged until the stream has passed
+ * the copies); device inputs are adopted (the caller keeps them alive).  The band bounds and the FP32 copies of the mixed form
+ * are rebuilt, a captured graph is dropped.  Lets repeated calls on new data reuse the plan's
+ * allocations.  Errors: CHI0_EINVAL (NULL plan or energies, evecs NULL without CMA, energies
+ * not ascending), CHI0_ECUDA. */
+int chi0_plan_update(chi0_plan_t *plan, const double *energies, const void *evecs);
+
 /* Static chi0(q, w = 0) (Eq. 1 at w = 0, Sec. III) for nq q points: chi[iq].
  * Errors: CHI0_EINVAL (nq <= 0, NULL pointers, shift on a non-periodic grid, window
  * outside the plan's), CHI0_ECUDA, CHI0_ETIMEOUT (a tensor-core overlap wait ran out of
@@ -354,7 +364,7 @@ void chi0_destroy(chi0_plan_t *plan);
 const char *chi0_last_error(const chi0_plan_t *plan);
 
 /* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow
- * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs; 103 adds chi0_dynamic_kk; 104 adds chi0_interpolate_kq. */
+ * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs; 103 adds chi0_dynamic_kk; 104 adds chi0_interpolate_kq; 105 adds chi0_plan_update. */
 int chi0_version(void);
 
 #ifdef __cplusplus

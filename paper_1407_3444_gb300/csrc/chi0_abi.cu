@@ -124,7 +124,7 @@ extern "C" void chi0_opts_default(chi0_opts_t *o) {
   o->wait_budget = 0;
 }
 
-extern "C" int chi0_version(void) { return 104; }
+extern "C" int chi0_version(void) { return 105; }
 
 extern "C" const char *chi0_last_error(const chi0_plan_t *p) { return p ? p->err : g_plan_err; }
 
@@ -774,6 +774,37 @@ extern "C" int chi0_static_pairs(chi0_plan_t *p, const chi0_q_t *q, int nq, doub
   if (!pairs) return fail(p, CHI0_EINVAL, "pairs is NULL");
   if (p && p->win.hi - p->win.lo > 1024) return fail(p, CHI0_EINVAL, "band-pair output: window wider than 1024");
   return run(p, q, nq, nullptr, 0, chi, nullptr, pairs);
+}
+
+extern "C" int chi0_plan_update(chi0_plan_t *p, const double *energies, const void *evecs) {
+  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
+  if (!energies) return fail(p, CHI0_EINVAL, "energies is NULL");
+  if (!p->opts.cma && !evecs) return fail(p, CHI0_EINVAL, "evecs is NULL without CMA");
+  const Grid &g = p->g;
+  const chi0_opts_t &op = p->opts;
+  const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;
+  const size_t cb = op.cma ? 0 : cplx_size(p->dtype) * (size_t)g.nc * g.norb * g.nb;
+  drop_graph(p);  // a captured call holds the old pointers
+  if (op.inputs_on_device) {
+    p->E_d = (double *)energies;
+    if (!op.cma) p->C_d = (void *)evecs;
+  } else {
+    for (long long c = 0; c < g.nc; ++c)
+      for (int b = 1; b < g.nb; ++b)
+        if (energies[c * g.nb + b] < energies[c * g.nb + b - 1])
+          return fail(p, CHI0_EINVAL, "energies not ascending at corner %lld band %d", c, b);
+    CK(p, cudaMemcpyAsync(p->E_d, energies, eb, cudaMemcpyHostToDevice, p->stream));
+    if (!op.cma) CK(p, cudaMemcpyAsync(p->C_d, evecs, cb, cudaMemcpyHostToDevice, p->stream));
+  }
+  CK(p, launch_bands(p->E_d, g.nc, g.nb, g.ef, p->occ_d, p->emp_d, p->E32_d, p->stream,
+                     p->E32_d ? p->E32_d + (size_t)g.nc * g.nb : nullptr));
+  p->stats.kernels += 1;
+  if (p->C32_d) {
+    CK(p, launch_c128_to_c64(p->C_d, p->C32_d, g.nc * (long long)g.norb * g.nb, p->stream));
+    p->stats.kernels += 1;
+  }
+  CK(p, cudaGetLastError());
+  return CHI0_OK;
 }
 
 extern "C" int chi0_interpolate_kq(chi0_plan_t *p, const double *qfrac, double *e_kq, void *c_kq) {

@@ -181,6 +181,33 @@ def test_interpolated_kq(C, O, cdt):
     assert nerr(got[:, None], ref[:, None]) < (1e-12 if cdt == "c128" else 1e-6)
 
 
+@pytest.mark.parametrize("device", [True, False])
+def test_plan_update_matches_a_fresh_plan(C, device):
+    """chi0_plan_update: a plan built on one model's eigen-data and handed another's (same
+    shapes) gives bitwise the results of a plan built on the second, static and dynamic, mixed
+    (its FP32 copies rebuilt) and FP64."""
+    Wa = wl.tiny_tb(n=6, norb=4, nq=0, seed=wl.SEED_BASE + 55)
+    Wb = wl.tiny_tb(n=6, norb=4, nq=0, seed=wl.SEED_BASE + 56)
+    Wb.ef = Wa.ef  # the plan keeps its Fermi level
+    qs = [wl.QPoint(shift=(1, 0, 2)), wl.QPoint(shift=(3, 3, 1))]
+    Wa.qs, Wb.qs = qs, qs
+    omega = np.linspace(0.0, 2.0, 40)
+    for prec in ("mixed", "fp64"):
+        Pa = C.Plan(Wa, precision=prec, device=device)
+        Sb = C.DeviceInputs(Wb) if device else C.HostInputs(Wb, pinned=False)
+        Pa.update(Sb)
+        got_s = Pa.static()
+        got_d = Pa.dynamic(omega)
+        Pa.close()
+        Pb = C.Plan(Wb, precision=prec, device=device)
+        ref_s = Pb.static()
+        ref_d = Pb.dynamic(omega)
+        Pb.close()
+        cv = (lambda x: x.cpu().numpy()) if device else np.asarray
+        assert np.array_equal(cv(got_s), cv(ref_s))
+        assert np.array_equal(cv(got_d[0]), cv(ref_d[0])) and np.array_equal(cv(got_d[1]), cv(ref_d[1]))
+
+
 def test_static_host_inputs_and_c64(C, O):
     W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 43, cdtype=np.complex64)
     ref = O.chi0(W)  # the oracle promotes the same complex64 values
