@@ -245,39 +245,6 @@ __device__ __forceinline__ void box_moments_fx(const float e[4], const float f[4
 // faster than calling them.
 template <typename T> __device__ __noinline__ T delta_sum_ol(const T d[4], const T f[4]) { return delta_sum(d, f, T(0)); }
 
-// own-series terms for convergence ratio rho (rho^kk <= tol), at most K
-template <typename T> __device__ __forceinline__ int own_terms(int K, T rho) {
-  if (!(rho > T(0))) return K > 0 ? 1 : 0;
-  const float need = __fdividef(Num<T>::log2_tol, __log2f((float)rho));
-  const int kk = 2 + (int)need;
-  return kk < K ? kk : K;
-}
-
-// (1/(c - w)) sum_{k<kk} a_k z^k, z = c/(c - w), as two half-length Horner chains (even and
-// odd powers); FP32 coefficients read in aligned pairs
-template <typename T> __device__ __forceinline__ T far_eval_k(const T *a, int kk, T c, T w) {
-  const T den = c - w, rd = rcp(den);
-  const T z = c * rd, z2 = z * z;
-  T e = T(0), o = T(0);
-  int k = kk - 1;
-  if (k >= 0 && (k & 1) == 0) e = a[k--];
-#pragma unroll 2
-  for (; k >= 1; k -= 2) {
-    T lo_, hi_;
-    if constexpr (sizeof(T) == 4) {
-      const float2 pr = *reinterpret_cast<const float2 *>(a + k - 1);
-      lo_ = pr.x;
-      hi_ = pr.y;
-    } else {
-      lo_ = a[k - 1];
-      hi_ = a[k];
-    }
-    o = o * z2 + hi_;
-    e = e * z2 + lo_;
-  }
-  return (e + z * o) * rd;
-}
-
 // does box b stand in for term (0: 1/(D - u), 1: 1/(D + u)) at frequency u = om?  Fine boxes
 // only near themselves; geometric boxes always.  Same expression in both kernels.
 template <typename T> __device__ __forceinline__ bool box_far(T C, T R, int b, T om, int term) {

@@ -515,25 +515,48 @@ template <typename T, int KMAX> __device__ int far_moments(const T d[4], const T
   return k;
 }
 
-// (1/(c - w)) sum_{k<K} a_k z^k with z = c/(c - w), truncated where rho^k < tol.  The
-// polynomial is split into its even and odd parts, E(z^2) + z O(z^2), two independent Horner
-// chains of half the length (the weight kernels are bound by dependent latency).
-template <typename T> __device__ __forceinline__ T far_eval(const T *a, int K, T c, T w, T rho) {
+// own-series terms for convergence ratio rho (rho^kk <= tol), at most K
+template <typename T> __device__ __forceinline__ int own_terms(int K, T rho) {
+  if (!(rho > T(0))) return K > 0 ? 1 : 0;
+  const float need = __fdividef(Num<T>::log2_tol, __log2f((float)rho));  // rho^need = tol
+  const int kk = 2 + (int)need;
+  return kk < K ? kk : K;
+}
+
+// (1/(c - w)) sum_{k<kk} a_k z^k, z = c/(c - w), as two half-length Horner chains (even and
+// odd powers: the weight kernels are bound by dependent latency); on the device, FP32
+// coefficients are read in aligned pairs (a + k - 1 even: the caller's stride is even)
+template <typename T> __device__ __forceinline__ T far_eval_k(const T *a, int kk, T c, T w) {
   const T den = c - w, rd = rcp(den);
   const T z = c * rd, z2 = z * z;
-  int kk = K;
-  if (rho > T(0)) {
-    const float need = __fdividef(Num<T>::log2_tol, __log2f((float)rho));  // rho^need = tol
-    kk = min(K, 2 + (int)need);
-  }
   T e = T(0), o = T(0);
   int k = kk - 1;
-  if (k >= 0 && (k & 1) == 0) e = a[k--];  // the top index odd from here on
+  if (k >= 0 && (k & 1) == 0) e = a[k--];
+#pragma unroll 2
   for (; k >= 1; k -= 2) {
-    o = o * z2 + a[k];
-    e = e * z2 + a[k - 1];
+    T lo_, hi_;
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+      const float2 pr = *reinterpret_cast<const float2 *>(a + k - 1);
+      lo_ = pr.x;
+      hi_ = pr.y;
+    } else {
+      lo_ = a[k - 1];
+      hi_ = a[k];
+    }
+#else
+    lo_ = a[k - 1];
+    hi_ = a[k];
+#endif
+    o = o * z2 + hi_;
+    e = e * z2 + lo_;
   }
   return (e + z * o) * rd;
+}
+
+// (1/(c - w)) sum_{k<K} a_k z^k with z = c/(c - w), truncated where rho^k < tol
+template <typename T> __device__ __forceinline__ T far_eval(const T *a, int K, T c, T w, T rho) {
+  return far_eval_k(a, own_terms(K, rho), c, w);
 }
 
 // Normalised cubic B-spline density M(w; t0..t4) (integral 1) by the de Boor-Cox
