@@ -1,7 +1,8 @@
-"""Planted mistakes: each test copies the oracle, plants one plausible error in its C source
-(a wrong repeated knot, a sign, a cut fraction, a missing conjugate or factor, a transposed
-band index), builds the copy on the CPU and checks that the pins of test_oracle_pins.py
-reject it.  The real oracle is never modified."""
+"""Planted mistakes: each test copies the oracle, plants one plausible error in its C source or
+its Python part (a wrong repeated knot, a sign, a cut fraction, a missing conjugate or
+factor, a transposed band index, a dropped term of the Kramers-Kronig kernel, swapped
+interpolation weights, no phase alignment), builds the copy on the CPU and checks that the
+pins of test_oracle_pins.py reject it.  The real oracle is never modified."""
 import importlib.util
 import os
 import shutil
@@ -36,16 +37,37 @@ MUTANTS = [
     ("gamma_dos_dropped", "if (nw == 0 || in->omega[k] == 0.0) re_out[k] += sgn * 2.0 * acc_val(&G);",
      "if (nw == 0 || in->omega[k] == 0.0) re_out[k] += 0.0 * acc_val(&G);",
      ["test_free_electron_q0_limit"]),
+    ("pairs_transposed", "acc_add(&P[((size_t)tid * w + (m - in->lo)) * w + (n - in->lo)], acc_val(&one));",
+     "acc_add(&P[((size_t)tid * w + (n - in->lo)) * w + (m - in->lo)], acc_val(&one));",
+     ["test_pairs_flat_bands_closed_form"]),
+    ("pairs_gamma_dos_dropped", "pairs[(m - in->lo) * (w + 1)] += sgn * 2.0 * acc_val(&G);",
+     "pairs[(m - in->lo) * (w + 1)] += 0.0 * acc_val(&G);",
+     ["test_pairs_add_up_to_chi0"]),
+    ("kk_plus_term_dropped@py", "        for c in (wv, -wv):\n            for j in range(len(uu) - 1):",
+     "        for c in (wv,):\n            for j in range(len(uu) - 1):",
+     ["test_kk_transform_matches_cauchy_quadrature", "test_kk_route_converges_to_principal_value"]),
+    ("interp_weights_swapped@py",
+     "w = [1.0 - tc[order[0]], tc[order[0]] - tc[order[1]], tc[order[1]] - tc[order[2]], tc[order[2]]]",
+     "w = [1.0 - tc[order[0]], tc[order[1]] - tc[order[2]], tc[order[0]] - tc[order[1]], tc[order[2]]]",
+     ["test_kq_interpolation_on_grid_and_linear"]),
+    ("interp_no_phase@py", "ph = np.where(m > 0, np.conj(ov) / np.where(m > 0, m, 1.0), 1.0)",
+     "ph = np.ones(vi.shape[1], dtype=np.complex128)",
+     ["test_kq_interpolation_gauge_and_convergence"]),
 ]
 
 
 def _mutant_module(tmp_path, name, old, new):
-    src = open(os.path.join(ORACLE_DIR, "chi0_oracle.c")).read()
+    """A copy of the oracle with `old` replaced by `new` in its C source, or in its Python part
+    for names ending in "@py"."""
+    target = "__init__.py" if name.endswith("@py") else "chi0_oracle.c"
+    other = "chi0_oracle.c" if target == "__init__.py" else "__init__.py"
+    src = open(os.path.join(ORACLE_DIR, target)).read()
     assert src.count(old) == 1, "planting site not unique: %r" % old
+    name = name.replace("@py", "_py")
     d = tmp_path / ("oracle_mut_" + name)
     d.mkdir()
-    shutil.copy(os.path.join(ORACLE_DIR, "__init__.py"), d / "__init__.py")
-    (d / "chi0_oracle.c").write_text(src.replace(old, new))
+    shutil.copy(os.path.join(ORACLE_DIR, other), d / other)
+    (d / target).write_text(src.replace(old, new))
     spec = importlib.util.spec_from_file_location("oracle_mut_" + name, str(d / "__init__.py"),
                                                   submodule_search_locations=[str(d)])
     mod = importlib.util.module_from_spec(spec)
