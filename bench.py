@@ -287,7 +287,8 @@ TRAFFIC_PER_PIECE_MIXED = 3.58
 # (ncu instruction counters of k_dynamic on a seeded sample of 16384 tetrahedra of the 80-band
 # 72^3 mesh, one q: the full mesh's mix of pieces; the FP64 kernel's FP64 operations likewise).
 # DRAM bytes: not taken from the sample (its scattered tetrahedra defeat the caches that the
-# whole mesh uses), None until counted on the whole mesh.
+# whole mesh uses); on whole meshes they fall per final tetrahedron as the mesh grows (29.3 B at
+# 24^3, 16.4 B at 48^3), so no per-unit figure scales to the 72^3 launch: None until counted there.
 FLOPS_PER_PIECE_DYN32 = 2987.4
 FLOPS_PER_PIECE_DYN64 = 6346.5
 TRAFFIC_PER_PIECE_DYN32 = None
