@@ -225,6 +225,23 @@ int chi0_plan(const chi0_kgrid_t *kgrid, const chi0_tetra_t *tetra, chi0_band_wi
  * not ascending), CHI0_ECUDA. */
 int chi0_plan_update(chi0_plan_t *plan, const double *energies, const void *evecs);
 
+/* Staged eigen-data for a later call, for plans with host inputs: the arrays (same shapes and
+ * rules as chi0_plan_update) are checked and their copies enqueued on a copy stream of the
+ * plan's own, and the call returns.  Up to two staged sets wait for calls; each call that
+ * reads the eigen-data (chi0_static, chi0_static_pairs, chi0_dynamic, chi0_dynamic_kk,
+ * chi0_interpolate_kq, chi0_tune) first takes the oldest of them: the plan's stream waits for
+ * its copies and the call computes on it.  So with stage(i + 1) issued before call(i), step
+ * i + 1's data are copied while step i computes.  The plan holds a second set of eigen-data
+ * buffers (allocated on the first staging); a staged set lands in whichever of the two sets no
+ * later call reads, after the work already enqueued on the plan's stream.  From page-locked
+ * host memory the copies run alongside the kernels; from pageable memory this call returns
+ * only once the arrays have been read.  The host arrays must stay unchanged until the plan's
+ * stream has passed the call that takes them (for a call with host outputs: until it has
+ * returned).  chi0_plan_update drops the staged sets that no call has taken.  Errors:
+ * CHI0_EINVAL (NULL plan or energies, evecs NULL without CMA, energies not ascending, a plan
+ * with device inputs, two staged sets waiting already), CHI0_ENOMEM, CHI0_ECUDA. */
+int chi0_plan_stage(chi0_plan_t *plan, const double *energies, const void *evecs);
+
 /* Static chi0(q, w = 0) (Eq. 1 at w = 0, Sec. III) for nq q points: chi[iq].
  * Errors: CHI0_EINVAL (nq <= 0, NULL pointers, shift on a non-periodic grid, window
  * outside the plan's), CHI0_ECUDA, CHI0_ETIMEOUT (a tensor-core overlap wait ran out of
@@ -364,7 +381,7 @@ void chi0_destroy(chi0_plan_t *plan);
 const char *chi0_last_error(const chi0_plan_t *plan);
 
 /* Library ABI version (major*10000 + minor*100 + patch): 101 adds chi0_stats_t.queue_overflow
- * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs; 103 adds chi0_dynamic_kk; 104 adds chi0_interpolate_kq; 105 adds chi0_plan_update. */
+ * and chi0_stats_t.box_pieces; 102 adds chi0_static_pairs; 103 adds chi0_dynamic_kk; 104 adds chi0_interpolate_kq; 105 adds chi0_plan_update; 106 adds chi0_plan_stage. */
 int chi0_version(void);
 
 #ifdef __cplusplus

@@ -93,7 +93,8 @@ _lib = None
 # every entry point declared in include/chi0.h (checked by the ABI test)
 EXPORTS = ["chi0_opts_default", "chi0_plan", "chi0_static", "chi0_dynamic", "chi0_plan_stats",
            "chi0_destroy", "chi0_last_error", "chi0_version", "chi0_static_noalloc", "chi0_tune", "chi0_peak",
-           "chi0_static_pairs", "chi0_dynamic_kk", "chi0_interpolate_kq", "chi0_plan_update"]
+           "chi0_static_pairs", "chi0_dynamic_kk", "chi0_interpolate_kq", "chi0_plan_update",
+           "chi0_plan_stage"]
 CHI0_PEAK_FP32_FMA, CHI0_PEAK_FP64_FMA, CHI0_PEAK_TF32_MMA, CHI0_PEAK_BF16_MMA = 0, 1, 2, 3
 CHI0_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -121,6 +122,8 @@ def lib():
         L.chi0_interpolate_kq.restype = ct.c_int
         L.chi0_plan_update.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
         L.chi0_plan_update.restype = ct.c_int
+        L.chi0_plan_stage.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
+        L.chi0_plan_stage.restype = ct.c_int
         L.chi0_dynamic.argtypes = [ct.c_void_p, ct.POINTER(chi0_q_t), ct.c_int, ct.c_void_p, ct.c_int,
                                    ct.c_void_p, ct.c_void_p]
         L.chi0_dynamic.restype = ct.c_int
@@ -423,6 +426,13 @@ class Plan:
         """New eigen-data (a ``Staged`` of the same shapes and placement) for this plan."""
         _check(lib().chi0_plan_update(self.h, staged.E, staged.C if not self.cma else None), self.h)
         self.staged = staged
+
+    def stage(self, staged):
+        """Eigen-data (a host ``Staged``, best pinned) for a later call: up to two staged sets
+        wait, and each call takes the oldest; the copies run while the plan's stream computes.
+        The plan keeps references to the last three staged sets (two waiting, one current)."""
+        _check(lib().chi0_plan_stage(self.h, staged.E, staged.C if not self.cma else None), self.h)
+        self._held = getattr(self, "_held", ())[-2:] + (staged,)
 
     def interpolate_kq(self, qfrac):
         """Energies [Nc, nb] and eigenvectors [Nc, norb, nb] at k+q by linear interpolation from

@@ -40,6 +40,12 @@ struct chi0_plan {
   cudaStream_t copy_s = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   int stage_slot = 0;
+  double *E_alt = nullptr;                    // chi0_plan_stage: the second set of eigen-data
+  void *C_alt = nullptr;                      // buffers, filled on a stream of its own while
+  cudaStream_t next_s = nullptr;              // the plan's stream computes.  npend staged sets
+  cudaEvent_t ev_staged[2] = {nullptr, nullptr};  // wait for calls (the oldest in the alt set,
+  cudaEvent_t ev_readers = nullptr;           // a second one in the current set, which no call
+  int npend = 0;                              // reads again); ev_staged: their copies done
   unsigned long long *counters_d = nullptr;
   short *occ_d = nullptr, *emp_d = nullptr, *occq_d = nullptr, *empq_d = nullptr;
   float *E32_d = nullptr, *Eq32_d = nullptr;  // energies - eF in FP32 (mixed precision): hi, then lo
@@ -124,7 +130,7 @@ extern "C" void chi0_opts_default(chi0_opts_t *o) {
   o->wait_budget = 0;
 }
 
-extern "C" int chi0_version(void) { return 105; }
+extern "C" int chi0_version(void) { return 106; }
 
 extern "C" const char *chi0_last_error(const chi0_plan_t *p) { return p ? p->err : g_plan_err; }
 
@@ -156,6 +162,15 @@ static void release(chi0_plan_t *p) {
     if (p->ev_free[i]) cudaEventDestroy(p->ev_free[i]);
   }
   if (p->copy_s) cudaStreamDestroy(p->copy_s);
+  if (p->next_s) {
+    cudaStreamSynchronize(p->next_s);  // a staged copy may still be in flight
+    cudaStreamDestroy(p->next_s);
+  }
+  cudaFree(p->E_alt);
+  cudaFree(p->C_alt);
+  for (int i = 0; i < 2; ++i)
+    if (p->ev_staged[i]) cudaEventDestroy(p->ev_staged[i]);
+  if (p->ev_readers) cudaEventDestroy(p->ev_readers);
   cudaFree(p->counters_d);
   cudaFree(p->occ_d);
   cudaFree(p->emp_d);
@@ -630,6 +645,39 @@ static void drop_graph(chi0_plan_t *p) {
   p->gkernels = 0;
 }
 
+// band bounds and FP32 copies of the plan's current eigen-data (the mixed form's inputs)
+static int derive_inputs(chi0_plan_t *p) {
+  const Grid &g = p->g;
+  CK(p, launch_bands(p->E_d, g.nc, g.nb, g.ef, p->occ_d, p->emp_d, p->E32_d, p->stream,
+                     p->E32_d ? p->E32_d + (size_t)g.nc * g.nb : nullptr));
+  p->stats.kernels += 1;
+  if (p->C32_d) {
+    CK(p, launch_c128_to_c64(p->C_d, p->C32_d, g.nc * (long long)g.norb * g.nb, p->stream));
+    p->stats.kernels += 1;
+  }
+  return CHI0_OK;
+}
+
+// the oldest set staged by chi0_plan_stage (always in the alt buffers) becomes the current
+// eigen-data: the plan's stream waits for its copies, and the sets swap places (a second
+// staged set, in the old current buffers, is then the one in the alt buffers)
+static int take_staged(chi0_plan_t *p) {
+  if (p->npend == 0) return CHI0_OK;
+  drop_graph(p);  // a captured call holds the old pointers
+  CK(p, cudaStreamWaitEvent(p->stream, p->ev_staged[0], 0));
+  double *e = p->E_d;
+  p->E_d = p->E_alt;
+  p->E_alt = e;
+  void *c = p->C_d;
+  p->C_d = p->C_alt;
+  p->C_alt = c;
+  cudaEvent_t ev = p->ev_staged[0];
+  p->ev_staged[0] = p->ev_staged[1];
+  p->ev_staged[1] = ev;
+  p->npend -= 1;
+  return derive_inputs(p);
+}
+
 static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, int nw, double *re,
                double *im, double *pairs = nullptr, double kk_du = 0.0) {
   if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
@@ -639,6 +687,10 @@ static int run(chi0_plan_t *p, const chi0_q_t *qs, int nq, const double *omega, 
   if (!dyn && !re) return fail(p, CHI0_EINVAL, "chi is NULL");
   for (int iq = 0; iq < nq; ++iq) {  // validation before any launch
     const int rc = validate_q(p, qs[iq]);
+    if (rc) return rc;
+  }
+  {
+    const int rc = take_staged(p);
     if (rc) return rc;
   }
   const chi0_opts_t &op = p->opts;
@@ -785,6 +837,10 @@ extern "C" int chi0_plan_update(chi0_plan_t *p, const double *energies, const vo
   const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;
   const size_t cb = op.cma ? 0 : cplx_size(p->dtype) * (size_t)g.nc * g.norb * g.nb;
   drop_graph(p);  // a captured call holds the old pointers
+  if (p->npend > 0) {  // the new data replace staged sets, whose copies may still write the
+    CK(p, cudaStreamWaitEvent(p->stream, p->ev_staged[p->npend - 1], 0));  // current buffers
+    p->npend = 0;
+  }
   if (op.inputs_on_device) {
     p->E_d = (double *)energies;
     if (!op.cma) p->C_d = (void *)evecs;
@@ -796,14 +852,43 @@ extern "C" int chi0_plan_update(chi0_plan_t *p, const double *energies, const vo
     CK(p, cudaMemcpyAsync(p->E_d, energies, eb, cudaMemcpyHostToDevice, p->stream));
     if (!op.cma) CK(p, cudaMemcpyAsync(p->C_d, evecs, cb, cudaMemcpyHostToDevice, p->stream));
   }
-  CK(p, launch_bands(p->E_d, g.nc, g.nb, g.ef, p->occ_d, p->emp_d, p->E32_d, p->stream,
-                     p->E32_d ? p->E32_d + (size_t)g.nc * g.nb : nullptr));
-  p->stats.kernels += 1;
-  if (p->C32_d) {
-    CK(p, launch_c128_to_c64(p->C_d, p->C32_d, g.nc * (long long)g.norb * g.nb, p->stream));
-    p->stats.kernels += 1;
-  }
+  const int rc = derive_inputs(p);
+  if (rc) return rc;
   CK(p, cudaGetLastError());
+  return CHI0_OK;
+}
+
+extern "C" int chi0_plan_stage(chi0_plan_t *p, const double *energies, const void *evecs) {
+  if (!p) return fail(nullptr, CHI0_EINVAL, "plan is NULL");
+  if (!energies) return fail(p, CHI0_EINVAL, "energies is NULL");
+  if (!p->opts.cma && !evecs) return fail(p, CHI0_EINVAL, "evecs is NULL without CMA");
+  if (p->opts.inputs_on_device) return fail(p, CHI0_EINVAL, "staging copies host inputs; a device-input plan adopts new pointers with chi0_plan_update");
+  if (p->npend >= 2) return fail(p, CHI0_EINVAL, "two staged sets wait for calls already");
+  const Grid &g = p->g;
+  const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;
+  const size_t cb = p->opts.cma ? 0 : cplx_size(p->dtype) * (size_t)g.nc * g.norb * g.nb;
+  for (long long c = 0; c < g.nc; ++c)
+    for (int b = 1; b < g.nb; ++b)
+      if (energies[c * g.nb + b] < energies[c * g.nb + b - 1])
+        return fail(p, CHI0_EINVAL, "energies not ascending at corner %lld band %d", c, b);
+  if (!p->next_s) {
+    CK(p, cudaStreamCreateWithFlags(&p->next_s, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) CK(p, cudaEventCreateWithFlags(&p->ev_staged[i], cudaEventDisableTiming));
+    CK(p, cudaEventCreateWithFlags(&p->ev_readers, cudaEventDisableTiming));
+  }
+  if (!p->E_alt) CK(p, cudaMalloc(&p->E_alt, eb));
+  if (cb && !p->C_alt) CK(p, cudaMalloc(&p->C_alt, cb));
+  // nothing staged: the copies go to the alt buffers; one set staged (in the alt buffers): to
+  // the current ones, which the next call swaps out unread.  Either way the buffers' readers
+  // are enqueued on the plan's stream before this point, so the copies wait for that work.
+  double *E_dst = p->npend == 0 ? p->E_alt : p->E_d;
+  void *C_dst = p->npend == 0 ? p->C_alt : p->C_d;
+  CK(p, cudaEventRecord(p->ev_readers, p->stream));
+  CK(p, cudaStreamWaitEvent(p->next_s, p->ev_readers, 0));
+  CK(p, cudaMemcpyAsync(E_dst, energies, eb, cudaMemcpyHostToDevice, p->next_s));
+  if (cb) CK(p, cudaMemcpyAsync(C_dst, evecs, cb, cudaMemcpyHostToDevice, p->next_s));
+  CK(p, cudaEventRecord(p->ev_staged[p->npend], p->next_s));
+  p->npend += 1;
   return CHI0_OK;
 }
 
@@ -813,6 +898,10 @@ extern "C" int chi0_interpolate_kq(chi0_plan_t *p, const double *qfrac, double *
   if (!p->g.periodic) return fail(p, CHI0_EINVAL, "k+q interpolation needs a periodic grid");
   for (int d = 0; d < 3; ++d)
     if (!(fabs(qfrac[d]) < 1e6)) return fail(p, CHI0_EINVAL, "qfrac[%d] = %g", d, qfrac[d]);
+  {
+    const int rc = take_staged(p);
+    if (rc) return rc;
+  }
   const Grid &g = p->g;
   const bool vecs = c_kq && !p->opts.cma;
   const size_t eb = sizeof(double) * (size_t)g.nc * g.nb;

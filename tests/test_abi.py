@@ -142,6 +142,9 @@ def test_null_plan_calls_fail_cleanly(lib):
     with pytest.raises(lib.Chi0Error) as ei:
         lib.chi0_static(None, q, 1, out.ctypes.data)
     assert ei.value.code == lib.CHI0_EINVAL
+    e = np.zeros(4)
+    for fn in ("chi0_plan_update", "chi0_plan_stage"):  # checked before any CUDA call
+        assert getattr(lib.lib(), fn)(None, e.ctypes.data, e.ctypes.data) == lib.CHI0_EINVAL
 
 
 def test_noalloc_rejects_orbital_counts_beyond_the_plan_limit(lib):

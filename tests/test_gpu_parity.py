@@ -208,6 +208,60 @@ def test_plan_update_matches_a_fresh_plan(C, device):
         assert np.array_equal(cv(got_d[0]), cv(ref_d[0])) and np.array_equal(cv(got_d[1]), cv(ref_d[1]))
 
 
+def test_plan_stage_feeds_the_next_call(C):
+    """chi0_plan_stage: calls take the staged sets oldest first and compute on them (bitwise
+    the results of a plan built on each set), also with two sets waiting (the second copied
+    into the buffers of the set in use before); a call with nothing staged keeps the current
+    set; a third waiting set is refused; chi0_plan_update drops the staged sets; a plan with
+    device inputs refuses staging."""
+    Wa = wl.tiny_tb(n=6, norb=4, nq=0, seed=wl.SEED_BASE + 57)
+    Wb = wl.tiny_tb(n=6, norb=4, nq=0, seed=wl.SEED_BASE + 58)
+    Wb.ef = Wa.ef  # the plan keeps its Fermi level
+    qs = [wl.QPoint(shift=(1, 0, 2)), wl.QPoint(shift=(2, 3, 1))]
+    Wa.qs, Wb.qs = qs, qs
+    omega = np.linspace(0.0, 2.0, 40)
+    for prec in ("mixed", "fp64"):
+        ref = {}
+        for name, W in (("a", Wa), ("b", Wb)):
+            P = C.Plan(W, precision=prec, device=False)
+            ref[name] = (P.static(), P.dynamic(omega))
+            P.close()
+        Sa, Sb = C.HostInputs(Wa, pinned=True), C.HostInputs(Wb, pinned=True)
+        P = C.Plan(Wa, precision=prec, device=False)
+        P.stage(Sb)  # -> the alt buffers
+        P.stage(Sa)  # -> the current buffers (holding a: no call reads them again)
+        with pytest.raises(C.Chi0Error) as ei:
+            P.stage(Sb)  # two sets wait already
+        assert ei.value.code == C.CHI0_EINVAL
+        d1 = P.dynamic(omega)  # takes b
+        s2 = P.static()  # takes a
+        d3 = P.dynamic(omega)  # nothing staged: still a
+        P.stage(Sb)
+        P.stage(Sb)  # into the buffers the current a sits in
+        P.update(Sa)  # drops both (after their copies) and copies a
+        s4 = P.static()
+        seq = "babab"  # the pipeline: stage(i + 1) before call(i)
+        sets = {"a": Sa, "b": Sb}
+        P.stage(sets[seq[0]])
+        s5 = []
+        for i in range(len(seq)):
+            if i + 1 < len(seq):
+                P.stage(sets[seq[i + 1]])
+            s5.append(P.static())
+        d6 = P.dynamic(omega)  # nothing staged: the last set
+        P.close()
+        for got, want in ((d1, ref["b"][1]), (d3, ref["a"][1]), (d6, ref[seq[-1]][1])):
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+        assert np.array_equal(s2, ref["a"][0]) and np.array_equal(s4, ref["a"][0])
+        for got, name in zip(s5, seq):
+            assert np.array_equal(got, ref[name][0])
+    Pd = C.Plan(Wa, precision="mixed", device=True)
+    with pytest.raises(C.Chi0Error) as ei:
+        Pd.stage(C.HostInputs(Wb, pinned=False))
+    assert ei.value.code == C.CHI0_EINVAL
+    Pd.close()
+
+
 def test_static_host_inputs_and_c64(C, O):
     W = wl.tiny_tb(n=6, norb=4, nq=2, seed=wl.SEED_BASE + 43, cdtype=np.complex64)
     ref = O.chi0(W)  # the oracle promotes the same complex64 values
