@@ -1,4 +1,5 @@
-"""Comparison drivers of Sec. III over the library's static entry points.
+"""Comparison drivers of Sec. III over the library's static entry points (the band-pair
+histogram of Fig. 8, the band-truncation and matrix-element studies).
 
 - ``band_truncation``: static chi0(q) with the band sum restricted to windows around E_F
   (the convergence of chi0 with the number of bands, Sec. III; the paper's FeSe result needs
