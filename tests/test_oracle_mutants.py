@@ -53,6 +53,11 @@ MUTANTS = [
     ("interp_no_phase@py", "ph = np.where(m > 0, np.conj(ov) / np.where(m > 0, m, 1.0), 1.0)",
      "ph = np.ones(vi.shape[1], dtype=np.complex128)",
      ["test_kq_interpolation_gauge_and_convergence"]),
+    ("interp_not_normalised@py", "Cq[c] = acc / np.where(nrm > 0, nrm, 1.0)[None, :]", "Cq[c] = acc",
+     ["test_kq_interpolation_gauge_and_convergence"]),
+    ("kk_segment_expanded_at_its_start@py", "tot += beta * (b - a) + (alpha + beta * c) * (lb - la)",
+     "tot += beta * (b - a) + (alpha + beta * a) * (lb - la)",
+     ["test_kk_transform_matches_cauchy_quadrature"]),
 ]
 
 

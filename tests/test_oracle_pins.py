@@ -660,8 +660,9 @@ def test_kq_interpolation_on_grid_and_linear(oracle_mod):
 
 def test_kq_interpolation_gauge_and_convergence(oracle_mod):
     """|<m,k|n,k+q>|^2 from interpolated eigenvectors does not depend on the phases the mesh's
-    eigenvectors carry; interpolated energies converge to the exact ones at k+q at second order
-    in the mesh spacing (smooth bands of the seeded model)."""
+    eigenvectors carry; interpolated eigenvectors have unit norm; interpolated energies and
+    eigenvectors (up to their phase, away from avoided crossings) converge to the exact ones at
+    k+q at second order in the mesh spacing (the seeded model's smooth bands)."""
     rng = np.random.default_rng(4)
     W = wl.tiny_tb(n=4, norb=3, nq=0, seed=wl.SEED_BASE + 52)
     q = (0.173, 0.061, 0.29)
@@ -672,12 +673,17 @@ def test_kq_interpolation_gauge_and_convergence(oracle_mod):
     M = np.abs(np.einsum("kom,kon->kmn", np.conj(W.C), Cq)) ** 2
     Mp = np.abs(np.einsum("kom,kon->kmn", np.conj(Wp.C), Cqp)) ** 2
     assert np.allclose(M, Mp, atol=1e-12)
+    assert np.allclose(np.sum(np.abs(Cq) ** 2, axis=1), 1.0, atol=1e-12)
     m = wl.random_model(2, wl.SEED_BASE + 53, spread=2.0)
-    errs = []
+    errs, verrs = [], []
     for n in (8, 16):
         E, C = m.eig_grid((n, n, n))
         Wn = wl.Workload("s", (n, n, n), True, 2, 2, E, C, 0.0, (0, 2), False, [])
-        Eq, _ = oracle_mod.kq_interpolate(Wn, q)
+        Eq, Cn = oracle_mod.kq_interpolate(Wn, q)
         Qx = wl.explicit_q(m, (n, n, n), np.array(q))
         errs.append(np.max(np.abs(Eq - Qx.Eq)))
+        # 1 - |<exact|interpolated>| per corner and band: its median (the largest values sit at
+        # the model's avoided crossings, where the bands' gap is below the mesh's resolution)
+        verrs.append(np.median(1.0 - np.abs(np.sum(np.conj(Qx.Cq) * Cn, axis=1))))
     assert errs[1] < errs[0] / 3.0, errs
+    assert verrs[1] < verrs[0] / 4.0 and verrs[1] < 1e-4, verrs
