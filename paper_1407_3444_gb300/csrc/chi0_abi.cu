@@ -142,6 +142,7 @@ extern "C" int chi0_plan_stats(const chi0_plan_t *p, chi0_stats_t *s) {
 
 static void release(chi0_plan_t *p) {
   if (!p) return;
+  if (p->next_s) cudaStreamSynchronize(p->next_s);  // staged copies may still write either set
   drop_graph(p);
   if (p->own_E) cudaFree(p->E_d);
   if (p->own_C) cudaFree(p->C_d);
@@ -162,10 +163,7 @@ static void release(chi0_plan_t *p) {
     if (p->ev_free[i]) cudaEventDestroy(p->ev_free[i]);
   }
   if (p->copy_s) cudaStreamDestroy(p->copy_s);
-  if (p->next_s) {
-    cudaStreamSynchronize(p->next_s);  // a staged copy may still be in flight
-    cudaStreamDestroy(p->next_s);
-  }
+  if (p->next_s) cudaStreamDestroy(p->next_s);
   cudaFree(p->E_alt);
   cudaFree(p->C_alt);
   for (int i = 0; i < 2; ++i)
