@@ -280,9 +280,11 @@ def arithmetic_peaks(chi0):
 
 # Executed FP32 operations (FFMA counted twice, FADD, FMUL) per final tetrahedron of the mixed
 # static weight kernels on the Cr-like 48^3 workload (ncu instruction counters of k_static +
-# k_static_tab) and their DRAM bytes per final tetrahedron.
+# k_static_tab, before the long-series queue was compacted over the call: the same arithmetic
+# per piece now runs in k_tab_eval).  Their DRAM bytes per final tetrahedron (3.58 then) are
+# not reported: the kernels have changed since the counters were taken.
 FLOPS_PER_PIECE_MIXED = 202.6
-TRAFFIC_PER_PIECE_MIXED = 3.58
+TRAFFIC_PER_PIECE_MIXED = None
 # The same for the dynamic weight kernel per final tetrahedron over one pass of 256 frequencies
 # (ncu instruction counters of k_dynamic on a seeded sample of 16384 tetrahedra of the 80-band
 # 72^3 mesh, one q: the full mesh's mix of pieces; the FP64 kernel's FP64 operations likewise).
