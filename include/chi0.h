@@ -25,8 +25,10 @@
  * chi0 is returned per unit cell, both spins, in states/(energy unit) -- i.e. the
  * dk/(4 pi^3) measure of Eq. 1 times the cell volume.  Energies in any unit (eV, Ha).
  *
- * Threading: a plan is used by one host thread at a time; all work of a plan runs on
- * the CUDA stream given in its options.  Every call returns CHI0_OK (0) or a negative
+ * Threading: a plan is used by one host thread at a time; all work of a plan is ordered on
+ * the CUDA stream given in its options (host-to-device copies of staged eigen-data and of
+ * explicit k+q data run on copy streams of the plan's own, ordered against that stream by
+ * events).  Every call returns CHI0_OK (0) or a negative
  * status; no C++ exception crosses this interface.  Validation happens before any
  * launch.  After any error the plan can still be destroyed, and chi0_last_error()
  * describes the failure.
@@ -55,7 +57,7 @@ extern "C" {
 
 #define CHI0_PREC_FP64 0  /* every step in FP64 (overlaps, weights, accumulation)          */
 #define CHI0_PREC_MIXED 1 /* FP32 overlaps/weights, FP64 in the near-degenerate branches,
-                             FP64 accumulation                                            */
+                             FP64 or exact 64-bit fixed-point accumulation                */
 
 #define CHI0_OVL_FP32 0   /* mixed precision: overlaps with FP32 FMA on the CUDA cores     */
 #define CHI0_OVL_BF16X3 1 /* mixed precision: overlaps on the tensor cores (tcgen05), each
